@@ -1,0 +1,590 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by plain
+mathematics (closed forms, brute force, invariants, theorems).  CPU only.
+
+Each test names the passage it pins.  None of them re-types the oracle's
+own formulas: the references are closed forms, a different algorithm
+(closed-triangle projection with edge clamping), dense sampling, or
+brute-force enumeration.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import ConvexHull
+
+import datagen as dg
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# --------------------------------------------------------------------------
+# helpers written independently of the oracle
+# --------------------------------------------------------------------------
+
+def closest_on_closed_triangles(V, F, q):
+    """Distance from each q to the union of closed triangles, by projecting
+    onto each triangle's plane and, when the projection falls outside,
+    clamping onto the three closed edges (a different algorithm from the
+    oracle's gated minimum over open primitives)."""
+    V = np.asarray(V, np.float64)
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    best = np.full(q.shape[0], np.inf)
+
+    def seg(p, s0, s1):
+        d = s1 - s0
+        t = np.clip(((p - s0) * d).sum(-1) / (d * d).sum(-1), 0.0, 1.0)
+        x = s0 + t[..., None] * d
+        return np.linalg.norm(p - x, axis=-1)
+
+    for i in range(0, q.shape[0], 256):
+        p = q[i:i + 256, None, :]
+        n = np.cross(b - a, c - a)
+        nn = n / np.linalg.norm(n, axis=1, keepdims=True)
+        h = ((p - a) * nn).sum(-1)
+        x = p - h[..., None] * nn
+        # inside test by same-side signs of the three edge cross products
+        s0 = (np.cross(b - a, x - a) * n).sum(-1)
+        s1 = (np.cross(c - b, x - b) * n).sum(-1)
+        s2 = (np.cross(a - c, x - c) * n).sum(-1)
+        inside = (s0 >= 0) & (s1 >= 0) & (s2 >= 0)
+        dplane = np.abs(h)
+        dedge = np.minimum(np.minimum(seg(p, a, b), seg(p, b, c)), seg(p, c, a))
+        d = np.where(inside, dplane, dedge)
+        best[i:i + 256] = d.min(1)
+    return best
+
+
+def brute_nn(V, q):
+    V = np.asarray(V, np.float64)
+    out = np.empty(q.shape[0], np.int64)
+    for i in range(0, q.shape[0], 512):
+        d2 = ((q[i:i + 512, None, :] - V[None]) ** 2).sum(-1)
+        out[i:i + 512] = d2.argmin(1)  # first minimum = lowest index on ties
+    return out
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# --------------------------------------------------------------------------
+# the plain definition (brute force) against closed forms
+# --------------------------------------------------------------------------
+
+def test_bruteforce_cube_closed_form():
+    """Cube [-1,1]^3: outside d = |max(|q|-1, 0)|, inside d = 1 - max|q_i|;
+    the number of coordinates beyond the cube fixes vertex/edge/face
+    (Sec. 4.1: primitives are vertices, open edges, open faces)."""
+    V, F = dg.cube()
+    o = oracle.OracleMesh(V.astype(np.float32), F, build_tables=False)
+    q = rng(1).uniform(-2.5, 2.5, size=(4000, 3))
+    r = o.bruteforce(q)
+    a = np.abs(q)
+    outside = (a > 1).any(1)
+    d_ref = np.where(outside, np.linalg.norm(np.maximum(a - 1, 0), axis=1), 1 - a.max(1))
+    np.testing.assert_allclose(r["dist"], d_ref, rtol=0, atol=1e-12)
+    k = (a > 1).sum(1)
+    assert (r["ptype"][k == 3] == oracle.VERTEX).all()
+    np.testing.assert_allclose(r["cp"][k == 3], np.sign(q[k == 3]), atol=0)
+    assert (r["ptype"][k == 2] == oracle.EDGE).all()
+    assert np.isin(r["ptype"][k == 1], [oracle.FACE, oracle.EDGE]).all()
+    # an edge answer for k == 1 can only be a square's diagonal (a tie)
+    E = o.edges()
+    e1 = r["pid"][(k == 1) & (r["ptype"] == oracle.EDGE)]
+    if e1.size:
+        diff = np.abs(V[E[e1, 0]] - V[E[e1, 1]])
+        assert ((diff > 0).sum(1) == 2).all()
+
+
+def test_bruteforce_octahedron_face_regions():
+    """Octahedron |x|+|y|+|z| = 1: where the projection onto the octant's
+    face plane lands inside the face, d = |s.q - 1| / sqrt(3)."""
+    V, F = dg.octahedron()
+    o = oracle.OracleMesh(V.astype(np.float32), F, build_tables=False)
+    q = rng(2).uniform(-1.5, 1.5, size=(6000, 3))
+    s = np.sign(q)
+    h = (s * q).sum(1) - 1.0
+    p = q - (h / 3.0)[:, None] * s
+    inside_face = ((s * p) > 1e-9).all(1)
+    r = o.bruteforce(q)
+    np.testing.assert_allclose(r["dist"][inside_face], np.abs(h[inside_face]) / math.sqrt(3),
+                               rtol=0, atol=1e-12)
+    assert (r["ptype"][inside_face] == oracle.FACE).all()
+
+
+def test_bruteforce_sphere_bounds():
+    """Unperturbed icosphere inscribed in the unit sphere with inradius
+    r_in: outside |q|-1 <= d <= |q|-r_in, inside r_in-|q| <= d <= 1-|q|."""
+    V, F = dg.icosphere(2)
+    V32 = V.astype(np.float32)
+    Vd = V32.astype(np.float64)
+    n = np.cross(Vd[F[:, 1]] - Vd[F[:, 0]], Vd[F[:, 2]] - Vd[F[:, 0]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    r_in = (n * Vd[F[:, 0]]).sum(1).min()
+    rmax = np.linalg.norm(Vd, axis=1).max()
+    o = oracle.OracleMesh(V32, F, build_tables=False)
+    q = rng(3).uniform(-2, 2, size=(5000, 3))
+    rq = np.linalg.norm(q, axis=1)
+    d = o.bruteforce(q)["dist"]
+    out = rq > rmax
+    inn = rq < r_in
+    tol = 1e-9
+    assert (d[out] >= rq[out] - rmax - tol).all() and (d[out] <= rq[out] - r_in + tol).all()
+    assert (d[inn] >= r_in - rq[inn] - tol).all() and (d[inn] <= rmax - rq[inn] + tol).all()
+
+
+def test_bruteforce_matches_closed_triangle_projection():
+    """Gated minimum over open primitives == distance to the union of closed
+    triangles computed by projection + edge clamping (different algorithm)."""
+    m = dg.workload(0, n_queries=3000, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    q = m.queries.astype(np.float64)
+    d = o.bruteforce(q)["dist"]
+    ref = closest_on_closed_triangles(m.verts.astype(np.float64), m.tris, q)
+    np.testing.assert_allclose(d, ref, rtol=0, atol=1e-12)
+
+
+def test_bruteforce_dense_sampling():
+    """Dense barycentric sampling of every triangle never beats the oracle
+    and approaches it to within the sampling resolution."""
+    r_ = rng(4)
+    V = r_.normal(size=(9, 3)).astype(np.float32)
+    F = np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8]], np.int32)
+    o = oracle.OracleMesh(V, F, build_tables=False)
+    q = r_.normal(size=(60, 3)) * 1.5
+    d = o.bruteforce(q)["dist"]
+    k = 240
+    i, j = np.meshgrid(np.arange(k + 1), np.arange(k + 1), indexing="ij")
+    ok = (i + j) <= k
+    w1, w2 = (i[ok] / k), (j[ok] / k)
+    Vd = V.astype(np.float64)
+    pts = []
+    for f in F:
+        a, b, c = Vd[f]
+        pts.append(a + w1[:, None] * (b - a) + w2[:, None] * (c - a))
+    pts = np.concatenate(pts)
+    ds = np.sqrt(((q[:, None, :] - pts[None]) ** 2).sum(-1)).min(1)
+    edge = max(np.linalg.norm(Vd[f[0]] - Vd[f[1]]) for f in F) * 2
+    assert (ds >= d - 1e-12).all()
+    assert (ds - d <= edge / k * 1.5).all()
+
+
+def test_closest_point_consistency():
+    """The reported closest point lies at the reported distance and is the
+    barycentric combination of the reported primitive's vertices."""
+    m = dg.workload(0, n_queries=2000, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    r = o.bruteforce(m.queries)
+    q = m.queries.astype(np.float64)
+    np.testing.assert_allclose(np.linalg.norm(q - r["cp"], axis=1), r["dist"], atol=1e-12)
+    Vd = m.verts.astype(np.float64)
+    bv = np.where(r["bv"] < 0, 0, r["bv"])
+    recon = (r["bw"][:, :, None] * Vd[bv]).sum(1)
+    np.testing.assert_allclose(recon, r["cp"], atol=1e-12)
+    np.testing.assert_allclose(r["bw"].sum(1), 1.0, atol=1e-12)
+    assert (r["bw"] >= 0).all()
+    assert (r["second"] >= r["dist"]).all()
+
+
+# --------------------------------------------------------------------------
+# KD tree (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+def test_kdt_nearest_equals_brute_force():
+    r_ = rng(5)
+    V = r_.uniform(-1, 1, size=(3000, 3)).astype(np.float32)
+    F = np.stack([np.arange(0, 3000, 3), np.arange(1, 3000, 3), np.arange(2, 3000, 3)], 1)
+    o = oracle.OracleMesh(V, F.astype(np.int32), build_tables=False)
+    q = r_.uniform(-1.5, 1.5, size=(5000, 3))
+    nn, vis = o.kdt_nn(q)
+    np.testing.assert_array_equal(nn, brute_nn(V, q))
+    assert vis.mean() < 200  # pruning works
+
+
+def test_kdt_ties_go_to_lowest_index():
+    V = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 2], [0, 0, -2]], np.float32)
+    F = np.array([[0, 2, 4], [1, 3, 5]], np.int32)
+    o = oracle.OracleMesh(V, F, build_tables=False)
+    nn, _ = o.kdt_nn(np.zeros((1, 3)))
+    assert nn[0] == 0
+
+
+# --------------------------------------------------------------------------
+# convex polytope cutting (Sec. 4.4 "Implementation") and Voronoi cells
+# --------------------------------------------------------------------------
+
+def _unique_rows(x, tol):
+    out = []
+    for p in x:
+        if not any(np.linalg.norm(p - u) <= tol for u in out):
+            out.append(p)
+    return np.array(out).reshape(-1, 3)
+
+
+def test_clipping_matches_halfspace_enumeration():
+    """Corners of a box cut by random half-spaces == all feasible triple-plane
+    intersections (brute-force vertex enumeration)."""
+    r_ = rng(6)
+    lo, hi = np.array([-1.0, -1, -1]), np.array([1.0, 1, 1])
+    for trial in range(20):
+        k = int(r_.integers(3, 10))
+        nrm = r_.normal(size=(k, 3))
+        nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+        c = r_.uniform(0.2, 0.9, size=k)
+        planes = np.concatenate([nrm, c[:, None]], 1)
+        got = _unique_rows(oracle.clip_box(lo, hi, planes), 1e-9)
+        allp = list(planes)
+        for ax in range(3):
+            for s in (-1, 1):
+                n = np.zeros(3)
+                n[ax] = s
+                allp.append(np.array([*n, 1.0]))
+        allp = np.array(allp)
+        pts = []
+        for i, j, l in itertools.combinations(range(allp.shape[0]), 3):
+            A = allp[[i, j, l], :3]
+            if abs(np.linalg.det(A)) < 1e-12:
+                continue
+            x = np.linalg.solve(A, allp[[i, j, l], 3])
+            if (allp[:, :3] @ x - allp[:, 3] <= 1e-9).all():
+                pts.append(x)
+        ref = _unique_rows(np.array(pts), 1e-9)
+        assert got.shape[0] == ref.shape[0], trial
+        for p in ref:
+            assert np.linalg.norm(got - p, axis=1).min() < 1e-9
+
+
+def test_voronoi_cells_equal_all_bisector_cells():
+    """Cell(v) from k-nearest seeding + corner certification == D cut by the
+    bisectors of ALL other vertices (same volume, same neighbours)."""
+    r_ = rng(7)
+    n = 180
+    V = r_.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    F = np.stack([np.arange(0, n, 3), np.arange(1, n, 3), np.arange(2, n, 3)], 1).astype(np.int32)
+    o = oracle.OracleMesh(V, F, domain_scale=1.5, delta_rel=0.0)
+    Vd = V.astype(np.float64)
+    lo, hi = o.domain_lo, o.domain_hi
+    for v in range(0, n, 9):
+        w = np.array([i for i in range(n) if i != v])
+        nrm = Vd[w] - Vd[v]
+        ln = np.linalg.norm(nrm, axis=1)
+        nrm /= ln[:, None]
+        c = (nrm * (0.5 * (Vd[w] + Vd[v]))).sum(1)
+        corners = oracle.clip_box(lo, hi, np.concatenate([nrm, c[:, None]], 1))
+        vol = ConvexHull(corners).volume
+        assert abs(vol - o.cell_volume(v)) <= 1e-9 * vol
+        # neighbours: bisector planes carrying >= 3 corners of the cell
+        on = np.abs(corners @ nrm.T - c[None, :]) < 1e-9
+        ref = set(w[on.sum(0) >= 3].tolist())
+        assert ref == set(o.cell_neighbors(v).tolist()), v
+    vol_all = sum(o.cell_volume(v) for v in range(n))
+    assert abs(vol_all - np.prod(hi - lo)) < 1e-9 * np.prod(hi - lo)
+
+
+def test_voronoi_volume_sum_workload0():
+    m = dg.workload(0, n_queries=10)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    tot = sum(o.cell_volume(v) for v in range(o.nv))
+    D = np.prod(o.domain_hi - o.domain_lo)
+    assert abs(tot - D) < 1e-9 * D
+
+
+# --------------------------------------------------------------------------
+# interception table: Thm. 2, Thm. 5/6 soundness, Thm. 7 completeness
+# --------------------------------------------------------------------------
+
+def _table_set(o):
+    off, t, i, b = o.table()
+    s = {}
+    for v in range(o.nv):
+        for j in range(off[v], off[v + 1]):
+            s[(v, int(t[j]), int(i[j]))] = b[j]
+    return s
+
+
+@pytest.fixture(scope="module")
+def small_meshes():
+    out = {}
+    m = dg.workload(0, n_queries=10)
+    out["noisy-L3"] = (m.verts, m.tris, m.domain_scale, m.domain_margin)
+    V, F = dg.icosphere(2)
+    out["sphere-L2"] = (V.astype(np.float32), F.astype(np.int32), 1.5, 0.0)
+    V, F = dg.cube()
+    out["cube"] = (V.astype(np.float32), F.astype(np.int32), 3.0, 0.0)
+    V, F = dg.octahedron()
+    out["octahedron"] = (V.astype(np.float32), F.astype(np.int32), 3.0, 0.0)
+    m = dg.workload(2, n_queries=10, grid=24)
+    out["heightfield-24"] = (m.verts, m.tris, m.domain_scale, m.domain_margin)
+    return out
+
+
+@pytest.mark.parametrize("name", ["noisy-L3", "sphere-L2", "cube", "octahedron", "heightfield-24"])
+def test_incident_primitives_are_intercepted(small_meshes, name):
+    """Thm. 2: every vertex intercepts its incident edges and faces."""
+    V, F, s, mg = small_meshes[name]
+    o = oracle.OracleMesh(V, F, s, mg)
+    T = _table_set(o)
+    E = o.edges()
+    for e, (a, b) in enumerate(E):
+        assert (a, oracle.EDGE, e) in T and (b, oracle.EDGE, e) in T
+    for f, tri in enumerate(F):
+        for v in tri:
+            assert (int(v), oracle.FACE, f) in T
+
+
+@pytest.mark.parametrize("name", ["noisy-L3", "sphere-L2", "cube", "octahedron", "heightfield-24"])
+def test_table_complete_by_sampling(small_meshes, name):
+    """Thm. 7 (flooding finds every interceptor), checked empirically: for
+    sampled points of D, the brute-force closest primitive p and nearest
+    vertex v satisfy p in IT[v] (or p = v), and the point lies in the
+    Region box of (v, p) (Sec. 4.6)."""
+    V, F, s, mg = small_meshes[name]
+    o = oracle.OracleMesh(V, F, s, mg)
+    T = _table_set(o)
+    q = rng(8).uniform(o.domain_lo, o.domain_hi, size=(40000, 3))
+    r = o.bruteforce(q)
+    nn = brute_nn(V, q)
+    for i in range(q.shape[0]):
+        t, pid = int(r["ptype"][i]), int(r["pid"][i])
+        if t == oracle.VERTEX:
+            assert pid == nn[i] or abs(r["dist"][i] - np.linalg.norm(q[i] - V[nn[i]])) < 1e-12
+            continue
+        key = (int(nn[i]), t, pid)
+        assert key in T, (name, i, key)
+        b = T[key]
+        assert (q[i] >= b[:3]).all() and (q[i] <= b[3:]).all(), (name, i)
+
+
+def test_table_sound_against_exhaustive_filter():
+    """Thm. 5/6: every flooded pair passes the convexity filter, and the
+    flood never reports a pair that exhaustive inspection of all V x (E+F)
+    pairs rejects."""
+    m = dg.workload(0, n_queries=10, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    T = _table_set(o)
+    exhaustive = set()
+    for v in range(o.nv):
+        for e in range(o.ne):
+            if o.intercepts(v, oracle.EDGE, e)[0]:
+                exhaustive.add((v, oracle.EDGE, e))
+        for f in range(o.nf):
+            if o.intercepts(v, oracle.FACE, f)[0]:
+                exhaustive.add((v, oracle.FACE, f))
+    assert set(T.keys()) <= exhaustive
+    # flooding reaches nearly every filter-accepted pair on this mesh
+    assert len(T) >= 0.9 * len(exhaustive)
+
+
+# --------------------------------------------------------------------------
+# the query (Alg. A.2) equals the plain definition
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["noisy-L3", "sphere-L2", "cube", "octahedron", "heightfield-24"])
+@pytest.mark.parametrize("use_boxes", [False, True])
+def test_query_equals_bruteforce(small_meshes, name, use_boxes):
+    V, F, s, mg = small_meshes[name]
+    o = oracle.OracleMesh(V, F, s, mg)
+    q = rng(9).uniform(o.domain_lo, o.domain_hi, size=(20000, 3)).astype(np.float32)
+    bf = o.bruteforce(q)
+    r = o.query(q, use_boxes=use_boxes)
+    np.testing.assert_array_equal(r["dist"], bf["dist"])
+    np.testing.assert_array_equal(r["ptype"], bf["ptype"])
+    np.testing.assert_array_equal(r["pid"], bf["pid"])
+    # invariant of Alg. A.2: d_min starts at the nearest-vertex distance
+    qd = q.astype(np.float64)
+    dv = np.linalg.norm(qd - V.astype(np.float64)[r["nn"]], axis=1)
+    assert (r["dist"] <= dv).all()
+
+
+@pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 4}), (2, {"grid": 48}),
+                                    (3, {"level": 4})])
+def test_query_equals_bruteforce_workloads(idx, kw):
+    m = dg.workload(idx, n_queries=20000, **kw)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    bf = o.bruteforce(m.queries)
+    for ub in (False, True):
+        r = o.query(m.queries, use_boxes=ub)
+        np.testing.assert_array_equal(r["dist"], bf["dist"])
+        np.testing.assert_array_equal(r["pid"], bf["pid"])
+
+
+# --------------------------------------------------------------------------
+# gradient against central finite differences
+# --------------------------------------------------------------------------
+
+def test_gradient_matches_finite_differences():
+    """dd/dq = (q-c)/d and dd/dv_k = -b_k (q-c)/d against FP64 central
+    differences (h = 1e-6) of the brute-force distance, away from ties and
+    from d = 0."""
+    m = dg.workload(3, n_queries=400, level=3)
+    Vd = m.verts.astype(np.float64)
+    o = oracle.OracleMesh(Vd, m.tris, build_tables=False)
+    q = m.queries.astype(np.float64)
+    r = o.bruteforce(q)
+    keep = (r["second"] - r["dist"] > 1e-4) & (r["dist"] > 1e-4)
+    idx = np.nonzero(keep)[0][:60]
+    h = 1e-6
+    gq, bv, gv = oracle.gradient(q, r)
+    for i in idx:
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            dp = o.bruteforce((q[i] + e)[None])["dist"][0]
+            dm = o.bruteforce((q[i] - e)[None])["dist"][0]
+            assert abs((dp - dm) / (2 * h) - gq[i, k]) < 1e-6
+    for i in idx[:15]:
+        for slot in range(3):
+            v = bv[i, slot]
+            if v < 0:
+                continue
+            for k in range(3):
+                Vp = Vd.copy()
+                Vp[v, k] += h
+                Vm = Vd.copy()
+                Vm[v, k] -= h
+                dp = oracle.OracleMesh(Vp, m.tris, build_tables=False).bruteforce(q[i][None])["dist"][0]
+                dm = oracle.OracleMesh(Vm, m.tris, build_tables=False).bruteforce(q[i][None])["dist"][0]
+                assert abs((dp - dm) / (2 * h) - gv[i, slot, k]) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# robustness of the input checks
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case,msg", [
+    ("index", "index out of range"), ("repeat", "repeated index"),
+    ("dup", "duplicate vertex"), ("unref", "unreferenced vertex"),
+    ("nan", "non-finite"), ("empty", "no triangles")])
+def test_invalid_meshes_rejected(case, msg):
+    V, F = dg.octahedron()
+    V = V.astype(np.float32)
+    F = F.astype(np.int32)
+    if case == "index":
+        F = F.copy(); F[0, 0] = 99
+    elif case == "repeat":
+        F = F.copy(); F[0, 1] = F[0, 0]
+    elif case == "dup":
+        V = np.concatenate([V, V[:1]]); F = np.concatenate([F, [[6, 2, 4]]]).astype(np.int32)
+    elif case == "unref":
+        V = np.concatenate([V, [[5, 5, 5]]]).astype(np.float32)
+    elif case == "nan":
+        V = V.copy(); V[0, 0] = np.nan
+    elif case == "empty":
+        F = np.zeros((0, 3), np.int32)
+    with pytest.raises(ValueError, match=msg):
+        oracle.OracleMesh(V, F)
+
+
+# --------------------------------------------------------------------------
+# statistics the paper reports as ranges (sanity only; parity unpinned:
+# the paper's models are not available)
+# --------------------------------------------------------------------------
+
+def test_statistics_in_paper_ranges():
+    """Sec. 5.1: list lengths mostly 20-100; Sec. 6: about 85 % of the
+    vertices visited by flooding are not interceptors."""
+    m = dg.workload(0, n_queries=10)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    off = o.table()[0]
+    L = np.diff(off)
+    assert 20 <= L.mean() <= 100
+    reject = 1 - o.n_entries / o.n_inspections
+    assert 0.6 <= reject <= 0.95
+
+
+# --------------------------------------------------------------------------
+# ConvexPoly and the Region boxes (Sec. 4.4, 4.6)
+# --------------------------------------------------------------------------
+
+def _in_space_perp(V, F, E, ptype, pid, x, tol):
+    """Membership in Space-perp(p) written from Eq. 4/5 directly: a face's
+    prism (projection inside the triangle), an edge's slab between the
+    endpoint planes and on the far side of every adjacent face."""
+    if ptype == oracle.FACE:
+        a, b, c = V[F[pid]]
+        n = np.cross(b - a, c - a)
+        ok = np.ones(x.shape[0], bool)
+        for p0, p1 in ((a, b), (b, c), (c, a)):
+            inward = np.cross(n, p1 - p0)
+            inward /= np.linalg.norm(inward)
+            ok &= (x - p0) @ inward >= -tol
+        return ok
+    a, b = V[E[pid, 0]], V[E[pid, 1]]
+    u = (b - a) / np.linalg.norm(b - a)
+    s = (x - a) @ u
+    ok = (s >= -tol) & (s <= np.linalg.norm(b - a) + tol)
+    for f in np.nonzero((F == E[pid, 0]).any(1) & (F == E[pid, 1]).any(1))[0]:
+        third = [w for w in F[f] if w not in E[pid]][0]
+        c = V[third]
+        w = (c - a) - ((c - a) @ u) * u       # in-plane direction into the face
+        w /= np.linalg.norm(w)
+        ok &= (x - a) @ w <= tol
+    return ok
+
+
+def test_convexpoly_volume_matches_sampling():
+    """ConvexPoly(v,p) = Cell(v) ∩ Space-perp(p): its volume matches a Monte
+    Carlo estimate whose membership test uses the nearest vertex and the
+    Space-perp definitions directly."""
+    m = dg.workload(0, n_queries=10, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    V = m.verts.astype(np.float64)
+    E = o.edges()
+    r_ = rng(11)
+    off, t, ids, boxes = o.table()
+    checked = 0
+    for j in r_.choice(off[-1], size=40, replace=False):
+        v = int(np.searchsorted(off, j, side="right") - 1)
+        cor = o.convexpoly(v, int(t[j]), int(ids[j]))
+        if cor.shape[0] < 4:
+            continue
+        try:
+            vol = ConvexHull(cor).volume
+        except Exception:
+            continue
+        lo, hi = cor.min(0), cor.max(0)
+        x = r_.uniform(lo, hi, size=(20000, 3))
+        nn = brute_nn(V, x)
+        inside = (nn == v) & _in_space_perp(V, m.tris, E, int(t[j]), int(ids[j]), x, 0.0)
+        est = inside.mean() * np.prod(hi - lo)
+        err = 4 * np.sqrt(max(inside.mean(), 1e-4) / x.shape[0]) * np.prod(hi - lo)
+        assert abs(est - vol) <= err + 1e-3 * vol, (v, t[j], ids[j], est, vol)
+        checked += 1
+    assert checked >= 20
+
+
+def test_region_box_contains_relaxed_region_corners():
+    """The Region box of (v,p) contains every ConvexPoly corner where v is
+    not nearer than the primitive's line or plane (the relaxed Bisect^e side
+    of Thm. 5/6), with the delta padding on every side."""
+    m = dg.workload(0, n_queries=10, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    V = m.verts.astype(np.float64)
+    E = o.edges()
+    diag = np.linalg.norm(o.domain_hi - o.domain_lo)
+    eta = 2 * o.delta * diag + o.delta ** 2
+    off, t, ids, boxes = o.table()
+    n_seen = 0
+    for j in range(0, off[-1], 7):
+        v = int(np.searchsorted(off, j, side="right") - 1)
+        cor = o.convexpoly(v, int(t[j]), int(ids[j]))
+        if t[j] == oracle.EDGE:
+            a, b = V[E[ids[j]]]
+            u = (b - a) / np.linalg.norm(b - a)
+            w = cor - a
+            dist2 = (w * w).sum(1) - (w @ u) ** 2
+        else:
+            a, b, c = V[m.tris[ids[j]]]
+            n = np.cross(b - a, c - a)
+            n /= np.linalg.norm(n)
+            dist2 = ((cor - a) @ n) ** 2
+        g = ((cor - V[v]) ** 2).sum(1) - dist2 + eta
+        sel = cor[g > 0]
+        if sel.size == 0:
+            continue
+        bx = boxes[j]
+        assert (sel >= bx[:3] + 0.5 * o.delta).all() and (sel <= bx[3:] - 0.5 * o.delta).all()
+        n_seen += 1
+    assert n_seen > 100
