@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the point-to-mesh query stage on GB300.
+
+One step = one pass of the whole query path (Morton bucket sort, KD-tree
+nearest vertex, interception-list scan with Region-box filter, edge/face
+tests, minimum, outputs in caller order) over the 10M uniform queries of the
+1.3M-triangle displaced icosphere.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (the plain brute-force definition of
+the distance, all host cores) on a bounded sample of the same workload.
+For N > 1 (torchrun) every rank runs an independent replica (the query path
+has no exchange step): value = all ranks' queries / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen as dg  # noqa: E402
+
+METRIC = "point-to-mesh queries/sec (1.3M tris)"
+UNIT = "queries/s"
+WORKLOAD = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1024,
+                    help="queries of the bounded CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--level", type=int, default=None, help="smaller mesh (profiling only)")
+    ap.add_argument("--queries", type=int, default=None, help="fewer queries (profiling only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    return dg.workload(WORKLOAD, n_queries=args.queries, level=args.level)
+
+
+def config_of(m, args, extra=None):
+    c = {"workload": m.name, "mesh": "icosphere subdivided 8x, radial displacement 0.2",
+         "n_tris": int(m.tris.shape[0]), "n_verts": int(m.verts.shape[0]),
+         "n_queries_per_gpu": int(m.queries.shape[0]),
+         "query_distribution": "uniform in bbox scaled 1.5x",
+         "domain": f"bbox x{m.domain_scale} + {m.domain_margin} diag"}
+    if args.level is not None or args.queries is not None:
+        c["reduced"] = True
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------- oracle arm
+
+def oracle_sample(m, k):
+    idx = np.linspace(0, m.queries.shape[0] - 1, k).astype(np.int64)
+    return idx
+
+
+def time_oracle(m, n_sample, threads):
+    import oracle
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False, threads=threads)
+    q = m.queries[oracle_sample(m, n_sample)]
+    t0 = time.perf_counter()
+    o.bruteforce(q, threads=threads)
+    return time.perf_counter() - t0, o
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    m = workload(args)
+    threads = os.cpu_count() or 1
+    import oracle
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False, threads=threads)
+    per = max(16, args.cpu_sample // 8)
+    idx = oracle_sample(m, per * (args.steps + args.warmup))
+    for s in range(args.warmup):
+        o.bruteforce(m.queries[idx[s * per:(s + 1) * per]], threads=threads)
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        o.bruteforce(m.queries[idx[s * per:(s + 1) * per]], threads=threads)
+    dt = time.perf_counter() - t0
+    v = per * args.steps / dt
+    sample = (f"{per} queries per step, evenly strided over the {m.queries.shape[0]} queries; "
+              "FP64 brute force over all vertices, open edges and open faces")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config_of(m, args, {"parallelism": f"{threads} host threads"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (read only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm
+
+def kernel_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2308_16084_gb300", "csrc", "kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_queries):
+    """DRAM bytes per query-kernel launch from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_query_dram.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_sha") != kernel_hash() or not d.get("dram_bytes_per_query"):
+        return None
+    return d["dram_bytes_per_query"] * n_queries
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def bytes_per_query(c, n):
+    """Algorithmic bytes one query touches (record sizes of the layout):
+    query 12 B, outputs 21 B (dist, closest, id, type), 48 B per internal
+    KD node (two child boxes), 16 B per vertex examined, 8 B CSR range,
+    28 B per list entry scanned (Region box + typed id), 32 B per edge and
+    48 B per face tested."""
+    per = (12 + 21 + 8) * n + 48 * c["nodes"] + 16 * c["points"] + 28 * c["entries"] + \
+        32 * c["edges"] + 48 * c["faces"]
+    return per / n
+
+
+def run_ours(args):
+    import torch
+    import paper_2308_16084_gb300 as pg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    m = workload(args)
+    n = m.queries.shape[0]
+
+    # build once (rank 0), share the layout file with the other replicas
+    t0 = time.perf_counter()
+    layout = os.path.join("/tmp", f"p2m_bench_{os.getpid() if world == 1 else 'shared'}.p2m")
+    if rank == 0:
+        mesh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
+        if world > 1:
+            mesh.save(layout)
+    if world > 1:
+        dist.barrier()
+        if rank != 0:
+            mesh = pg.P2M.load(layout)
+        dist.barrier()
+    build_s = time.perf_counter() - t0
+    st = mesh.stats()
+
+    q = torch.from_numpy(m.queries).cuda()
+    out = {"dist": torch.empty(n, device="cuda"),
+           "prim_id": torch.empty(n, dtype=torch.int32, device="cuda"),
+           "closest": torch.empty(n, 3, device="cuda"),
+           "prim_type": torch.empty(n, dtype=torch.uint8, device="cuda")}
+    mesh.reserve(n)
+    tuned_ms = None
+    if not args.no_autotune:
+        tuned_ms = mesh.autotune(q, reps=2)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        mesh.query(q, out=out)
+    torch.cuda.synchronize()
+
+    # device-resident timed region
+    mesh.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mesh.query(q, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    calls, sort_ms, kern_ms = mesh.timing_summary()
+    mesh.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * args.steps * world / (ms / 1e3)
+
+    # end to end through the host API: pinned host buffers, copies in the timed region
+    qh = torch.from_numpy(m.queries).pin_memory()
+    dh = torch.empty(n, dtype=torch.float32).pin_memory()
+    ph = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        mesh.query_host(qh, dh, ph)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mesh.query_host(qh, dh, ph)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": n * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 8 * n}
+
+    # roofline of the dominant kernel (the fused query kernel)
+    cnt = mesh.counters(q)
+    bpq = bytes_per_query(cnt, n)
+    kern_avg_s = kern_ms / max(1, calls) / 1e3
+    peak, src = peaks()
+    achieved = bpq * n / kern_avg_s / 1e9
+    traffic = measured_traffic(n)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
+            else "fallback 6.8 TB/s",
+            "kernel": "k_query", "kernel_ms": kern_avg_s * 1e3,
+            "sort_ms": sort_ms / max(1, calls), "bytes_per_query": bpq,
+            "work_per_query": {k: v / n for k, v in cnt.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        dt, _ = time_oracle(m, args.cpu_sample, threads)
+        cpu = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_sample} of the {n} queries (evenly strided), FP64 brute "
+                         "force over all vertices, open edges and open faces"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": config_of(m, args, {
+                "parallelism": "replicas only" if world > 1 else "single GPU",
+                "l2": f"inputs larger than L2: layout {st['device_bytes'] / 1e9:.2f} GB + "
+                      f"queries {12 * n / 1e6:.0f} MB per step",
+                "tuning": mesh.tuning, "autotune_ms": tuned_ms, "build_s": round(build_s, 1),
+                "table_entries": st["n_entries"], "max_list": st["max_list"]}),
+            "clocks": clk, "e2e": e2e, "gpu_launches": 4 * args.steps,
+            "roofline": roof, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0 and world > 1:
+        try:
+            os.remove(layout)
+        except OSError:
+            pass
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,263 @@
+/*
+ * p2m.h -- C ABI of the GB300 point-to-mesh query library (libp2m.so).
+ *
+ * The library answers, for every query point q, the closest point on a
+ * triangle mesh, the distance to it and the closest primitive (vertex, open
+ * edge or open face), following the query stage of P2M (Zong et al., "P2M:
+ * A Fast Solver for Querying Distance from Point to Mesh Surface", ACM TOG
+ * 2023; query = Alg. A.2, preprocessing = Alg. A.1).
+ *
+ * Conventions shared by every entry point
+ *   - Plain pointers and sizes only.  "host" pointers are CPU memory,
+ *     "device" pointers are CUDA global memory on the current device.
+ *   - The caller owns every buffer it passes; the library never frees or
+ *     keeps a caller pointer beyond the call.  A handle owns its device
+ *     layout and a scratch arena, both released by p2m_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it and the call returns without
+ *     synchronising, unless stated otherwise.
+ *   - Coordinates are float32, xyz interleaved; triangle indices int32.
+ *   - Every call returns a p2m_status.  Per-query conditions (non-finite
+ *     input, point outside the domain) are reported in the optional status
+ *     array, never through the return code.  No call traps the GPU.
+ *   - Edge ids follow the canonical order: unique (min,max) vertex pairs
+ *     sorted lexicographically (p2m_get_edges exports them).
+ */
+#ifndef P2M_H
+#define P2M_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  P2M_OK = 0,
+  P2M_ERR_INVALID_ARG = 1,      /* NULL pointer, negative size, unknown option        */
+  P2M_ERR_INVALID_MESH = 2,     /* index out of range, repeated index in a triangle,
+                                   unreferenced vertex, non-finite coordinate, no faces */
+  P2M_ERR_DUPLICATE_VERTEX = 3, /* two vertices at one position (Voronoi cells would
+                                   be undefined; the paper assumes one copy per vertex,
+                                   Sec. 4.1)                                            */
+  P2M_ERR_OOM = 4,              /* host or device allocation failed                    */
+  P2M_ERR_CUDA = 5,             /* a CUDA runtime call failed                          */
+  P2M_ERR_QUEUE_TIMEOUT = 6,    /* the batched work queue gave up after its bounded wait */
+  P2M_ERR_IO = 7,               /* file missing, short, corrupt or wrong version       */
+  P2M_ERR_NO_DEVICE = 8,        /* no usable CUDA device                               */
+  P2M_ERR_TOO_LARGE = 9         /* a size exceeds a documented limit                   */
+} p2m_status;
+
+/* primitive types; distance ties go to the lower value, then the lower id */
+typedef enum { P2M_PRIM_VERTEX = 0, P2M_PRIM_EDGE = 1, P2M_PRIM_FACE = 2 } p2m_prim_type;
+
+/* per-query status bits written to the optional status array */
+enum {
+  P2M_Q_OUTSIDE_DOMAIN = 1, /* q outside the domain D: answered, exactness not guaranteed */
+  P2M_Q_NONFINITE = 2       /* q has a NaN/inf coordinate: outputs are NaN / -1       */
+};
+
+/* A triangle mesh with one shared copy per vertex (Sec. 4.1).  Host memory. */
+typedef struct {
+  const float *verts;   /* n_verts * 3 */
+  int64_t n_verts;
+  const int32_t *tris;  /* n_tris * 3 */
+  int64_t n_tris;
+} p2m_mesh;
+
+/* Build options.  Pass NULL to p2m_build for the defaults. */
+typedef struct {
+  float domain_scale;  /* query domain D = bbox scaled about its centre by this factor
+                          (default 10: the paper samples queries in 10x the bbox, Sec. 5) */
+  float domain_margin; /* plus this fraction of the bbox diagonal on every side (default 0) */
+  float delta_rel;     /* conservative widening of cells, Space-perp half-spaces, filter
+                          and Region boxes, as a fraction of diag(D) (default 4e-6)        */
+  int host_threads;    /* preprocessing threads, 0 = all cores (default 0)                 */
+  int device_assist;   /* 1 = certify Voronoi cells with the GPU nearest-vertex kernel,
+                          0 = CPU only (default 1; 0 works without a GPU for the tables)   */
+  int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
+} p2m_build_opts;
+
+/* Fill *opts with the defaults. */
+void p2m_default_opts(p2m_build_opts *opts);
+
+typedef struct p2m_handle p2m_handle;
+
+/*
+ * Preprocess a mesh (Alg. A.1) and upload the query layout to the current
+ * CUDA device: KD tree of V, Voronoi cells of V clipped to D, flooding
+ * interception inspection (Alg. 1) with the convexity filter (Thm. 5/6),
+ * Region bounding boxes (Sec. 4.6), packed as a CSR interception table.
+ * The mesh is copied; `mesh` may be freed after the call.  Synchronous.
+ * Errors: INVALID_ARG, INVALID_MESH, DUPLICATE_VERTEX, OOM, CUDA, NO_DEVICE.
+ */
+p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out);
+
+/* Release the handle and all device memory it owns (NULL is a no-op). */
+void p2m_destroy(p2m_handle *h);
+
+/*
+ * Closest point query (Alg. A.2) for n points, on `stream`.
+ *   q            device, n*3 float   query points
+ *   dist         device, n float     distance to the mesh
+ *   closest      device, n*3 float   closest point (may be NULL)
+ *   prim_id      device, n int32     vertex / edge / face id of the closest primitive
+ *   prim_type    device, n uint8     p2m_prim_type (may be NULL)
+ *   save         device, n*4 float   what p2m_backward needs: {typed id bits, w0, w1, w2}
+ *                                    (barycentric weights of the closest point), or NULL
+ *   status       device, n uint8     P2M_Q_* bits, or NULL
+ * Outputs are in the caller's order.  Queries are Morton-sorted internally
+ * (scratch owned by the handle; grown on demand, see p2m_reserve).
+ * n == 0 is a no-op.  Errors: INVALID_ARG, OOM, CUDA, TOO_LARGE (n >= 2^31).
+ */
+p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
+                     int32_t *prim_id, uint8_t *prim_type, float *save, uint8_t *status,
+                     void *stream);
+
+/* Same as p2m_query with HOST buffers: copies q in, runs, copies results out,
+ * synchronises `stream` before returning (dist/prim_id required, others may
+ * be NULL). */
+p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
+                          int32_t *prim_id, uint8_t *prim_type, void *stream);
+
+/* Launch tuning of the query path (chosen by the autotuner or by hand).
+ *   sort_bits      Morton bucket bits of the query sort, 0..24 (0 = no sort);
+ *                  queries are grouped into 2^sort_bits spatial buckets
+ *   block_threads  threads per CTA of the query kernel: 64, 128, 256 or 512 */
+typedef struct {
+  int sort_bits;
+  int block_threads;
+} p2m_tuning;
+p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
+p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
+
+/* Instrumentation.  While timing is enabled, every p2m_query brackets its
+ * sort and its query kernel with CUDA events on the caller's stream (a ring
+ * of the last 1024 calls; no host synchronisation).  p2m_timing_summary
+ * waits for the calls recorded since its previous call and returns
+ * {calls, total sort ms, total query-kernel ms}.  Enabling (or disabling)
+ * clears the ring. */
+p2m_status p2m_set_timing(p2m_handle *h, int enable);
+p2m_status p2m_timing_summary(p2m_handle *h, double out[3]);
+
+/* Work counters of a query batch (device q, n points): runs a counting
+ * variant of the query kernel (outputs are not written) and returns the
+ * totals of KD-tree internal nodes visited, vertices examined, list entries
+ * scanned, edges tested and faces tested in out[0..4].  Synchronous. */
+p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[5],
+                              void *stream);
+
+/* Pre-size the handle's scratch arena for queries of up to n points, so that
+ * later p2m_query calls with n or fewer points allocate nothing (needed
+ * before capturing p2m_query into a CUDA graph). */
+p2m_status p2m_reserve(p2m_handle *h, int64_t n);
+
+/*
+ * Backward pass of d(q) = |q - c(q)| for n queries, on `stream`.  With
+ * u = (q - c)/d: grad_q = grad_dist * u, and for the vertices v_k of the
+ * closest primitive with barycentric weights w_k (from `save`):
+ * grad_verts[v_k] -= grad_dist * w_k * u  (accumulated with atomics, so the
+ * caller zeroes grad_verts first if it wants a fresh gradient).  Queries
+ * with d == 0 contribute nothing.
+ *   q, dist, closest, save: device, as produced by p2m_query
+ *   grad_dist    device, n float
+ *   grad_q       device, n*3 float or NULL
+ *   grad_verts   device, n_verts*3 float or NULL
+ * Errors: INVALID_ARG, CUDA.
+ */
+p2m_status p2m_backward(p2m_handle *h, const float *q, const float *dist, const float *closest,
+                        const float *save, const float *grad_dist, int64_t n, float *grad_q,
+                        float *grad_verts, void *stream);
+
+/* One mesh's slice of a batched query (device pointers, n points). */
+typedef struct {
+  const float *q;     /* n*3 */
+  int64_t n;
+  float *dist;        /* n */
+  float *closest;     /* n*3, may be NULL */
+  int32_t *prim_id;   /* n */
+  uint8_t *prim_type; /* n, may be NULL */
+} p2m_batch_io;
+
+/* Tuning of a batched run.
+ *   sort_bits  Morton bucket bits per mesh, 0..16 (all meshes share one sort
+ *              keyed by (mesh, bucket))
+ *   tile       queries per work-queue item, a multiple of block_threads
+ *   block_threads, grid_ctas  persistent launch shape (grid_ctas 0 = one
+ *              wave: SM count x resident CTAs per SM) */
+typedef struct {
+  int sort_bits;
+  int tile;
+  int block_threads;
+  int grid_ctas;
+} p2m_batch_tuning;
+
+typedef struct p2m_batch p2m_batch;
+
+/*
+ * Many meshes in one persistent launch (the paper has no batched mode).
+ * p2m_batch_create checks the slices, allocates the batch's scratch and
+ * uploads the mesh descriptors (synchronous; allocates).  p2m_batch_run then
+ * enqueues, on `stream`: one Morton sort of all queries keyed by (mesh,
+ * bucket), and one persistent query kernel whose CTAs take tiles of the
+ * sorted queries from a device work queue (a single atomic counter, so no
+ * CTA ever waits on another).  p2m_batch_run allocates nothing and does not
+ * synchronise, so it can be captured into a CUDA graph.  The handles and
+ * the io buffers must stay alive while the batch is used.
+ * Errors: INVALID_ARG, OOM, CUDA, TOO_LARGE (total queries >= 2^31),
+ * QUEUE_TIMEOUT (p2m_batch_check: the device reported a malformed item).
+ */
+p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, int n_meshes,
+                            p2m_batch **out);
+p2m_status p2m_batch_run(p2m_batch *b, void *stream);
+p2m_status p2m_batch_get_tuning(const p2m_batch *b, p2m_batch_tuning *t);
+p2m_status p2m_batch_set_tuning(p2m_batch *b, const p2m_batch_tuning *t);
+/* Times every candidate tuning on `stream` (each run `reps` times after one
+ * warm-up) and keeps the fastest; *best_ms receives its time. */
+p2m_status p2m_batch_autotune(p2m_batch *b, int reps, void *stream, float *best_ms);
+/* Synchronises `stream` and reads the device error word of the last runs. */
+p2m_status p2m_batch_check(p2m_batch *b, void *stream);
+void p2m_batch_destroy(p2m_batch *b);
+
+/* Convenience: create, run, check and destroy (synchronous). */
+p2m_status p2m_query_batched(p2m_handle *const *meshes, const p2m_batch_io *io, int n_meshes,
+                             void *stream);
+
+/* Times the single-mesh query for every candidate p2m_tuning on the given
+ * device queries (reps runs each after a warm-up) and keeps the fastest. */
+p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void *stream,
+                        float *best_ms);
+
+/* Export the canonical edge list (host, n_edges*2).  *n_edges receives the
+ * count; pass edges == NULL to query the count only. */
+p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges);
+
+/* Statistics of the built layout: out[0..15] = n_verts, n_tris, n_edges,
+ * table entries, max list length, device bytes, KD-tree leaves, KD-tree
+ * depth, voronoi neighbour pairs, flooding inspections, build ms total,
+ * cells ms, inspection ms, certification rounds, certification queries,
+ * degenerate faces. */
+p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]);
+
+/* The domain D (lo xyz, hi xyz) and delta of a handle. */
+p2m_status p2m_domain(const p2m_handle *h, float out[7]);
+
+/* Interception list of a vertex (original id), host output: types[] and
+ * ids[] of up to cap entries, Region boxes box[6*] (lo, hi) or NULL.
+ * Returns the list length in *len. */
+p2m_status p2m_get_list(const p2m_handle *h, int32_t vertex, int32_t *types, int32_t *ids,
+                        float *boxes, int64_t cap, int64_t *len);
+
+/* Serialise the built layout to a file (versioned header + checksum) and
+ * load it back onto the current device.  Errors: IO, OOM, CUDA. */
+p2m_status p2m_save(const p2m_handle *h, const char *path);
+p2m_status p2m_load(const char *path, p2m_handle **out);
+
+/* Human-readable name of a status code (static string). */
+const char *p2m_status_string(p2m_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P2M_H */

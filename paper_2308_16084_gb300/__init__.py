@@ -1,0 +1,342 @@
+"""GB300 point-to-mesh distance queries (query stage of P2M, Zong et al.,
+ACM TOG 2023) behind the C ABI of ``libp2m.so`` (include/p2m.h).
+
+This module only marshals arguments: every step of the query runs in the
+library's CUDA kernels, and the preprocessing in its host builder.  PyTorch
+supplies device memory and streams.  There is no fallback: if the library is
+missing, importing this package raises ``ImportError``; on a machine without
+a GPU, handles can still be built (tables only) but queries raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._lib import LIB_PATH, P2MError, check, lib  # noqa: F401
+
+VERTEX, EDGE, FACE = 0, 1, 2
+Q_OUTSIDE_DOMAIN, Q_NONFINITE = 1, 2
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("domain_scale", ctypes.c_float), ("domain_margin", ctypes.c_float),
+                ("delta_rel", ctypes.c_float), ("host_threads", ctypes.c_int),
+                ("device_assist", ctypes.c_int), ("leaf_size", ctypes.c_int)]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int64),
+                ("tris", ctypes.c_void_p), ("n_tris", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int)]
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_void_p), ("n", ctypes.c_int64), ("dist", ctypes.c_void_p),
+                ("closest", ctypes.c_void_p), ("prim_id", ctypes.c_void_p),
+                ("prim_type", ctypes.c_void_p)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("sort_bits", ctypes.c_int), ("tile", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int)]
+
+
+def _stream(stream=None):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(None)  # the library reports the missing device
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class P2M:
+    """A preprocessed mesh on the current CUDA device.
+
+    ``P2M(verts, tris, domain_scale=10, domain_margin=0, delta_rel=4e-6,
+    host_threads=0, device_assist=True, leaf_size=8)`` runs the paper's
+    preprocessing (Alg. A.1) through ``p2m_build``.  ``verts`` (V,3) float32
+    and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors."""
+
+    def __init__(self, verts=None, tris=None, *, domain_scale=10.0, domain_margin=0.0,
+                 delta_rel=4e-6, host_threads=0, device_assist=True, leaf_size=8, _handle=None):
+        self._h = None
+        if _handle is not None:
+            self._h = _handle
+        else:
+            V = np.ascontiguousarray(np.asarray(verts, dtype=np.float32).reshape(-1, 3))
+            F = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+            desc = MeshDesc(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
+            opts = BuildOpts(domain_scale, domain_margin, delta_rel, host_threads,
+                             int(bool(device_assist)), leaf_size)
+            h = ctypes.c_void_p()
+            check(lib.p2m_build(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
+                  "p2m_build")
+            self._h = h
+        st = self.stats()
+        self.n_verts, self.n_tris, self.n_edges = st["n_verts"], st["n_tris"], st["n_edges"]
+
+    @classmethod
+    def load(cls, path):
+        h = ctypes.c_void_p()
+        check(lib.p2m_load(os.fsencode(path), ctypes.byref(h)), "p2m_load")
+        return cls(_handle=h)
+
+    def save(self, path):
+        check(lib.p2m_save(self._h, os.fsencode(path)), "p2m_save")
+
+    def close(self):
+        if self._h:
+            lib.p2m_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- info
+    def stats(self):
+        out = (ctypes.c_int64 * 16)()
+        check(lib.p2m_stats(self._h, out), "p2m_stats")
+        keys = ["n_verts", "n_tris", "n_edges", "n_entries", "max_list", "device_bytes",
+                "kd_leaves", "kd_depth", "neighbour_pairs", "inspections", "build_ms",
+                "cells_ms", "inspect_ms", "cert_rounds", "cert_queries", "n_degenerate"]
+        return dict(zip(keys, list(out)))
+
+    def domain(self):
+        out = (ctypes.c_float * 7)()
+        check(lib.p2m_domain(self._h, out), "p2m_domain")
+        return np.array(out[:3]), np.array(out[3:6]), float(out[6])
+
+    def edges(self):
+        n = ctypes.c_int64()
+        check(lib.p2m_get_edges(self._h, None, ctypes.byref(n)), "p2m_get_edges")
+        E = np.zeros((n.value, 2), np.int32)
+        check(lib.p2m_get_edges(self._h, E.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
+              "p2m_get_edges")
+        return E
+
+    def interception_list(self, v):
+        """(types, ids, boxes) of vertex v's interception list."""
+        n = ctypes.c_int64()
+        check(lib.p2m_get_list(self._h, int(v), None, None, None, 0, ctypes.byref(n)),
+              "p2m_get_list")
+        t = np.zeros(n.value, np.int32)
+        i = np.zeros(n.value, np.int32)
+        b = np.zeros((n.value, 6), np.float32)
+        check(lib.p2m_get_list(self._h, int(v), t.ctypes.data_as(ctypes.c_void_p),
+                               i.ctypes.data_as(ctypes.c_void_p),
+                               b.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)),
+              "p2m_get_list")
+        return t, i, b
+
+    # --------------------------------------------------------------- tuning
+    @property
+    def tuning(self):
+        t = Tuning()
+        check(lib.p2m_get_tuning(self._h, ctypes.byref(t)), "p2m_get_tuning")
+        return {"sort_bits": t.sort_bits, "block_threads": t.block_threads}
+
+    @tuning.setter
+    def tuning(self, d):
+        cur = self.tuning
+        cur.update(d)
+        t = Tuning(cur["sort_bits"], cur["block_threads"])
+        check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
+
+    def autotune(self, q, reps=3, stream=None):
+        ms = ctypes.c_float()
+        check(lib.p2m_autotune(self._h, _ptr(q), q.shape[0], reps, _stream(stream),
+                               ctypes.byref(ms)), "p2m_autotune")
+        return ms.value
+
+    def set_timing(self, enable=True):
+        check(lib.p2m_set_timing(self._h, int(bool(enable))), "p2m_set_timing")
+
+    def timing_summary(self):
+        """(calls, total sort ms, total query-kernel ms) of the queries made
+        since the previous summary (timing enabled)."""
+        out = (ctypes.c_double * 3)()
+        check(lib.p2m_timing_summary(self._h, out), "p2m_timing_summary")
+        return int(out[0]), float(out[1]), float(out[2])
+
+    def counters(self, q, stream=None):
+        """Work totals of a query batch: internal KD nodes visited, vertices
+        examined, list entries scanned, edges tested, faces tested."""
+        out = (ctypes.c_int64 * 5)()
+        check(lib.p2m_query_counters(self._h, _ptr(q), q.shape[0], out, _stream(stream)),
+              "p2m_query_counters")
+        return dict(zip(["nodes", "points", "entries", "edges", "faces"], list(out)))
+
+    def reserve(self, n):
+        check(lib.p2m_reserve(self._h, int(n)), "p2m_reserve")
+
+    # ---------------------------------------------------------------- query
+    def query(self, q, *, closest=True, prim_type=True, save=False, status=False,
+              out=None, stream=None):
+        """Closest-point query of a (N,3) float32 CUDA tensor.  Returns a dict
+        of CUDA tensors: dist, prim_id and optionally closest, prim_type,
+        save (N,4: typed id bits + barycentric weights), status."""
+        import torch
+        assert q.is_cuda and q.dtype == torch.float32 and q.is_contiguous()
+        n = q.shape[0]
+        dev = q.device
+        r = out if out is not None else {}
+        if "dist" not in r:
+            r["dist"] = torch.empty(n, dtype=torch.float32, device=dev)
+            r["prim_id"] = torch.empty(n, dtype=torch.int32, device=dev)
+            if closest:
+                r["closest"] = torch.empty(n, 3, dtype=torch.float32, device=dev)
+            if prim_type:
+                r["prim_type"] = torch.empty(n, dtype=torch.uint8, device=dev)
+            if save:
+                r["save"] = torch.empty(n, 4, dtype=torch.float32, device=dev)
+            if status:
+                r["status"] = torch.empty(n, dtype=torch.uint8, device=dev)
+        check(lib.p2m_query(self._h, _ptr(q), n, _ptr(r["dist"]), _ptr(r.get("closest")),
+                            _ptr(r["prim_id"]), _ptr(r.get("prim_type")), _ptr(r.get("save")),
+                            _ptr(r.get("status")), _stream(stream)), "p2m_query")
+        return r
+
+    def query_host(self, q, dist, prim_id, closest=None, prim_type=None, stream=None):
+        """End-to-end query on HOST buffers (numpy or pinned CPU tensors):
+        copies in, queries, copies out, synchronises."""
+        def p(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+        check(lib.p2m_query_host(self._h, p(q), int(q.shape[0]), p(dist), p(closest),
+                                 p(prim_id), p(prim_type), _stream(stream)), "p2m_query_host")
+
+    def backward(self, q, res, grad_dist, grad_q=True, grad_verts=None, stream=None):
+        """Gradients of sum(grad_dist * dist): returns (grad_q, grad_verts);
+        grad_verts is accumulated into the given (V,3) tensor if passed."""
+        import torch
+        n = q.shape[0]
+        gq = torch.empty(n, 3, dtype=torch.float32, device=q.device) if grad_q else None
+        check(lib.p2m_backward(self._h, _ptr(q), _ptr(res["dist"]), _ptr(res["closest"]),
+                               _ptr(res["save"]), _ptr(grad_dist), n, _ptr(gq), _ptr(grad_verts),
+                               _stream(stream)), "p2m_backward")
+        return gq, grad_verts
+
+
+def _torch_autograd():
+    import torch
+
+    class P2MFunction(torch.autograd.Function):
+        """d = dist(q, mesh) with gradients to the query points and to the
+        vertex positions.  The forward saves only (typed primitive id,
+        barycentric weights), the closest points and the distances; the
+        backward kernel recomputes nothing of the query."""
+
+        @staticmethod
+        def forward(ctx, q, verts, mesh):
+            r = mesh.query(q.contiguous(), closest=True, prim_type=False, save=True)
+            ctx.mesh = mesh
+            ctx.n_verts = verts.shape[0]
+            ctx.save_for_backward(q, r["dist"], r["closest"], r["save"])
+            ctx.mark_non_differentiable(r["prim_id"])
+            return r["dist"], r["prim_id"]
+
+        @staticmethod
+        def backward(ctx, gdist, _gid):
+            q, dist, cp, save = ctx.saved_tensors
+            gv = None
+            if ctx.needs_input_grad[1]:
+                gv = torch.zeros(ctx.n_verts, 3, dtype=torch.float32, device=q.device)
+            gq, gv = ctx.mesh.backward(q, {"dist": dist, "closest": cp, "save": save},
+                                       gdist.contiguous(), grad_q=ctx.needs_input_grad[0],
+                                       grad_verts=gv)
+            return gq, gv, None
+
+    return P2MFunction
+
+
+_autograd_cls = None
+
+
+def distance(q, verts, mesh):
+    """Differentiable point-to-mesh distance: returns (dist, prim_id)."""
+    global _autograd_cls
+    if _autograd_cls is None:
+        _autograd_cls = _torch_autograd()
+    return _autograd_cls.apply(q, verts, mesh)
+
+
+class P2MBatch:
+    """Many meshes and their query sets in one persistent launch."""
+
+    def __init__(self, meshes, queries, closest=False, prim_type=False):
+        import torch
+        self.meshes = list(meshes)
+        self.queries = list(queries)
+        self.out = []
+        ios = (BatchIO * len(self.meshes))()
+        for k, (m, q) in enumerate(zip(self.meshes, self.queries)):
+            n = q.shape[0]
+            r = {"dist": torch.empty(n, dtype=torch.float32, device=q.device),
+                 "prim_id": torch.empty(n, dtype=torch.int32, device=q.device)}
+            if closest:
+                r["closest"] = torch.empty(n, 3, dtype=torch.float32, device=q.device)
+            if prim_type:
+                r["prim_type"] = torch.empty(n, dtype=torch.uint8, device=q.device)
+            self.out.append(r)
+            ios[k] = BatchIO(q.data_ptr(), n, r["dist"].data_ptr(),
+                             r["closest"].data_ptr() if closest else None,
+                             r["prim_id"].data_ptr(),
+                             r["prim_type"].data_ptr() if prim_type else None)
+        hs = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        b = ctypes.c_void_p()
+        check(lib.p2m_batch_create(hs, ios, len(self.meshes), ctypes.byref(b)), "p2m_batch_create")
+        self._b = b
+
+    def run(self, stream=None):
+        check(lib.p2m_batch_run(self._b, _stream(stream)), "p2m_batch_run")
+        return self.out
+
+    def check(self, stream=None):
+        check(lib.p2m_batch_check(self._b, _stream(stream)), "p2m_batch_check")
+
+    def autotune(self, reps=3, stream=None):
+        ms = ctypes.c_float()
+        check(lib.p2m_batch_autotune(self._b, reps, _stream(stream), ctypes.byref(ms)),
+              "p2m_batch_autotune")
+        return ms.value
+
+    @property
+    def tuning(self):
+        t = BatchTuning()
+        check(lib.p2m_batch_get_tuning(self._b, ctypes.byref(t)), "p2m_batch_get_tuning")
+        return {"sort_bits": t.sort_bits, "tile": t.tile, "block_threads": t.block_threads,
+                "grid_ctas": t.grid_ctas}
+
+    @tuning.setter
+    def tuning(self, d):
+        cur = self.tuning
+        cur.update(d)
+        t = BatchTuning(cur["sort_bits"], cur["tile"], cur["block_threads"], cur["grid_ctas"])
+        check(lib.p2m_batch_set_tuning(self._b, ctypes.byref(t)), "p2m_batch_set_tuning")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib.p2m_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

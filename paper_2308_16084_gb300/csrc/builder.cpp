@@ -1,0 +1,1002 @@
+// builder.cpp -- host preprocessing of the P2M query layout (Alg. A.1).
+//
+//   topology -> KD tree of V -> Voronoi cells of V clipped to D (k-nearest
+//   seeding, then rounds of corner certification) -> flooding interception
+//   inspection per edge and face (Alg. 1) with the convexity filter of
+//   Thm. 5/6 -> Region boxes (Sec. 4.6) -> packed float32 layout.
+//
+// Every approximation errs toward a larger table: cells, Space-perp
+// half-spaces and Region boxes are widened by delta, and the filter keeps a
+// pair when |x-v|^2 - Dist(x)^2 + eta > 0 at some corner x of ConvexPoly,
+// eta = 2 delta diag(D) + delta^2.  A float32 query that a rounding error
+// puts just outside the exact cell of its nearest vertex therefore still
+// finds its primitive in the list of the vertex the kernel picks.
+#include "builder.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <thread>
+
+namespace p2m {
+namespace {
+
+// ---------------------------------------------------------------- vectors
+struct V3 {
+  double x, y, z;
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double len2(V3 a) { return dot(a, a); }
+inline bool lex_less(V3 a, V3 b) {
+  if (a.x != b.x) return a.x < b.x;
+  if (a.y != b.y) return a.y < b.y;
+  return a.z < b.z;
+}
+
+// half-space n.x <= c, with the id of whatever generated it
+struct Plane {
+  V3 n;
+  double c;
+  int32_t src;
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, int64_t chunk, F &&fn) {
+  if (threads <= 1 || n <= chunk) {
+    for (int64_t i = 0; i < n; ++i) fn(i, 0);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < threads; ++t)
+    pool.emplace_back([&, t] {
+      for (;;) {
+        int64_t s = next.fetch_add(chunk);
+        if (s >= n) break;
+        int64_t e = std::min(n, s + chunk);
+        for (int64_t i = s; i < e; ++i) fn(i, t);
+      }
+    });
+  for (auto &th : pool) th.join();
+}
+
+// ------------------------------------------------------------- polytope
+// Convex polytope as faces; every face keeps its plane and the loop of its
+// corners, counter-clockwise seen from outside.  Cutting by a half-space
+// clips every loop and closes the hole with a cap face whose loop is
+// chained from the per-face exit/entry points, so corners shared by faces
+// are produced bit-identically from both sides.
+struct Poly {
+  std::vector<Plane> pl;
+  std::vector<int32_t> beg{0};  // loop of face f: pt[beg[f] .. beg[f+1])
+  std::vector<V3> pt;
+  void clear() {
+    pl.clear();
+    beg.assign(1, 0);
+    pt.clear();
+  }
+  bool empty() const { return pl.empty(); }
+  int nf() const { return (int)pl.size(); }
+};
+
+struct CutScratch {
+  std::vector<double> s;
+  std::vector<V3> seg_in, seg_out;
+  std::vector<char> used;
+};
+
+void make_box(Poly &p, const double lo[3], const double hi[3]) {
+  p.clear();
+  auto face = [&](V3 n, double c, int src, V3 a, V3 b, V3 cc, V3 d) {
+    p.pl.push_back({n, c, src});
+    p.pt.push_back(a);
+    p.pt.push_back(b);
+    p.pt.push_back(cc);
+    p.pt.push_back(d);
+    p.beg.push_back((int32_t)p.pt.size());
+  };
+  double X0 = lo[0], Y0 = lo[1], Z0 = lo[2], X1 = hi[0], Y1 = hi[1], Z1 = hi[2];
+  face({1, 0, 0}, X1, -1, {X1, Y0, Z0}, {X1, Y1, Z0}, {X1, Y1, Z1}, {X1, Y0, Z1});
+  face({-1, 0, 0}, -X0, -2, {X0, Y0, Z0}, {X0, Y0, Z1}, {X0, Y1, Z1}, {X0, Y1, Z0});
+  face({0, 1, 0}, Y1, -3, {X0, Y1, Z0}, {X0, Y1, Z1}, {X1, Y1, Z1}, {X1, Y1, Z0});
+  face({0, -1, 0}, -Y0, -4, {X0, Y0, Z0}, {X1, Y0, Z0}, {X1, Y0, Z1}, {X0, Y0, Z1});
+  face({0, 0, 1}, Z1, -5, {X0, Y0, Z1}, {X1, Y0, Z1}, {X1, Y1, Z1}, {X0, Y1, Z1});
+  face({0, 0, -1}, -Z0, -6, {X0, Y0, Z0}, {X0, Y1, Z0}, {X1, Y1, Z0}, {X1, Y0, Z0});
+}
+
+inline V3 crossing(V3 a, V3 b, double sa, double sb) {
+  if (lex_less(b, a)) {
+    std::swap(a, b);
+    std::swap(sa, sb);
+  }
+  double t = sa / (sa - sb);
+  return a + t * (b - a);
+}
+
+// Cut `in` by h into `out`.  Returns false (and leaves out untouched) when
+// nothing lies beyond h.  An emptied polytope comes back with no faces.
+bool cut(const Poly &in, const Plane &h, double eps, Poly &out, CutScratch &S) {
+  const size_t np = in.pt.size();
+  S.s.resize(np);
+  bool beyond = false, within = false;
+  for (size_t i = 0; i < np; ++i) {
+    double s = dot(h.n, in.pt[i]) - h.c;
+    S.s[i] = s;
+    beyond |= s > eps;
+    within |= s < -eps;
+  }
+  if (!beyond) return false;
+  out.clear();
+  if (!within) return true;
+  S.seg_in.clear();
+  S.seg_out.clear();
+  for (int f = 0; f < in.nf(); ++f) {
+    const int b = in.beg[f], k = in.beg[f + 1] - b;
+    const size_t start = out.pt.size();
+    bool has_x = false, has_y = false;
+    V3 X{0, 0, 0}, Y{0, 0, 0};
+    for (int i = 0; i < k; ++i) {
+      const int ia = b + i, ib = b + (i + 1) % k;
+      const double sa = S.s[ia], sb = S.s[ib];
+      const bool ka = sa <= eps, kb = sb <= eps;
+      if (ka) out.pt.push_back(in.pt[ia]);
+      if (ka && !kb) {  // leaving the kept side
+        if (sa >= -eps) {
+          X = in.pt[ia];
+        } else {
+          X = crossing(in.pt[ia], in.pt[ib], sa, sb);
+          out.pt.push_back(X);
+        }
+        has_x = true;
+      } else if (!ka && kb) {  // coming back
+        if (sb >= -eps) {
+          Y = in.pt[ib];
+        } else {
+          Y = crossing(in.pt[ia], in.pt[ib], sa, sb);
+          out.pt.push_back(Y);
+        }
+        has_y = true;
+      }
+    }
+    if (out.pt.size() - start >= 3) {
+      out.pl.push_back(in.pl[f]);
+      out.beg.push_back((int32_t)out.pt.size());
+    } else {
+      out.pt.resize(start);
+    }
+    if (has_x && has_y && len2(X - Y) > eps * eps) {
+      S.seg_in.push_back(Y);
+      S.seg_out.push_back(X);
+    }
+  }
+  // chain the cap loop: the face walks X -> Y along h, the cap walks Y -> X
+  const int m = (int)S.seg_in.size();
+  if (m >= 3) {
+    S.used.assign(m, 0);
+    const size_t start = out.pt.size();
+    out.pt.push_back(S.seg_in[0]);
+    V3 cur = S.seg_out[0];
+    S.used[0] = 1;
+    bool ok = true;
+    for (int step = 1; step < m; ++step) {
+      out.pt.push_back(cur);
+      int best = -1;
+      double bd = std::numeric_limits<double>::infinity();
+      for (int j = 0; j < m; ++j)
+        if (!S.used[j]) {
+          double d = len2(S.seg_in[j] - cur);
+          if (d < bd) {
+            bd = d;
+            best = j;
+          }
+        }
+      if (best < 0 || bd > 1e6 * eps * eps) {
+        ok = false;
+        break;
+      }
+      S.used[best] = 1;
+      cur = S.seg_out[best];
+    }
+    if (ok && len2(cur - S.seg_in[0]) <= 1e6 * eps * eps) {
+      out.pl.push_back(h);
+      out.beg.push_back((int32_t)out.pt.size());
+    } else {
+      // fall back: order the distinct cap points by angle in the plane
+      out.pt.resize(start);
+      std::vector<V3> q;
+      for (int j = 0; j < m; ++j)
+        for (V3 p : {S.seg_in[j], S.seg_out[j]}) {
+          bool dup = false;
+          for (V3 r : q) dup |= len2(r - p) <= 1e6 * eps * eps;
+          if (!dup) q.push_back(p);
+        }
+      if (q.size() >= 3) {
+        V3 c{0, 0, 0};
+        for (V3 p : q) c = c + (1.0 / q.size()) * p;
+        V3 t = std::fabs(h.n.x) < 0.6 ? V3{1, 0, 0} : V3{0, 1, 0};
+        V3 u = cross(h.n, t);
+        u = (1.0 / std::sqrt(len2(u))) * u;
+        V3 w = cross(h.n, u);
+        std::sort(q.begin(), q.end(), [&](V3 a, V3 b) {
+          return std::atan2(dot(a - c, w), dot(a - c, u)) < std::atan2(dot(b - c, w), dot(b - c, u));
+        });
+        for (V3 p : q) out.pt.push_back(p);
+        out.pl.push_back(h);
+        out.beg.push_back((int32_t)out.pt.size());
+      }
+    }
+  }
+  if (out.nf() < 4) out.clear();
+  return true;
+}
+
+// ---------------------------------------------------------------- mesh
+struct Mesh {
+  int64_t nv = 0, nf = 0, ne = 0;
+  std::vector<V3> V;
+  std::vector<int32_t> F;       // nf * 3
+  std::vector<int32_t> E;       // ne * 2
+  std::vector<int32_t> fedge;   // nf * 3, edge of (F[k], F[k+1])
+  std::vector<int64_t> ef_off;  // ne + 1
+  std::vector<int32_t> ef;      // edge -> faces
+  std::vector<uint8_t> degenerate;
+};
+
+int validate(const float *V, int64_t nv, const int32_t *F, int64_t nf, std::string &err) {
+  if (nf <= 0 || nv < 3) {
+    err = "mesh has no triangles";
+    return 2;
+  }
+  for (int64_t i = 0; i < 3 * nv; ++i)
+    if (!std::isfinite(V[i])) {
+      err = "non-finite vertex coordinate";
+      return 2;
+    }
+  std::vector<uint8_t> used(nv, 0);
+  for (int64_t f = 0; f < nf; ++f) {
+    int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) {
+      err = "triangle index out of range";
+      return 2;
+    }
+    if (a == b || b == c || a == c) {
+      err = "triangle repeats a vertex";
+      return 2;
+    }
+    used[a] = used[b] = used[c] = 1;
+  }
+  for (int64_t i = 0; i < nv; ++i)
+    if (!used[i]) {
+      err = "vertex referenced by no triangle";
+      return 2;
+    }
+  std::vector<int32_t> ord(nv);
+  for (int64_t i = 0; i < nv; ++i) ord[i] = (int32_t)i;
+  std::sort(ord.begin(), ord.end(), [&](int32_t i, int32_t j) {
+    return std::memcmp(V + 3 * i, V + 3 * j, 12) < 0 ||
+           (std::memcmp(V + 3 * i, V + 3 * j, 12) == 0 && i < j);
+  });
+  for (int64_t i = 1; i < nv; ++i) {
+    const float *p = V + 3 * ord[i], *q = V + 3 * ord[i - 1];
+    if (p[0] == q[0] && p[1] == q[1] && p[2] == q[2]) {
+      err = "duplicate vertex position";
+      return 3;
+    }
+  }
+  return 0;
+}
+
+void build_topology(Mesh &M) {
+  struct HalfEdge {
+    int64_t key;  // min << 32 | max
+    int32_t face;
+    int32_t k;
+  };
+  std::vector<HalfEdge> h(3 * M.nf);
+  for (int64_t f = 0; f < M.nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int64_t u = M.F[3 * f + k], w = M.F[3 * f + (k + 1) % 3];
+      h[3 * f + k] = {std::min(u, w) << 32 | std::max(u, w), (int32_t)f, k};
+    }
+  std::sort(h.begin(), h.end(), [](const HalfEdge &a, const HalfEdge &b) {
+    return a.key < b.key || (a.key == b.key && a.face < b.face);
+  });
+  M.fedge.assign(3 * M.nf, -1);
+  M.E.clear();
+  M.ef_off.assign(1, 0);
+  M.ef.resize(3 * M.nf);
+  for (size_t i = 0; i < h.size(); ++i) {
+    if (i == 0 || h[i].key != h[i - 1].key) {
+      M.E.push_back((int32_t)(h[i].key >> 32));
+      M.E.push_back((int32_t)(h[i].key & 0xffffffff));
+      M.ef_off.push_back(M.ef_off.back());
+    }
+    M.fedge[3 * h[i].face + h[i].k] = (int32_t)(M.E.size() / 2 - 1);
+    M.ef[i] = h[i].face;
+    M.ef_off.back()++;
+  }
+  M.ne = (int64_t)M.E.size() / 2;
+  M.degenerate.assign(M.nf, 0);
+  for (int64_t f = 0; f < M.nf; ++f) {
+    V3 a = M.V[M.F[3 * f]], b = M.V[M.F[3 * f + 1]], c = M.V[M.F[3 * f + 2]];
+    V3 e1 = b - a, e2 = c - a;
+    double s = len2(e1) * len2(e2);
+    if (!(len2(cross(e1, e2)) > 1e-24 * s)) M.degenerate[f] = 1;
+  }
+}
+
+// -------------------------------------------------------------- KD tree
+// Perfect binary tree with L = 2^depth leaves; heap order; leaf j holds the
+// tree positions [j*n/L, (j+1)*n/L).  Median splits on the widest axis.
+struct Tree {
+  int depth = 0;
+  int64_t L = 0, n = 0;
+  std::vector<int32_t> order;   // position -> vertex
+  std::vector<V3> P;            // points in tree order (double copies of float inputs)
+  std::vector<double> box;      // (2L-1) * 6
+  int64_t first(int64_t j) const { return (int64_t)(((__int128)j * n) / L); }
+};
+
+void build_tree(const Mesh &M, int leaf, Tree &T) {
+  T.n = M.nv;
+  int64_t want = (T.n + leaf - 1) / leaf;
+  T.depth = 1;
+  while (((int64_t)1 << T.depth) < want) ++T.depth;
+  T.L = (int64_t)1 << T.depth;
+  T.order.resize(T.n);
+  for (int64_t i = 0; i < T.n; ++i) T.order[i] = (int32_t)i;
+  T.box.assign((2 * T.L - 1) * 6, 0.0);
+  struct Job {
+    int64_t node, j0, j1;
+  };
+  std::vector<Job> st{{0, 0, T.L}};
+  while (!st.empty()) {
+    Job jb = st.back();
+    st.pop_back();
+    int64_t p0 = T.first(jb.j0), p1 = T.first(jb.j1);
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t p = p0; p < p1; ++p) {
+      V3 v = M.V[T.order[p]];
+      double c[3] = {v.x, v.y, v.z};
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], c[d]);
+        hi[d] = std::max(hi[d], c[d]);
+      }
+    }
+    double *b = &T.box[6 * jb.node];
+    for (int d = 0; d < 3; ++d) {
+      b[d] = lo[d];
+      b[3 + d] = hi[d];
+    }
+    if (jb.j1 - jb.j0 == 1) continue;
+    int ax = 0;
+    for (int d = 1; d < 3; ++d)
+      if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+    int64_t jm = (jb.j0 + jb.j1) / 2, pm = T.first(jm);
+    auto key = [&](int32_t i) {
+      V3 v = M.V[i];
+      return ax == 0 ? v.x : (ax == 1 ? v.y : v.z);
+    };
+    std::nth_element(T.order.begin() + p0, T.order.begin() + pm, T.order.begin() + p1,
+                     [&](int32_t a, int32_t c) {
+                       double ka = key(a), kc = key(c);
+                       return ka < kc || (ka == kc && a < c);
+                     });
+    st.push_back({2 * jb.node + 1, jb.j0, jm});
+    st.push_back({2 * jb.node + 2, jm, jb.j1});
+  }
+  T.P.resize(T.n);
+  for (int64_t p = 0; p < T.n; ++p) T.P[p] = M.V[T.order[p]];
+}
+
+inline double box_d2(const double *b, V3 q) {
+  double dx = q.x < b[0] ? b[0] - q.x : (q.x > b[3] ? q.x - b[3] : 0.0);
+  double dy = q.y < b[1] ? b[1] - q.y : (q.y > b[4] ? q.y - b[4] : 0.0);
+  double dz = q.z < b[2] ? b[2] - q.z : (q.z > b[5] ? q.z - b[5] : 0.0);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// nearest tree position strictly closer than sqrt(r2), or -1
+int64_t nearest_within(const Tree &T, V3 q, double r2) {
+  struct Item {
+    int64_t node;
+    double d2;
+  };
+  Item st[128];
+  int sp = 0;
+  int64_t best = -1;
+  double bd = r2;
+  st[sp++] = {0, box_d2(&T.box[0], q)};
+  while (sp) {
+    Item it = st[--sp];
+    if (!(it.d2 < bd)) continue;
+    if (it.node >= T.L - 1) {
+      int64_t j = it.node - (T.L - 1);
+      for (int64_t p = T.first(j), e = T.first(j + 1); p < e; ++p) {
+        double d = len2(T.P[p] - q);
+        if (d < bd) {
+          bd = d;
+          best = p;
+        }
+      }
+      continue;
+    }
+    int64_t c0 = 2 * it.node + 1, c1 = c0 + 1;
+    double d0 = box_d2(&T.box[6 * c0], q), d1 = box_d2(&T.box[6 * c1], q);
+    if (d0 > d1) {
+      std::swap(c0, c1);
+      std::swap(d0, d1);
+    }
+    if (d1 < bd) st[sp++] = {c1, d1};
+    if (d0 < bd) st[sp++] = {c0, d0};
+  }
+  return best;
+}
+
+// k nearest tree positions to q excluding `self`, ascending
+int k_nearest(const Tree &T, V3 q, int64_t self, int k, int64_t *ids, double *d2s) {
+  struct Item {
+    int64_t node;
+    double d2;
+  };
+  Item st[128];
+  int sp = 0, cnt = 0;
+  st[sp++] = {0, box_d2(&T.box[0], q)};
+  while (sp) {
+    Item it = st[--sp];
+    if (cnt == k && !(it.d2 < d2s[k - 1])) continue;
+    if (it.node >= T.L - 1) {
+      int64_t j = it.node - (T.L - 1);
+      for (int64_t p = T.first(j), e = T.first(j + 1); p < e; ++p) {
+        if (p == self) continue;
+        double d = len2(T.P[p] - q);
+        if (cnt < k || d < d2s[cnt - 1]) {
+          int s = cnt < k ? cnt++ : k - 1;
+          while (s > 0 && d2s[s - 1] > d) {
+            d2s[s] = d2s[s - 1];
+            ids[s] = ids[s - 1];
+            --s;
+          }
+          d2s[s] = d;
+          ids[s] = p;
+        }
+      }
+      continue;
+    }
+    int64_t c0 = 2 * it.node + 1, c1 = c0 + 1;
+    double d0 = box_d2(&T.box[6 * c0], q), d1 = box_d2(&T.box[6 * c1], q);
+    if (d0 > d1) {
+      std::swap(c0, c1);
+      std::swap(d0, d1);
+    }
+    if (cnt < k || d1 < d2s[cnt - 1]) st[sp++] = {c1, d1};
+    if (cnt < k || d0 < d2s[cnt - 1]) st[sp++] = {c0, d0};
+  }
+  return cnt;
+}
+
+// ------------------------------------------------------- Voronoi cells
+// bisector half-space of tree positions a (own) and b, pushed out by w
+inline Plane bisector(const Tree &T, int64_t a, int64_t b, double w) {
+  V3 pa = T.P[a], pb = T.P[b], n = pb - pa;
+  double l = std::sqrt(len2(n));
+  n = (1.0 / l) * n;
+  return {n, 0.5 * (dot(n, pa) + dot(n, pb)) + w, (int32_t)b};
+}
+
+constexpr int KSEED = 32;
+
+struct CellWork {
+  Poly poly;
+  std::vector<int32_t> applied;  // tree positions whose bisectors cut it
+  double safe2 = 0;              // corners nearer than this need no check
+  bool done = false;
+};
+
+// distinct corners of a polytope (loops repeat shared corners bitwise)
+void distinct_corners(const Poly &p, std::vector<V3> &out) {
+  out = p.pt;
+  std::sort(out.begin(), out.end(), lex_less);
+  out.erase(std::unique(out.begin(), out.end(),
+                        [](V3 a, V3 b) { return a.x == b.x && a.y == b.y && a.z == b.z; }),
+            out.end());
+}
+
+// ------------------------------------------------------------- flooding
+struct Rec {
+  int32_t row, tid;  // table row (tree position) and typed id
+  float box[6];
+};
+
+struct PrimGeom {  // what the filter needs about a primitive
+  int type;        // 1 edge (line through a, unit u), 2 face (plane through a, unit u)
+  V3 a, u;
+};
+
+}  // namespace
+
+int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
+                 const BuildParams &prm, NearestService *nearest,
+                 bool (*on_tree)(void *, const Layout &), void *ctx, Layout &out,
+                 std::string &err) {
+  const double t_start = now_ms();
+  int st = validate(Vin, nv, Fin, nf, err);
+  if (st) return st;
+  const int threads = prm.threads > 0 ? prm.threads
+                                      : (int)std::max(1u, std::thread::hardware_concurrency());
+  Mesh M;
+  M.nv = nv;
+  M.nf = nf;
+  M.V.resize(nv);
+  for (int64_t i = 0; i < nv; ++i) M.V[i] = {Vin[3 * i], Vin[3 * i + 1], Vin[3 * i + 2]};
+  M.F.assign(Fin, Fin + 3 * nf);
+  build_topology(M);
+
+  // domain D
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (const V3 &v : M.V) {
+    double c[3] = {v.x, v.y, v.z};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], c[d]);
+      hi[d] = std::max(hi[d], c[d]);
+    }
+  }
+  double bbd = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                         (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  double Dlo[3], Dhi[3];
+  for (int d = 0; d < 3; ++d) {
+    double c = 0.5 * (lo[d] + hi[d]);
+    double h = 0.5 * (hi[d] - lo[d]) * prm.domain_scale + prm.domain_margin * bbd;
+    if (h <= 0) h = 1e-3 * bbd;
+    Dlo[d] = c - h;
+    Dhi[d] = c + h;
+  }
+  const double diag = std::sqrt((Dhi[0] - Dlo[0]) * (Dhi[0] - Dlo[0]) +
+                                (Dhi[1] - Dlo[1]) * (Dhi[1] - Dlo[1]) +
+                                (Dhi[2] - Dlo[2]) * (Dhi[2] - Dlo[2]));
+  const double delta = prm.delta_rel * diag;
+  const double eta = 2.0 * delta * diag + delta * delta;
+  const double eps = 1e-13 * diag;
+
+  Tree T;
+  build_tree(M, std::max(2, std::min(32, prm.leaf_size)), T);
+
+  // ---- device arrays of the KD tree (needed by the certification service)
+  out = Layout();
+  out.nv = nv;
+  out.nf = nf;
+  out.ne = M.ne;
+  for (int d = 0; d < 3; ++d) {
+    out.dom[d] = (float)Dlo[d];
+    out.dom[3 + d] = (float)Dhi[d];
+  }
+  out.delta = (float)delta;
+  out.kd_depth = T.depth;
+  out.kd_points.resize(4 * nv);
+  out.pos_of_vertex.resize(nv);
+  for (int64_t p = 0; p < nv; ++p) {
+    int32_t v = T.order[p];
+    out.kd_points[4 * p + 0] = Vin[3 * v + 0];
+    out.kd_points[4 * p + 1] = Vin[3 * v + 1];
+    out.kd_points[4 * p + 2] = Vin[3 * v + 2];
+    std::memcpy(&out.kd_points[4 * p + 3], &v, 4);
+    out.pos_of_vertex[v] = (int32_t)p;
+  }
+  out.kd_nodes.resize((T.L - 1) * 12);
+  for (int64_t i = 0; i < T.L - 1; ++i) {
+    const double *c0 = &T.box[6 * (2 * i + 1)], *c1 = &T.box[6 * (2 * i + 2)];
+    float *o = &out.kd_nodes[12 * i];
+    // boxes of float points are exact in float
+    o[0] = (float)c0[0]; o[1] = (float)c0[1]; o[2] = (float)c0[2]; o[3] = (float)c0[3];
+    o[4] = (float)c0[4]; o[5] = (float)c0[5]; o[6] = (float)c1[0]; o[7] = (float)c1[1];
+    o[8] = (float)c1[2]; o[9] = (float)c1[3]; o[10] = (float)c1[4]; o[11] = (float)c1[5];
+  }
+  for (int d = 0; d < 6; ++d) out.kd_root[d] = (float)T.box[d];
+  if (on_tree && nearest && !on_tree(ctx, out)) nearest = nullptr;
+
+  // ---- Voronoi cells: k-nearest seeding
+  const double t_cells = now_ms();
+  std::vector<CellWork> cells(nv);
+  std::vector<CutScratch> scratch(threads);
+  std::vector<Poly> tmp(threads);
+  parallel_for(nv, threads, 64, [&](int64_t p, int t) {
+    CellWork &C = cells[p];
+    make_box(C.poly, Dlo, Dhi);
+    int64_t ids[KSEED];
+    double d2s[KSEED];
+    int k = k_nearest(T, T.P[p], p, KSEED, ids, d2s);
+    for (int i = 0; i < k; ++i) {
+      if (cut(C.poly, bisector(T, p, ids[i], 0.0), eps, tmp[t], scratch[t])) std::swap(C.poly, tmp[t]);
+      C.applied.push_back((int32_t)ids[i]);
+    }
+    // no vertex outside the k nearest can be nearer than p to a corner that
+    // lies within half the k-th distance of p
+    C.safe2 = k == KSEED ? 0.25 * d2s[KSEED - 1] : std::numeric_limits<double>::infinity();
+  });
+
+  // ---- certification rounds: a corner x is settled when no vertex is
+  // strictly nearer to x than the cell's own vertex; a cell whose corners
+  // are all settled equals Cell(v) ∩ D (it is convex and contains the cell).
+  const double epsc = 1e-12 * diag * diag;
+  std::vector<std::vector<V3>> corner(nv);
+  std::vector<int64_t> coff(nv + 1);
+  std::vector<float> qbuf;
+  std::vector<int32_t> qans;
+  int64_t rounds = 0, cert_queries = 0;
+  for (;;) {
+    // far corners of the cells still open
+    parallel_for(nv, threads, 256, [&](int64_t p, int) {
+      auto &cv = corner[p];
+      cv.clear();
+      if (cells[p].done) return;
+      std::vector<V3> all;
+      distinct_corners(cells[p].poly, all);
+      for (V3 x : all)
+        if (len2(x - T.P[p]) > cells[p].safe2) cv.push_back(x);
+      if (cv.empty()) cells[p].done = true;
+    });
+    coff[0] = 0;
+    for (int64_t p = 0; p < nv; ++p) coff[p + 1] = coff[p] + (int64_t)corner[p].size();
+    const int64_t nq = coff[nv];
+    if (nq == 0) break;
+    ++rounds;
+    cert_queries += nq;
+    std::vector<int64_t> viol_pos(nq, -1);
+    bool used_device = false;
+    if (nearest) {
+      qbuf.resize(3 * nq);
+      qans.resize(nq);
+      parallel_for(nv, threads, 256, [&](int64_t p, int) {
+        for (size_t i = 0; i < corner[p].size(); ++i) {
+          V3 x = corner[p][i];
+          float *o = &qbuf[3 * (coff[p] + i)];
+          o[0] = (float)x.x;
+          o[1] = (float)x.y;
+          o[2] = (float)x.z;
+        }
+      });
+      used_device = nearest->query(qbuf.data(), nq, qans.data());
+    }
+    parallel_for(nv, threads, 64, [&](int64_t p, int t) {
+      CellWork &C = cells[p];
+      if (corner[p].empty()) return;
+      std::vector<int64_t> cand;
+      for (size_t i = 0; i < corner[p].size(); ++i) {
+        V3 x = corner[p][i];
+        double r2 = len2(x - T.P[p]) - epsc;
+        int64_t w;
+        if (used_device) {
+          // the float32 search proposes, double precision decides; when the
+          // proposal is another vertex that is not strictly nearer in double
+          // (a float32 near-tie), settle the corner with the host search
+          const int64_t prop = qans[coff[p] + i];
+          w = (prop >= 0 && prop != p && len2(T.P[prop] - x) < r2) ? prop : -1;
+          if (w < 0 && prop != p) w = nearest_within(T, x, r2);
+        } else {
+          w = nearest_within(T, x, r2);
+        }
+        if (w >= 0 && w != p &&
+            std::find(C.applied.begin(), C.applied.end(), (int32_t)w) == C.applied.end() &&
+            std::find(cand.begin(), cand.end(), w) == cand.end())
+          cand.push_back(w);
+      }
+      if (cand.empty()) {
+        C.done = true;
+        return;
+      }
+      std::sort(cand.begin(), cand.end(), [&](int64_t a, int64_t b) {
+        return len2(T.P[a] - T.P[p]) < len2(T.P[b] - T.P[p]);
+      });
+      for (int64_t w : cand) {
+        if (cut(C.poly, bisector(T, p, w, 0.0), eps, tmp[t], scratch[t])) std::swap(C.poly, tmp[t]);
+        C.applied.push_back((int32_t)w);
+      }
+    });
+    if (rounds > 64) break;
+  }
+  corner.clear();
+  corner.shrink_to_fit();
+
+  // neighbours (generators of surviving bisector faces) and widened cells
+  std::vector<std::vector<int32_t>> nbr(nv);
+  std::vector<Poly> cell(nv);
+  parallel_for(nv, threads, 64, [&](int64_t p, int t) {
+    auto &nb = nbr[p];
+    for (const Plane &h : cells[p].poly.pl)
+      if (h.src >= 0 && std::find(nb.begin(), nb.end(), h.src) == nb.end()) nb.push_back(h.src);
+    double wlo[3], whi[3];
+    for (int d = 0; d < 3; ++d) {
+      wlo[d] = Dlo[d] - delta;
+      whi[d] = Dhi[d] + delta;
+    }
+    Poly &c = cell[p];
+    make_box(c, wlo, whi);
+    for (int32_t w : nb)
+      if (cut(c, bisector(T, p, w, delta), eps, tmp[t], scratch[t])) std::swap(c, tmp[t]);
+    cells[p].poly.clear();
+    cells[p].poly.pl.shrink_to_fit();
+    cells[p].poly.pt.shrink_to_fit();
+    cells[p].applied.clear();
+    cells[p].applied.shrink_to_fit();
+  });
+  cells.clear();
+  cells.shrink_to_fit();
+  int64_t npairs = 0;
+  for (auto &nb : nbr) npairs += (int64_t)nb.size();
+  const double t_flood = now_ms();
+
+  // ---- flooding inspection (Alg. 1) over every edge and every face
+  auto face_inward = [&](int64_t f, int k) {
+    // unit normal of the plane through edge k of face f, perpendicular to
+    // the face, pointing into the face
+    V3 a = M.V[M.F[3 * f]], b = M.V[M.F[3 * f + 1]], c = M.V[M.F[3 * f + 2]];
+    V3 n = cross(b - a, c - a);
+    V3 d = M.V[M.F[3 * f + (k + 1) % 3]] - M.V[M.F[3 * f + k]];
+    V3 m = cross(n, d);
+    return (1.0 / std::sqrt(len2(m))) * m;
+  };
+  struct TLS {
+    std::vector<Rec> recs;
+    std::vector<int64_t> seen;
+    std::vector<int32_t> queue;
+    Poly A, B;
+    CutScratch S;
+    int64_t inspections = 0;
+  };
+  std::vector<TLS> tls(threads);
+  for (auto &x : tls) {
+    x.seen.assign(nv, -1);
+    x.queue.resize(nv + 3);
+  }
+  const int64_t nprim = M.ne + M.nf;
+  parallel_for(nprim, threads, 32, [&](int64_t i, int t) {
+    TLS &X = tls[t];
+    Plane perp[16];
+    int np_ = 0;
+    PrimGeom g;
+    int32_t seeds[3];
+    int ns;
+    int32_t tid;
+    if (i < M.ne) {
+      int64_t e = i;
+      V3 a = M.V[M.E[2 * e]], b = M.V[M.E[2 * e + 1]];
+      V3 u = b - a;
+      u = (1.0 / std::sqrt(len2(u))) * u;
+      perp[np_++] = {-1.0 * u, -dot(u, a) + delta, -10};
+      perp[np_++] = {u, dot(u, b) + delta, -11};
+      for (int64_t j = M.ef_off[e]; j < M.ef_off[e + 1] && np_ < 16; ++j) {
+        int64_t f = M.ef[j];
+        if (M.degenerate[f]) continue;
+        int k = M.fedge[3 * f] == e ? 0 : (M.fedge[3 * f + 1] == e ? 1 : 2);
+        V3 m = face_inward(f, k);  // the far side of f: m.(x - a) <= 0
+        perp[np_++] = {m, dot(m, a) + delta, (int32_t)(-12 - j)};
+      }
+      g = {1, a, u};
+      seeds[0] = M.E[2 * e];
+      seeds[1] = M.E[2 * e + 1];
+      ns = 2;
+      tid = (int32_t)(1u << 30 | (uint32_t)e);
+    } else {
+      int64_t f = i - M.ne;
+      if (M.degenerate[f]) return;
+      for (int k = 0; k < 3; ++k) {
+        V3 m = face_inward(f, k);  // inside: m.(x - p_k) >= 0
+        V3 pk = M.V[M.F[3 * f + k]];
+        perp[np_++] = {-1.0 * m, -dot(m, pk) + delta, -20 - k};
+      }
+      V3 a = M.V[M.F[3 * f]], b = M.V[M.F[3 * f + 1]], c = M.V[M.F[3 * f + 2]];
+      V3 n = cross(b - a, c - a);
+      g = {2, a, (1.0 / std::sqrt(len2(n))) * n};
+      for (int k = 0; k < 3; ++k) seeds[k] = M.F[3 * f + k];
+      ns = 3;
+      tid = (int32_t)(2u << 30 | (uint32_t)f);
+    }
+    auto gval = [&](V3 x, V3 pv) {
+      V3 w = x - g.a;
+      double s = dot(w, g.u);
+      double dist2 = g.type == 1 ? len2(w) - s * s : s * s;
+      return len2(x - pv) - dist2 + eta;
+    };
+    int64_t head = 0, tail = 0;
+    for (int s = 0; s < ns; ++s) {
+      int64_t p = out.pos_of_vertex[seeds[s]];
+      X.seen[p] = i;
+      X.queue[tail++] = (int32_t)p;
+    }
+    while (head < tail) {
+      const int64_t p = X.queue[head++];
+      ++X.inspections;
+      // ConvexPoly(v, prim) = Cell(v) ∩ Space-perp(prim)
+      const Poly *cur = &cell[p];
+      Poly *bufs[2] = {&X.A, &X.B};
+      int wsel = 0;
+      for (int j = 0; j < np_ && !cur->empty(); ++j) {
+        if (cut(*cur, perp[j], eps, *bufs[wsel], X.S)) {
+          cur = bufs[wsel];
+          wsel ^= 1;
+        }
+      }
+      if (cur->empty()) continue;
+      const V3 pv = T.P[p];
+      const int32_t vid = T.order[p];
+      bool keep = (g.type == 1) ? (seeds[0] == vid || seeds[1] == vid)
+                                : (seeds[0] == vid || seeds[1] == vid || seeds[2] == vid);
+      double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+      bool have = false;
+      auto grow = [&](V3 x) {
+        blo[0] = std::min(blo[0], x.x); bhi[0] = std::max(bhi[0], x.x);
+        blo[1] = std::min(blo[1], x.y); bhi[1] = std::max(bhi[1], x.y);
+        blo[2] = std::min(blo[2], x.z); bhi[2] = std::max(bhi[2], x.z);
+        have = true;
+      };
+      for (int f = 0; f < cur->nf(); ++f) {
+        const int b0 = cur->beg[f], k = cur->beg[f + 1] - b0;
+        for (int q = 0; q < k; ++q) {
+          V3 x0 = cur->pt[b0 + q], x1 = cur->pt[b0 + (q + 1) % k];
+          double g0 = gval(x0, pv), g1 = gval(x1, pv);
+          if (g0 > 0) {
+            keep = true;
+            grow(x0);
+          }
+          if ((g0 > 0) != (g1 > 0)) {
+            // g restricted to the edge is a quadratic in t: exact roots
+            V3 d = x1 - x0, w0 = x0 - g.a, r0 = x0 - pv;
+            double du = dot(d, g.u), wu = dot(w0, g.u);
+            double A, B, Cc;
+            if (g.type == 1) {  // |x-v|^2 - (|w|^2 - (w.u)^2)
+              A = len2(d) - (len2(d) - du * du);
+              B = 2 * dot(r0, d) - 2 * (dot(w0, d) - wu * du);
+              Cc = len2(r0) - (len2(w0) - wu * wu) + eta;
+            } else {            // |x-v|^2 - (w.u)^2
+              A = len2(d) - du * du;
+              B = 2 * dot(r0, d) - 2 * wu * du;
+              Cc = len2(r0) - wu * wu + eta;
+            }
+            double roots[2];
+            int nr = 0;
+            if (std::fabs(A) <= 1e-14 * (std::fabs(B) + std::fabs(Cc))) {
+              if (B != 0) roots[nr++] = -Cc / B;
+            } else {
+              double disc = std::max(0.0, B * B - 4 * A * Cc);
+              double sq = std::sqrt(disc);
+              double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
+              if (qq != 0) roots[nr++] = Cc / qq;
+              roots[nr++] = qq / A;
+            }
+            for (int r = 0; r < nr; ++r) {
+              double tt = roots[r];
+              if (!(tt >= -1e-9 && tt <= 1 + 1e-9)) continue;
+              tt = std::min(1.0, std::max(0.0, tt));
+              grow(x0 + tt * d);
+            }
+          }
+        }
+      }
+      if (!keep) continue;
+      if (!have)
+        for (V3 x : cur->pt) grow(x);
+      Rec r;
+      r.row = (int32_t)p;
+      r.tid = tid;
+      for (int d = 0; d < 3; ++d) {
+        float l = (float)(blo[d] - delta), h = (float)(bhi[d] + delta);
+        if ((double)l > blo[d] - delta) l = std::nextafter(l, -INFINITY);
+        if ((double)h < bhi[d] + delta) h = std::nextafter(h, INFINITY);
+        r.box[d] = l;
+        r.box[3 + d] = h;
+      }
+      X.recs.push_back(r);
+      for (int32_t w : nbr[p])
+        if (X.seen[w] != i) {
+          X.seen[w] = i;
+          X.queue[tail++] = w;
+        }
+    }
+  });
+  cell.clear();
+  cell.shrink_to_fit();
+
+  // ---- pack the CSR table in row (tree) order
+  int64_t total = 0, insp = 0;
+  for (auto &x : tls) {
+    total += (int64_t)x.recs.size();
+    insp += x.inspections;
+  }
+  if (total >= ((int64_t)1 << 32)) {
+    err = "interception table exceeds 2^32 entries";
+    return 9;
+  }
+  out.row_off.assign(nv + 1, 0);
+  for (auto &x : tls)
+    for (const Rec &r : x.recs) out.row_off[r.row + 1]++;
+  for (int64_t p = 0; p < nv; ++p) out.row_off[p + 1] += out.row_off[p];
+  std::vector<Rec> all(total);
+  {
+    std::vector<uint32_t> fill(out.row_off.begin(), out.row_off.end() - 1);
+    for (auto &x : tls) {
+      for (const Rec &r : x.recs) all[fill[r.row]++] = r;
+      std::vector<Rec>().swap(x.recs);
+    }
+  }
+  tls.clear();
+  parallel_for(nv, threads, 1024, [&](int64_t p, int) {
+    std::sort(all.begin() + out.row_off[p], all.begin() + out.row_off[p + 1],
+              [](const Rec &a, const Rec &b) { return (uint32_t)a.tid < (uint32_t)b.tid; });
+  });
+  out.entries.resize(8 * total);
+  int64_t maxl = 0;
+  for (int64_t p = 0; p < nv; ++p) maxl = std::max<int64_t>(maxl, out.row_off[p + 1] - out.row_off[p]);
+  parallel_for(total, threads, 1 << 16, [&](int64_t j, int) {
+    float *o = &out.entries[8 * j];
+    const Rec &r = all[j];
+    o[0] = r.box[0]; o[1] = r.box[1]; o[2] = r.box[2];
+    std::memcpy(&o[3], &r.tid, 4);
+    o[4] = r.box[3]; o[5] = r.box[4]; o[6] = r.box[5]; o[7] = 0.f;
+  });
+
+  // ---- geometry records
+  out.edges = M.E;
+  out.edge_rec.resize(8 * M.ne);
+  for (int64_t e = 0; e < M.ne; ++e) {
+    const float *a = Vin + 3 * M.E[2 * e], *b = Vin + 3 * M.E[2 * e + 1];
+    float dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    double l2 = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+    float *o = &out.edge_rec[8 * e];
+    o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; o[3] = (float)(1.0 / l2);
+    o[4] = dx; o[5] = dy; o[6] = dz; o[7] = 0.f;
+  }
+  out.face_rec.resize(12 * nf);
+  out.tris.resize(4 * nf);
+  int64_t ndeg = 0;
+  for (int64_t f = 0; f < nf; ++f) {
+    const float *a = Vin + 3 * M.F[3 * f], *b = Vin + 3 * M.F[3 * f + 1], *c = Vin + 3 * M.F[3 * f + 2];
+    double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+    double e2[3] = {(double)c[0] - a[0], (double)c[1] - a[1], (double)c[2] - a[2]};
+    double d00 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+    double d01 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+    double d11 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    double den = d00 * d11 - d01 * d01;
+    float *o = &out.face_rec[12 * f];
+    o[0] = a[0]; o[1] = a[1]; o[2] = a[2];
+    o[4] = (float)e1[0]; o[5] = (float)e1[1]; o[6] = (float)e1[2];
+    o[8] = (float)e2[0]; o[9] = (float)e2[1]; o[10] = (float)e2[2];
+    if (M.degenerate[f]) {
+      ++ndeg;
+      o[3] = o[7] = o[11] = std::numeric_limits<float>::quiet_NaN();
+    } else {
+      o[3] = (float)(d11 / den);
+      o[7] = (float)(d01 / den);
+      o[11] = (float)(d00 / den);
+    }
+    for (int k = 0; k < 3; ++k) out.tris[4 * f + k] = M.F[3 * f + k];
+    out.tris[4 * f + 3] = 0;
+  }
+  out.n_entries = total;
+  out.max_list = maxl;
+  out.neighbour_pairs = npairs;
+  out.inspections = insp;
+  out.cert_rounds = rounds;
+  out.cert_queries = cert_queries;
+  out.n_degenerate = ndeg;
+  const double t_end = now_ms();
+  out.ms_total = t_end - t_start;
+  out.ms_cells = t_flood - t_cells;
+  out.ms_inspect = t_end - t_flood;
+  return 0;
+}
+
+}  // namespace p2m

@@ -1,0 +1,75 @@
+// builder.h -- host preprocessing of the P2M query layout (Alg. A.1).
+//
+// Produces everything the query kernels read: a bucketed KD tree over the
+// vertices (perfect binary tree, child boxes in the parent), the CSR
+// interception table in KD-tree row order with one Region box per entry,
+// and per-primitive geometry records.  Runs on the host with std::thread;
+// the Voronoi-cell certification can hand its nearest-vertex queries to a
+// device kernel through the NearestOracle interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace p2m {
+
+struct BuildParams {
+  double domain_scale = 10.0;
+  double domain_margin = 0.0;
+  double delta_rel = 4e-6;
+  int threads = 0;
+  int leaf_size = 8;
+};
+
+// Batched nearest-vertex service used to certify Voronoi cells.  query()
+// receives float32 points and writes the KD-tree position of the nearest
+// vertex of each (or -1).
+struct NearestService {
+  virtual ~NearestService() = default;
+  virtual bool query(const float *xyz, int64_t n, int32_t *out_pos) = 0;
+};
+
+// Device-ready arrays (all little-endian, float32 unless stated).
+struct Layout {
+  int64_t nv = 0, nf = 0, ne = 0;
+  // domain D and the widening margin
+  float dom[6] = {0, 0, 0, 0, 0, 0};
+  float delta = 0.f;
+  // KD tree: depth d, L = 2^d leaves; leaf j holds tree positions
+  // [j*nv/L, (j+1)*nv/L).  Internal node i (heap order, 0..L-2) stores the
+  // boxes of its two children in 12 floats:
+  //   {c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x}, {c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y},
+  //   {c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z}
+  int kd_depth = 0;
+  std::vector<float> kd_nodes;    // (L-1) * 12
+  std::vector<float> kd_points;   // nv * 4: x, y, z, original vertex id (int bits)
+  float kd_root[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<int32_t> pos_of_vertex;   // original id -> tree position (= table row)
+  // interception table, rows in tree order
+  std::vector<uint32_t> row_off;   // nv + 1
+  // entry: {lo.x, lo.y, lo.z, typed id bits}, {hi.x, hi.y, hi.z, 0}
+  //   typed id = type << 30 | id   (type 1 = edge, 2 = face)
+  std::vector<float> entries;      // n_entries * 8
+  // geometry records
+  //   edge e: {a.x, a.y, a.z, 1/|b-a|^2}, {b.x-a.x, b.y-a.y, b.z-a.z, 0}
+  //   face f: {a, A}, {b-a, B}, {c-a, C} with the projection weights
+  //           s = A (e1.w) - B (e2.w), t = C (e2.w) - B (e1.w), w = q - a
+  std::vector<float> edge_rec;     // ne * 8
+  std::vector<float> face_rec;     // nf * 12
+  std::vector<int32_t> edges;      // ne * 2 canonical (min, max)
+  std::vector<int32_t> tris;       // nf * 4 (a, b, c, 0) for the backward scatter
+  // statistics
+  int64_t n_entries = 0, max_list = 0, neighbour_pairs = 0, inspections = 0;
+  int64_t cert_rounds = 0, cert_queries = 0, n_degenerate = 0;
+  double ms_total = 0, ms_cells = 0, ms_inspect = 0;
+};
+
+// Status codes mirror p2m_status.
+int build_layout(const float *V, int64_t nv, const int32_t *F, int64_t nf,
+                 const BuildParams &prm, NearestService *nearest,
+                 // called once the KD tree exists, before the cells need it
+                 bool (*on_tree)(void *ctx, const Layout &), void *ctx, Layout &out,
+                 std::string &err);
+
+}  // namespace p2m

@@ -1,0 +1,631 @@
+// kernels.cu -- sm_103a kernels of the P2M query stage.
+//
+//   a1  Morton bucket sort of the queries (count with warp-aggregated
+//       atomics, exclusive scan, scatter into a float4 stream)
+//   a2  nearest vertex: KD tree with the child boxes stored in the parent,
+//       nearer child first, far child on a short stack, pruning by box
+//       distance; candidate comparisons use the bisector form
+//       2 (q-b).(c-b) > |c-b|^2, whose rounding error does not grow with
+//       |q-b|^2 / |c-b| the way comparing two squared distances does
+//   a3  CSR interception list of that vertex
+//   a4  Region-box filter of every entry (Sec. 4.6)
+//   a5  d_min = d(q, v) (Alg. A.2)
+//   a6  edge: slab test, then the distance to its line
+//   a7  face: prism test, then the distance to its plane
+//   a8  minimum, written to the caller's order
+//   a9  backward scatter
+//   a10 batched persistent variant over many meshes
+//
+// None of this is a dense contraction: the kernels run on the CUDA cores
+// and are bound by dependent loads (tree nodes, list entries, records).
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace p2m {
+namespace {
+
+constexpr float kPruneSlack = 1.0f + 1.0f / (1 << 20);
+
+__device__ __forceinline__ float box_d2(float qx, float qy, float qz, float lx, float ly, float lz,
+                                        float hx, float hy, float hz) {
+  float dx = fmaxf(fmaxf(lx - qx, qx - hx), 0.f);
+  float dy = fmaxf(fmaxf(ly - qy, qy - hy), 0.f);
+  float dz = fmaxf(fmaxf(lz - qz, qz - hz), 0.f);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ int64_t leaf_first(const DevView &m, int64_t j) {
+  return (j * m.nv) >> m.depth;
+}
+
+// Work counters of one query (counting variant only): internal nodes
+// visited, points examined, list entries scanned, edges tested, faces tested.
+struct Work {
+  int nodes, points, entries, edges, faces;
+};
+
+// Nearest vertex of q: returns the KD-tree position (= table row).
+template <bool COUNT = false>
+__device__ __forceinline__ int nearest_pos(const DevView &m, float qx, float qy, float qz,
+                                           Work *wk = nullptr) {
+  int best = -1, bid = 0x7fffffff;
+  float bx = 0.f, by = 0.f, bz = 0.f, bd2 = FLT_MAX;
+  float wx = 0.f, wy = 0.f, wz = 0.f;  // q - best
+  int stk[48];
+  float sdd[48];
+  int sp = 0;
+  int node = 0;
+  const int64_t nleaf0 = m.L - 1;
+  for (;;) {
+    if (node >= nleaf0) {
+      const int64_t j = node - nleaf0;
+      const int64_t p0 = leaf_first(m, j), p1 = leaf_first(m, j + 1);
+      if (COUNT) wk->points += (int)(p1 - p0);
+      for (int64_t p = p0; p < p1; ++p) {
+        const float4 c = __ldg(&m.kd_points[p]);
+        const int cid = __float_as_int(c.w);
+        bool take;
+        if (best < 0) {
+          take = true;
+        } else {
+          const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
+          const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
+          take = lhs > 0.f || (lhs == 0.f && cid < bid);
+        }
+        if (take) {
+          best = (int)p;
+          bid = cid;
+          bx = c.x;
+          by = c.y;
+          bz = c.z;
+          wx = qx - bx;
+          wy = qy - by;
+          wz = qz - bz;
+          bd2 = wx * wx + wy * wy + wz * wz;
+        }
+      }
+    } else {
+      if (COUNT) ++wk->nodes;
+      const float4 A = __ldg(&m.kd_nodes[3 * node + 0]);
+      const float4 B = __ldg(&m.kd_nodes[3 * node + 1]);
+      const float4 C = __ldg(&m.kd_nodes[3 * node + 2]);
+      float d0 = box_d2(qx, qy, qz, A.x, A.y, A.z, A.w, B.x, B.y);
+      float d1 = box_d2(qx, qy, qz, B.z, B.w, C.x, C.y, C.z, C.w);
+      int c0 = 2 * node + 1, c1 = c0 + 1;
+      if (d1 < d0) {
+        const float t = d0; d0 = d1; d1 = t;
+        const int u = c0; c0 = c1; c1 = u;
+      }
+      const float bound = bd2 * kPruneSlack;
+      if (d1 <= bound && sp < 48) {
+        stk[sp] = c1;
+        sdd[sp] = d1;
+        ++sp;
+      }
+      if (d0 <= bound) {
+        node = c0;
+        continue;
+      }
+    }
+    bool more = false;
+    while (sp > 0) {
+      --sp;
+      if (sdd[sp] <= bd2 * kPruneSlack) {
+        node = stk[sp];
+        more = true;
+        break;
+      }
+    }
+    if (!more) break;
+  }
+  return best;
+}
+
+// ------------------------------------------------------------------ a1
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ff;
+  v = (v | (v << 16)) & 0x030000FF;
+  v = (v | (v << 8)) & 0x0300F00F;
+  v = (v | (v << 4)) & 0x030C30C3;
+  v = (v | (v << 2)) & 0x09249249;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t morton_bucket(float x, float y, float z, const float *lo,
+                                                  const float *inv, int shift) {
+  float u = fminf(fmaxf((x - lo[0]) * inv[0], 0.f), 0.99999994f);
+  float v = fminf(fmaxf((y - lo[1]) * inv[1], 0.f), 0.99999994f);
+  float w = fminf(fmaxf((z - lo[2]) * inv[2], 0.f), 0.99999994f);
+  if (!(u == u)) u = 0.f;
+  if (!(v == v)) v = 0.f;
+  if (!(w == w)) w = 0.f;
+  uint32_t code = spread10((uint32_t)(u * 1024.f)) | (spread10((uint32_t)(v * 1024.f)) << 1) |
+                  (spread10((uint32_t)(w * 1024.f)) << 2);
+  return code >> shift;
+}
+
+struct SortParams {
+  float lo[3];
+  float inv[3];
+  int shift;
+};
+
+__global__ void k_bucket_count(const float *__restrict__ q, int64_t n, SortParams sp,
+                               uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = q[3 * i], y = q[3 * i + 1], z = q[3 * i + 2];
+  const uint32_t b = morton_bucket(x, y, z, sp.lo, sp.inv, sp.shift);
+  // warp-aggregated atomic: lanes of one bucket share a single atomicAdd
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&hist[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+}
+
+// exclusive scan of hist[0..nb) into off[0..nb), one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t *__restrict__ hist,
+                                                     uint32_t *__restrict__ off, int nb) {
+  __shared__ uint32_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + 1023) / 1024;
+  const int b0 = t * per, b1 = min(nb, b0 + per);
+  uint32_t s = 0;
+  for (int b = b0; b < b1; ++b) s += hist[b];
+  part[t] = s;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    uint32_t v = t >= d ? part[t - d] : 0u;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - s;
+  for (int b = b0; b < b1; ++b) {
+    off[b] = run;
+    run += hist[b];
+  }
+}
+
+__global__ void k_bucket_scatter(const float *__restrict__ q, int64_t n,
+                                 const uint2 *__restrict__ key_rank,
+                                 const uint32_t *__restrict__ off, float4 *__restrict__ sorted) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 kr = key_rank[i];
+  sorted[off[kr.x] + kr.y] = make_float4(q[3 * i], q[3 * i + 1], q[3 * i + 2], __int_as_float((int)i));
+}
+
+__global__ void k_identity(const float *__restrict__ q, int64_t n, float4 *__restrict__ sorted) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  sorted[i] = make_float4(q[3 * i], q[3 * i + 1], q[3 * i + 2], __int_as_float((int)i));
+}
+
+// ------------------------------------------------------------ a2..a8
+struct Best {
+  float d2;
+  float cx, cy, cz;
+  uint32_t tid;  // type << 30 | id
+  float w0, w1, w2;
+};
+
+template <bool COUNT = false>
+__device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
+                                          Best &r, Work *wk = nullptr) {
+  const int v = nearest_pos<COUNT>(m, qx, qy, qz, wk);
+  const float4 pv = __ldg(&m.kd_points[v]);
+  {
+    const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
+    r.d2 = dx * dx + dy * dy + dz * dz;
+    r.cx = pv.x;
+    r.cy = pv.y;
+    r.cz = pv.z;
+    r.tid = (uint32_t)__float_as_int(pv.w);
+    r.w0 = 1.f;
+    r.w1 = 0.f;
+    r.w2 = 0.f;
+  }
+  const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
+  if (COUNT) wk->entries += (int)(j1 - j0);
+  for (uint32_t j = j0; j < j1; ++j) {
+    const float4 lo = __ldg(&m.entries[2 * (size_t)j]);
+    if (qx < lo.x || qy < lo.y || qz < lo.z) continue;
+    const float4 hi = __ldg(&m.entries[2 * (size_t)j + 1]);
+    if (qx > hi.x || qy > hi.y || qz > hi.z) continue;
+    const uint32_t tid = (uint32_t)__float_as_int(lo.w);
+    const uint32_t id = tid & 0x3fffffffu;
+    if ((tid >> 30) == 1u) {
+      if (COUNT) ++wk->edges;
+      const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
+      const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
+      const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+      const float t = (wx * d.x + wy * d.y + wz * d.z) * a.w;
+      if (t > 0.f && t < 1.f) {
+        const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
+        const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
+        const float d2 = ex * ex + ey * ey + ez * ez;
+        if (d2 < r.d2) {
+          r.d2 = d2;
+          r.cx = cx;
+          r.cy = cy;
+          r.cz = cz;
+          r.tid = tid;
+          r.w0 = 1.f - t;
+          r.w1 = t;
+          r.w2 = 0.f;
+        }
+      }
+    } else {
+      if (COUNT) ++wk->faces;
+      const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
+      const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
+      const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
+      const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+      const float p1 = wx * e1.x + wy * e1.y + wz * e1.z;
+      const float p2 = wx * e2.x + wy * e2.y + wz * e2.z;
+      const float s = a.w * p1 - e1.w * p2;
+      const float t = e2.w * p2 - e1.w * p1;
+      if (s > 0.f && t > 0.f && s + t < 1.f) {
+        const float cx = a.x + s * e1.x + t * e2.x;
+        const float cy = a.y + s * e1.y + t * e2.y;
+        const float cz = a.z + s * e1.z + t * e2.z;
+        const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
+        const float d2 = ex * ex + ey * ey + ez * ez;
+        if (d2 < r.d2) {
+          r.d2 = d2;
+          r.cx = cx;
+          r.cy = cy;
+          r.cz = cz;
+          r.tid = tid;
+          r.w0 = 1.f - s - t;
+          r.w1 = s;
+          r.w2 = t;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+  return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+__device__ __forceinline__ void store_result(int64_t o, const Best &r, bool ok, uint8_t st,
+                                             float *dist, float *closest, int32_t *prim_id,
+                                             uint8_t *prim_type, float4 *save, uint8_t *status) {
+  if (ok) {
+    dist[o] = sqrtf(r.d2);
+    if (closest) {
+      closest[3 * o] = r.cx;
+      closest[3 * o + 1] = r.cy;
+      closest[3 * o + 2] = r.cz;
+    }
+    prim_id[o] = (int32_t)(r.tid & 0x3fffffffu);
+    if (prim_type) prim_type[o] = (uint8_t)(r.tid >> 30);
+    if (save) save[o] = make_float4(__uint_as_float(r.tid), r.w0, r.w1, r.w2);
+  } else {
+    const float nan = __int_as_float(0x7fc00000);
+    dist[o] = nan;
+    if (closest) closest[3 * o] = closest[3 * o + 1] = closest[3 * o + 2] = nan;
+    prim_id[o] = -1;
+    if (prim_type) prim_type[o] = 0xff;
+    if (save) save[o] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+  }
+  if (status) status[o] = st;
+}
+
+__global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
+                        float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
+                        uint8_t *status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 s = sq[i];
+  const int64_t o = __float_as_int(s.w);
+  Best r;
+  const bool ok = finite3(s.x, s.y, s.z);
+  uint8_t st = ok ? 0 : 2;
+  if (ok) {
+    if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
+        s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
+      st |= 1;
+    query_one(m, s.x, s.y, s.z, r);
+  }
+  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+}
+
+// Counting variant of the query (not timed): sums the per-query work.
+__global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t n,
+                              unsigned long long *__restrict__ acc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Work w = {0, 0, 0, 0, 0};
+  if (i < n) {
+    const float4 s = sq[i];
+    Best r;
+    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w);
+  }
+  int v[5] = {w.nodes, w.points, w.entries, w.edges, w.faces};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    unsigned long long x = (unsigned long long)v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], x);
+  }
+}
+
+__global__ void k_nearest(DevView m, const float *__restrict__ xyz, int64_t n,
+                          int32_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  out[i] = finite3(x, y, z) ? nearest_pos(m, x, y, z) : -1;
+}
+
+// ------------------------------------------------------------------ a9
+__global__ void k_backward(DevView m, const float *__restrict__ q, const float *__restrict__ dist,
+                           const float *__restrict__ closest, const float4 *__restrict__ save,
+                           const float *__restrict__ gd, int64_t n, float *grad_q,
+                           float *grad_v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float d = dist[i], g = gd[i];
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+  const bool live = d > 0.f && isfinite(d);
+  if (live) {
+    const float inv = 1.f / d;
+    ux = (q[3 * i] - closest[3 * i]) * inv;
+    uy = (q[3 * i + 1] - closest[3 * i + 1]) * inv;
+    uz = (q[3 * i + 2] - closest[3 * i + 2]) * inv;
+  }
+  if (grad_q) {
+    grad_q[3 * i] = g * ux;
+    grad_q[3 * i + 1] = g * uy;
+    grad_q[3 * i + 2] = g * uz;
+  }
+  if (!grad_v || !live || g == 0.f) return;
+  const float4 s = save[i];
+  const uint32_t tid = __float_as_uint(s.x);
+  const uint32_t typ = tid >> 30, id = tid & 0x3fffffffu;
+  int vid[3] = {-1, -1, -1};
+  const float w[3] = {s.y, s.z, s.w};
+  if (typ == 0) {
+    vid[0] = (int)id;
+  } else if (typ == 1) {
+    const int2 e = __ldg(&m.edges[id]);
+    vid[0] = e.x;
+    vid[1] = e.y;
+  } else if (typ == 2) {
+    const int4 t = __ldg(&m.tris[id]);
+    vid[0] = t.x;
+    vid[1] = t.y;
+    vid[2] = t.z;
+  } else {
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (vid[k] < 0 || w[k] == 0.f) continue;
+    const float c = -g * w[k];
+    atomicAdd(&grad_v[3 * (size_t)vid[k]], c * ux);
+    atomicAdd(&grad_v[3 * (size_t)vid[k] + 1], c * uy);
+    atomicAdd(&grad_v[3 * (size_t)vid[k] + 2], c * uz);
+  }
+}
+
+// ----------------------------------------------------------------- a10
+// The mesh of a global query index: binary search of the query-count
+// prefix sums, kept in shared memory.
+__device__ __forceinline__ int mesh_of(const int64_t *qoff, int n_meshes, int64_t i) {
+  int lo = 0, hi = n_meshes;  // qoff[lo] <= i < qoff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (qoff[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kMaxBatchMeshes = 2048;
+
+__global__ void k_batch_count(BatchDesc d, int64_t total, int bits, uint32_t *__restrict__ hist,
+                              uint2 *__restrict__ key_rank) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = mesh_of(s_off, d.n_meshes, i);
+  const int64_t l = i - s_off[k];
+  const float *q = d.ios[k].q;
+  const DevView &m = d.views[k];
+  float inv[3];
+  for (int a = 0; a < 3; ++a) {
+    const float ext = m.dom_hi[a] - m.dom_lo[a];
+    inv[a] = ext > 0.f ? 1.f / ext : 0.f;
+  }
+  const uint32_t b = ((uint32_t)k << bits) |
+                     (bits ? morton_bucket(q[3 * l], q[3 * l + 1], q[3 * l + 2], m.dom_lo, inv,
+                                           30 - bits)
+                           : 0u);
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&hist[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+}
+
+__global__ void k_batch_scatter(BatchDesc d, int64_t total, const uint2 *__restrict__ key_rank,
+                                const uint32_t *__restrict__ off, float4 *__restrict__ sorted) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = mesh_of(s_off, d.n_meshes, i);
+  const int64_t l = i - s_off[k];
+  const float *q = d.ios[k].q;
+  const uint2 kr = key_rank[i];
+  sorted[off[kr.x] + kr.y] = make_float4(q[3 * l], q[3 * l + 1], q[3 * l + 2],
+                                         __int_as_float((int)i));
+}
+
+// Persistent CTAs drain the work queue: item t = sorted queries
+// [t*tile, (t+1)*tile).  The queue is one atomic counter, so no CTA ever
+// waits for another.
+__global__ void k_batch_query(BatchDesc d, const float4 *__restrict__ sorted, int64_t total,
+                              int tile, unsigned int *queue_head, unsigned int *error_word) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  __shared__ unsigned int s_item;
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  const int64_t n_items = (total + tile - 1) / tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(queue_head, 1u);
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= n_items) break;
+    const int64_t base = it * (int64_t)tile;
+    for (int t = threadIdx.x; t < tile; t += blockDim.x) {
+      const int64_t pos = base + t;
+      if (pos >= total) break;
+      const float4 s = sorted[pos];
+      const int64_t gi = __float_as_int(s.w);
+      if (gi < 0 || gi >= total) {
+        atomicOr(error_word, 1u);
+        continue;
+      }
+      const int k = mesh_of(s_off, d.n_meshes, gi);
+      const int64_t l = gi - s_off[k];
+      const BatchIO &io = d.ios[k];
+      Best r;
+      const bool ok = finite3(s.x, s.y, s.z);
+      if (ok) query_one(d.views[k], s.x, s.y, s.z, r);
+      store_result(l, r, ok, 0, io.dist, io.closest, io.prim_id, io.prim_type, nullptr, nullptr);
+    }
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t query_scratch_bytes(int64_t n, int sort_bits) {
+  size_t nb = sort_bits > 0 ? ((size_t)1 << sort_bits) : 0;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + 256;
+}
+
+cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
+                         float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
+                         uint8_t *status, void *scratch, size_t scratch_bytes,
+                         const QueryTuning &tune, cudaStream_t stream, cudaEvent_t *ev,
+                         unsigned long long *counters) {
+  if (n <= 0) return cudaSuccess;
+  if (scratch_bytes < query_scratch_bytes(n, tune.sort_bits)) return cudaErrorInvalidValue;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char *base = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  float4 *sorted = (float4 *)base;
+  base += al(16 * (size_t)n);
+  uint2 *key_rank = (uint2 *)base;
+  base += al(8 * (size_t)n);
+  const int T = 256;
+  if (ev) cudaEventRecord(ev[0], stream);
+  if (tune.sort_bits > 0) {
+    const size_t nb = (size_t)1 << tune.sort_bits;
+    uint32_t *hist = (uint32_t *)base;
+    base += al(4 * nb);
+    uint32_t *off = (uint32_t *)base;
+    SortParams sp;
+    for (int d = 0; d < 3; ++d) {
+      sp.lo[d] = m.dom_lo[d];
+      float ext = m.dom_hi[d] - m.dom_lo[d];
+      sp.inv[d] = ext > 0 ? 1.f / ext : 0.f;
+    }
+    sp.shift = 30 - tune.sort_bits;
+    cudaMemsetAsync(hist, 0, 4 * nb, stream);
+    k_bucket_count<<<blocks_for(n, T), T, 0, stream>>>(q, n, sp, hist, key_rank);
+    k_bucket_scan<<<1, 1024, 0, stream>>>(hist, off, (int)nb);
+    k_bucket_scatter<<<blocks_for(n, T), T, 0, stream>>>(q, n, key_rank, off, sorted);
+  } else {
+    k_identity<<<blocks_for(n, T), T, 0, stream>>>(q, n, sorted);
+  }
+  const int bt = tune.block_threads;
+  if (ev) cudaEventRecord(ev[1], stream);
+  if (counters) {
+    cudaMemsetAsync(counters, 0, 5 * sizeof(unsigned long long), stream);
+    k_query_count<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, counters);
+  } else {
+    k_query<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, dist, closest, prim_id,
+                                                  prim_type, save, status);
+  }
+  if (ev) cudaEventRecord(ev[2], stream);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
+                           cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_nearest<<<blocks_for(n, 128), 128, 0, stream>>>(m, xyz, n, out_pos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
+                            const float *closest, const float4 *save, const float *grad_dist,
+                            int64_t n, float *grad_q, float *grad_verts, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_backward<<<blocks_for(n, 256), 256, 0, stream>>>(m, q, dist, closest, save, grad_dist, n,
+                                                     grad_q, grad_verts);
+  return cudaGetLastError();
+}
+
+size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits) {
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nb = (size_t)n_meshes << sort_bits;
+  return al(16 * (size_t)total) + al(8 * (size_t)total) + 2 * al(4 * nb) + 256;
+}
+
+int batch_occupancy(int block_threads) {
+  int blocks = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_query, block_threads, 0);
+  return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_t scratch_bytes,
+                         const BatchTuning &t, int grid, unsigned int *queue_head,
+                         unsigned int *error_word, cudaStream_t stream) {
+  if (total <= 0) return cudaSuccess;
+  if (d.n_meshes > kMaxBatchMeshes || t.tile <= 0) return cudaErrorInvalidValue;
+  if (scratch_bytes < batch_scratch_bytes(total, d.n_meshes, t.sort_bits))
+    return cudaErrorInvalidValue;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char *base = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+  float4 *sorted = (float4 *)base;
+  base += al(16 * (size_t)total);
+  uint2 *key_rank = (uint2 *)base;
+  base += al(8 * (size_t)total);
+  const size_t nb = (size_t)d.n_meshes << t.sort_bits;
+  uint32_t *hist = (uint32_t *)base;
+  base += al(4 * nb);
+  uint32_t *off = (uint32_t *)base;
+  const int T = 256;
+  cudaMemsetAsync(hist, 0, 4 * nb, stream);
+  k_batch_count<<<blocks_for(total, T), T, 0, stream>>>(d, total, t.sort_bits, hist, key_rank);
+  k_bucket_scan<<<1, 1024, 0, stream>>>(hist, off, (int)nb);
+  k_batch_scatter<<<blocks_for(total, T), T, 0, stream>>>(d, total, key_rank, off, sorted);
+  cudaMemsetAsync(queue_head, 0, sizeof(unsigned int), stream);
+  k_batch_query<<<grid, t.block_threads, 0, stream>>>(d, sorted, total, t.tile, queue_head,
+                                                      error_word);
+  return cudaGetLastError();
+}
+
+}  // namespace p2m

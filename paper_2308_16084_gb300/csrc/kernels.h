@@ -1,0 +1,85 @@
+// kernels.h -- device layout view and the host-side launchers of the query
+// kernels (implemented in kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace p2m {
+
+// Read-only view of one mesh's device layout (see builder.h for formats).
+struct DevView {
+  const float4 *kd_nodes;   // (L-1) * 3: child boxes of every internal node
+  const float4 *kd_points;  // nv: x, y, z, original vertex id bits
+  const uint32_t *row_off;  // nv + 1
+  const float4 *entries;    // 2 per entry: {lo, typed id bits}, {hi, 0}
+  const float4 *edge_rec;   // 2 per edge
+  const float4 *face_rec;   // 3 per face
+  const int2 *edges;        // canonical edges
+  const int4 *tris;         // faces (a, b, c, 0)
+  int64_t nv;
+  int64_t L;                // KD-tree leaves (2^depth)
+  int depth;
+  float dom_lo[3], dom_hi[3];
+};
+
+// Launch configuration of the query path.
+struct QueryTuning {
+  int sort_bits = 18;
+  int block_threads = 256;
+};
+
+// Scratch needed by launch_query for n points, in bytes.
+size_t query_scratch_bytes(int64_t n, int sort_bits);
+
+// Morton bucket sort (a1) + fused query (a2..a8).  All pointers device.
+// ev (3 events or NULL) brackets the sort and the query kernel; with
+// `counters` (5 device u64) the counting variant runs instead of the query
+// and sums internal nodes, points, entries, edges and faces visited.
+cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
+                         float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
+                         uint8_t *status, void *scratch, size_t scratch_bytes,
+                         const QueryTuning &tune, cudaStream_t stream,
+                         cudaEvent_t *ev = nullptr, unsigned long long *counters = nullptr);
+
+// Nearest vertex (KD-tree position) of each point: used by the builder to
+// certify Voronoi cells.
+cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
+                           cudaStream_t stream);
+
+// Backward scatter (a9).
+cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
+                            const float *closest, const float4 *save, const float *grad_dist,
+                            int64_t n, float *grad_q, float *grad_verts, cudaStream_t stream);
+
+// Batched persistent query (a10): every mesh's queries in one Morton sort
+// keyed by (mesh, bucket), then one persistent kernel whose CTAs take tiles
+// of the sorted stream from an atomic counter.
+struct BatchIO {
+  const float *q;
+  int64_t n;
+  float *dist;
+  float *closest;
+  int32_t *prim_id;
+  uint8_t *prim_type;
+};
+struct BatchDesc {           // device pointers
+  const DevView *views;      // n_meshes
+  const BatchIO *ios;        // n_meshes
+  const int64_t *qoff;       // n_meshes + 1 prefix sums of the query counts
+  int n_meshes;
+};
+struct BatchTuning {
+  int sort_bits = 12;
+  int tile = 1024;
+  int block_threads = 256;
+  int grid_ctas = 0;
+};
+size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits);
+cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_t scratch_bytes,
+                         const BatchTuning &t, int grid, unsigned int *queue_head,
+                         unsigned int *error_word, cudaStream_t stream);
+// resident CTAs per SM of the persistent kernel for a block size
+int batch_occupancy(int block_threads);
+
+}  // namespace p2m

@@ -1,0 +1,823 @@
+// p2m_api.cu -- the extern "C" boundary of libp2m.so (include/p2m.h).
+//
+// Host glue only: argument checks, device memory of the handle, uploads,
+// and launches of the kernels in kernels.cu.  No query arithmetic happens
+// here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/p2m.h"
+#include "builder.h"
+#include "kernels.h"
+
+namespace {
+
+using p2m::DevView;
+using p2m::Layout;
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  ~DevBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t upload(const T *src, size_t count) {
+    reset();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    n = count;
+    return cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+  }
+};
+
+p2m_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return P2M_OK;
+  if (e == cudaErrorMemoryAllocation) return P2M_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return P2M_ERR_NO_DEVICE;
+  return P2M_ERR_CUDA;
+}
+
+bool have_device() {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
+}  // namespace
+
+struct p2m_handle {
+  int device = -1;          // -1: host-only handle (tables built, no queries)
+  Layout L;                 // host copy of the layout
+  DevBuf<float> kd_nodes, kd_points, entries, edge_rec, face_rec;
+  DevBuf<uint32_t> row_off;
+  DevBuf<int32_t> edges, tris;
+  DevView view{};
+  void *scratch = nullptr;  // query scratch arena
+  size_t scratch_bytes = 0;
+  p2m::QueryTuning tune;
+  size_t device_bytes = 0;
+  // timing ring: 3 events per recorded p2m_query
+  static constexpr int kRing = 1024;
+  std::vector<cudaEvent_t> ring;
+  int64_t ring_next = 0, ring_read = 0;
+  unsigned long long *counters = nullptr;
+
+  ~p2m_handle() {
+    if (scratch) cudaFree(scratch);
+    if (counters) cudaFree(counters);
+    for (auto &e : ring) cudaEventDestroy(e);
+  }
+
+  p2m_status ensure_scratch(size_t bytes) {
+    if (bytes <= scratch_bytes) return P2M_OK;
+    if (scratch) cudaFree(scratch);
+    scratch = nullptr;
+    scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&scratch, bytes);
+    if (e != cudaSuccess) {
+      scratch = nullptr;
+      return from_cuda(e);
+    }
+    scratch_bytes = bytes;
+    return P2M_OK;
+  }
+
+  void make_view() {
+    view.kd_nodes = (const float4 *)kd_nodes.p;
+    view.kd_points = (const float4 *)kd_points.p;
+    view.row_off = row_off.p;
+    view.entries = (const float4 *)entries.p;
+    view.edge_rec = (const float4 *)edge_rec.p;
+    view.face_rec = (const float4 *)face_rec.p;
+    view.edges = (const int2 *)edges.p;
+    view.tris = (const int4 *)tris.p;
+    view.nv = L.nv;
+    view.depth = L.kd_depth;
+    view.L = (int64_t)1 << L.kd_depth;
+    for (int d = 0; d < 3; ++d) {
+      view.dom_lo[d] = L.dom[d];
+      view.dom_hi[d] = L.dom[3 + d];
+    }
+  }
+
+  cudaError_t upload_tree() {
+    cudaError_t e = kd_nodes.upload(L.kd_nodes.data(), L.kd_nodes.size());
+    if (e == cudaSuccess) e = kd_points.upload(L.kd_points.data(), L.kd_points.size());
+    make_view();
+    return e;
+  }
+
+  cudaError_t upload_rest() {
+    cudaError_t e = row_off.upload(L.row_off.data(), L.row_off.size());
+    if (e == cudaSuccess) e = entries.upload(L.entries.data(), L.entries.size());
+    if (e == cudaSuccess) e = edge_rec.upload(L.edge_rec.data(), L.edge_rec.size());
+    if (e == cudaSuccess) e = face_rec.upload(L.face_rec.data(), L.face_rec.size());
+    if (e == cudaSuccess) e = edges.upload(L.edges.data(), L.edges.size());
+    if (e == cudaSuccess) e = tris.upload(L.tris.data(), L.tris.size());
+    make_view();
+    device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
+                        row_off.n + edges.n + tris.n);
+    return e;
+  }
+};
+
+namespace {
+
+// Nearest-vertex service for the builder: runs the device KD-tree search.
+struct DeviceNearest : p2m::NearestService {
+  p2m_handle *h;
+  explicit DeviceNearest(p2m_handle *hh) : h(hh) {}
+  bool query(const float *xyz, int64_t n, int32_t *out) override {
+    const int64_t chunk = 1 << 24;
+    float *dq = nullptr;
+    int32_t *dout = nullptr;
+    int64_t m = std::min(n, chunk);
+    if (cudaMalloc((void **)&dq, 12 * m) != cudaSuccess) return false;
+    if (cudaMalloc((void **)&dout, 4 * m) != cudaSuccess) {
+      cudaFree(dq);
+      return false;
+    }
+    bool ok = true;
+    for (int64_t s = 0; s < n && ok; s += chunk) {
+      int64_t k = std::min(chunk, n - s);
+      ok = cudaMemcpy(dq, xyz + 3 * s, 12 * k, cudaMemcpyHostToDevice) == cudaSuccess &&
+           p2m::launch_nearest(h->view, dq, k, dout, 0) == cudaSuccess &&
+           cudaMemcpy(out + s, dout, 4 * k, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    cudaFree(dq);
+    cudaFree(dout);
+    if (!ok) cudaGetLastError();
+    return ok;
+  }
+};
+
+// the builder fills the handle's own layout; once its KD tree exists the
+// tree goes to the device so the certification rounds can search it
+bool on_tree_cb(void *ctx, const Layout &) {
+  p2m_handle *h = (p2m_handle *)ctx;
+  return h->upload_tree() == cudaSuccess;
+}
+
+p2m_status check_ready(const p2m_handle *h) {
+  if (!h) return P2M_ERR_INVALID_ARG;
+  if (h->device < 0) return P2M_ERR_NO_DEVICE;
+  return P2M_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void p2m_default_opts(p2m_build_opts *o) {
+  if (!o) return;
+  o->domain_scale = 10.f;
+  o->domain_margin = 0.f;
+  o->delta_rel = 4e-6f;
+  o->host_threads = 0;
+  o->device_assist = 1;
+  o->leaf_size = 8;
+}
+
+const char *p2m_status_string(p2m_status s) {
+  switch (s) {
+    case P2M_OK: return "ok";
+    case P2M_ERR_INVALID_ARG: return "invalid argument";
+    case P2M_ERR_INVALID_MESH: return "invalid mesh";
+    case P2M_ERR_DUPLICATE_VERTEX: return "duplicate vertex position";
+    case P2M_ERR_OOM: return "out of memory";
+    case P2M_ERR_CUDA: return "CUDA error";
+    case P2M_ERR_QUEUE_TIMEOUT: return "work queue error";
+    case P2M_ERR_IO: return "I/O error";
+    case P2M_ERR_NO_DEVICE: return "no CUDA device";
+    case P2M_ERR_TOO_LARGE: return "size exceeds a limit";
+  }
+  return "unknown status";
+}
+
+p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out) {
+  if (!mesh || !out || !mesh->verts || !mesh->tris || mesh->n_verts < 0 || mesh->n_tris < 0)
+    return P2M_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (mesh->n_verts >= ((int64_t)1 << 30) || mesh->n_tris >= ((int64_t)1 << 29))
+    return P2M_ERR_TOO_LARGE;
+  p2m_build_opts o;
+  p2m_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.domain_scale > 0.f) || !(o.domain_margin >= 0.f) || !(o.delta_rel >= 0.f) ||
+      o.leaf_size < 2 || o.leaf_size > 32)
+    return P2M_ERR_INVALID_ARG;
+  std::unique_ptr<p2m_handle> h(new (std::nothrow) p2m_handle());
+  if (!h) return P2M_ERR_OOM;
+  if (have_device()) {
+    if (cudaGetDevice(&h->device) != cudaSuccess) return P2M_ERR_NO_DEVICE;
+  }
+  p2m::BuildParams prm;
+  prm.domain_scale = o.domain_scale;
+  prm.domain_margin = o.domain_margin;
+  prm.delta_rel = o.delta_rel;
+  prm.threads = o.host_threads;
+  prm.leaf_size = o.leaf_size;
+  DeviceNearest dn(h.get());
+  const bool assist = o.device_assist && h->device >= 0;
+  std::string err;
+  int st;
+  try {
+    st = p2m::build_layout(mesh->verts, mesh->n_verts, mesh->tris, mesh->n_tris, prm,
+                           assist ? &dn : nullptr, assist ? on_tree_cb : nullptr, h.get(), h->L,
+                           err);
+  } catch (const std::bad_alloc &) {
+    return P2M_ERR_OOM;
+  }
+  if (st) return (p2m_status)st;
+  if (h->device >= 0) {
+    cudaError_t e = h->upload_tree();
+    if (e == cudaSuccess) e = h->upload_rest();
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  *out = h.release();
+  return P2M_OK;
+}
+
+void p2m_destroy(p2m_handle *h) { delete h; }
+
+p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
+  if (!h || !t) return P2M_ERR_INVALID_ARG;
+  t->sort_bits = h->tune.sort_bits;
+  t->block_threads = h->tune.block_threads;
+  return P2M_OK;
+}
+
+p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
+  if (!h || !t || t->sort_bits < 0 || t->sort_bits > 24) return P2M_ERR_INVALID_ARG;
+  if (t->block_threads != 64 && t->block_threads != 128 && t->block_threads != 256 &&
+      t->block_threads != 512)
+    return P2M_ERR_INVALID_ARG;
+  h->tune.sort_bits = t->sort_bits;
+  h->tune.block_threads = t->block_threads;
+  return P2M_OK;
+}
+
+p2m_status p2m_reserve(p2m_handle *h, int64_t n) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  return h->ensure_scratch(p2m::query_scratch_bytes(n, 24) + 24 * (size_t)n + 4096);
+}
+
+p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
+                     int32_t *prim_id, uint8_t *prim_type, float *save, uint8_t *status,
+                     void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  size_t need = p2m::query_scratch_bytes(n, h->tune.sort_bits);
+  if ((s = h->ensure_scratch(need))) return s;
+  cudaEvent_t *ev = nullptr;
+  if (!h->ring.empty()) {
+    ev = &h->ring[3 * (h->ring_next % p2m_handle::kRing)];
+    ++h->ring_next;
+  }
+  return from_cuda(p2m::launch_query(h->view, q, n, dist, closest, prim_id, prim_type,
+                                     (float4 *)save, status, h->scratch, h->scratch_bytes,
+                                     h->tune, (cudaStream_t)stream, ev));
+}
+
+p2m_status p2m_set_timing(p2m_handle *h, int enable) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  for (auto &e : h->ring) cudaEventDestroy(e);
+  h->ring.clear();
+  h->ring_next = h->ring_read = 0;
+  if (enable) {
+    h->ring.resize(3 * p2m_handle::kRing, nullptr);
+    for (auto &e : h->ring)
+      if (cudaEventCreate(&e) != cudaSuccess) return P2M_ERR_CUDA;
+  }
+  return P2M_OK;
+}
+
+p2m_status p2m_timing_summary(p2m_handle *h, double out[3]) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (!out || h->ring.empty()) return P2M_ERR_INVALID_ARG;
+  out[0] = out[1] = out[2] = 0.0;
+  int64_t first = std::max(h->ring_read, h->ring_next - (int64_t)p2m_handle::kRing);
+  for (int64_t k = first; k < h->ring_next; ++k) {
+    cudaEvent_t *ev = &h->ring[3 * (k % p2m_handle::kRing)];
+    float a = 0, b = 0;
+    cudaError_t e = cudaEventSynchronize(ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (e != cudaSuccess) return from_cuda(e);
+    out[0] += 1.0;
+    out[1] += a;
+    out[2] += b;
+  }
+  h->ring_read = h->ring_next;
+  return P2M_OK;
+}
+
+p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[5],
+                              void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (!q || !out || n <= 0) return P2M_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  if ((s = h->ensure_scratch(p2m::query_scratch_bytes(n, h->tune.sort_bits)))) return s;
+  if (!h->counters && cudaMalloc((void **)&h->counters, 64) != cudaSuccess) return P2M_ERR_OOM;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p2m::launch_query(h->view, q, n, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                    nullptr, h->scratch, h->scratch_bytes, h->tune, st, nullptr,
+                                    h->counters);
+  unsigned long long c[5];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->counters, 40, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  for (int k = 0; k < 5; ++k) out[k] = (int64_t)c[k];
+  return P2M_OK;
+}
+
+p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
+                          int32_t *prim_id, uint8_t *prim_type, void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  // device staging lives in the scratch arena after the query's own part
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t need_q = p2m::query_scratch_bytes(n, h->tune.sort_bits);
+  size_t io = al(12 * (size_t)n) + al(4 * (size_t)n) + al(12 * (size_t)n) + al(4 * (size_t)n) +
+              al((size_t)n);
+  if ((s = h->ensure_scratch(al(need_q) + io + 256))) return s;
+  char *base = (char *)(((uintptr_t)h->scratch + 255) & ~(uintptr_t)255) + al(need_q);
+  float *dq = (float *)base;
+  base += al(12 * (size_t)n);
+  float *dd = (float *)base;
+  base += al(4 * (size_t)n);
+  float *dc = (float *)base;
+  base += al(12 * (size_t)n);
+  int32_t *dp = (int32_t *)base;
+  base += al(4 * (size_t)n);
+  uint8_t *dt = (uint8_t *)base;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dq, q, 12 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = p2m::launch_query(h->view, dq, n, dd, closest ? dc : nullptr, dp, prim_type ? dt : nullptr,
+                          nullptr, nullptr, h->scratch, al(need_q) + 256, h->tune, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dist, dd, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(prim_id, dp, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && closest)
+    e = cudaMemcpyAsync(closest, dc, 12 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && prim_type)
+    e = cudaMemcpyAsync(prim_type, dt, (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return from_cuda(e);
+}
+
+p2m_status p2m_backward(p2m_handle *h, const float *q, const float *dist, const float *closest,
+                        const float *save, const float *grad_dist, int64_t n, float *grad_q,
+                        float *grad_verts, void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !dist || !closest || !save || !grad_dist) return P2M_ERR_INVALID_ARG;
+  return from_cuda(p2m::launch_backward(h->view, q, dist, closest, (const float4 *)save,
+                                        grad_dist, n, grad_q, grad_verts, (cudaStream_t)stream));
+}
+
+p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges) {
+  if (!h || !n_edges) return P2M_ERR_INVALID_ARG;
+  *n_edges = h->L.ne;
+  if (edges) std::memcpy(edges, h->L.edges.data(), sizeof(int32_t) * 2 * h->L.ne);
+  return P2M_OK;
+}
+
+p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]) {
+  if (!h || !out) return P2M_ERR_INVALID_ARG;
+  const Layout &L = h->L;
+  out[0] = L.nv;
+  out[1] = L.nf;
+  out[2] = L.ne;
+  out[3] = L.n_entries;
+  out[4] = L.max_list;
+  out[5] = (int64_t)h->device_bytes;
+  out[6] = (int64_t)1 << L.kd_depth;
+  out[7] = L.kd_depth;
+  out[8] = L.neighbour_pairs;
+  out[9] = L.inspections;
+  out[10] = (int64_t)L.ms_total;
+  out[11] = (int64_t)L.ms_cells;
+  out[12] = (int64_t)L.ms_inspect;
+  out[13] = L.cert_rounds;
+  out[14] = L.cert_queries;
+  out[15] = L.n_degenerate;
+  return P2M_OK;
+}
+
+p2m_status p2m_domain(const p2m_handle *h, float out[7]) {
+  if (!h || !out) return P2M_ERR_INVALID_ARG;
+  for (int d = 0; d < 6; ++d) out[d] = h->L.dom[d];
+  out[6] = h->L.delta;
+  return P2M_OK;
+}
+
+p2m_status p2m_get_list(const p2m_handle *h, int32_t vertex, int32_t *types, int32_t *ids,
+                        float *boxes, int64_t cap, int64_t *len) {
+  if (!h || !len || vertex < 0 || vertex >= h->L.nv || cap < 0) return P2M_ERR_INVALID_ARG;
+  const Layout &L = h->L;
+  const int64_t row = L.pos_of_vertex[vertex];
+  const int64_t b = L.row_off[row], e = L.row_off[row + 1];
+  *len = e - b;
+  for (int64_t j = b; j < e && j - b < cap; ++j) {
+    uint32_t tid;
+    std::memcpy(&tid, &L.entries[8 * j + 3], 4);
+    if (types) types[j - b] = (int32_t)(tid >> 30);
+    if (ids) ids[j - b] = (int32_t)(tid & 0x3fffffffu);
+    if (boxes) {
+      for (int d = 0; d < 3; ++d) {
+        boxes[6 * (j - b) + d] = L.entries[8 * j + d];
+        boxes[6 * (j - b) + 3 + d] = L.entries[8 * j + 4 + d];
+      }
+    }
+  }
+  return P2M_OK;
+}
+
+// ---------------------------------------------------------------- batched
+}  // extern "C"
+
+struct p2m_batch {
+  int n = 0;
+  int64_t total = 0;
+  std::vector<p2m_handle *> meshes;
+  std::vector<p2m::BatchIO> io;
+  DevBuf<p2m::DevView> views;
+  DevBuf<p2m::BatchIO> ios;
+  DevBuf<int64_t> qoff;
+  DevBuf<unsigned int> words;  // [0] queue head, [1] error word
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  p2m::BatchTuning tune;
+  int sms = 0;
+  ~p2m_batch() {
+    if (scratch) cudaFree(scratch);
+  }
+  int grid() const {
+    if (tune.grid_ctas > 0) return tune.grid_ctas;
+    return sms * p2m::batch_occupancy(tune.block_threads);
+  }
+  p2m_status ensure(int sort_bits) {
+    size_t need = p2m::batch_scratch_bytes(total, n, sort_bits);
+    if (need <= scratch_bytes) return P2M_OK;
+    if (scratch) cudaFree(scratch);
+    scratch = nullptr;
+    scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&scratch, need);
+    if (e != cudaSuccess) {
+      scratch = nullptr;
+      return from_cuda(e);
+    }
+    scratch_bytes = need;
+    return P2M_OK;
+  }
+  p2m::BatchDesc desc() const {
+    return {views.p, ios.p, qoff.p, n};
+  }
+};
+
+extern "C" {
+
+p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, int n_meshes,
+                            p2m_batch **out) {
+  if (!meshes || !io || !out || n_meshes <= 0 || n_meshes > 2048) return P2M_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<p2m_batch> b(new (std::nothrow) p2m_batch());
+  if (!b) return P2M_ERR_OOM;
+  b->n = n_meshes;
+  std::vector<p2m::DevView> v(n_meshes);
+  std::vector<int64_t> off(n_meshes + 1, 0);
+  for (int k = 0; k < n_meshes; ++k) {
+    p2m_status s = check_ready(meshes[k]);
+    if (s) return s;
+    if (io[k].n < 0 || (io[k].n > 0 && (!io[k].q || !io[k].dist || !io[k].prim_id)))
+      return P2M_ERR_INVALID_ARG;
+    b->meshes.push_back(meshes[k]);
+    b->io.push_back({io[k].q, io[k].n, io[k].dist, io[k].closest, io[k].prim_id,
+                     io[k].prim_type});
+    v[k] = meshes[k]->view;
+    off[k + 1] = off[k] + io[k].n;
+  }
+  b->total = off[n_meshes];
+  if (b->total >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = b->views.upload(v.data(), v.size());
+  if (e == cudaSuccess) e = b->ios.upload(b->io.data(), b->io.size());
+  if (e == cudaSuccess) e = b->qoff.upload(off.data(), off.size());
+  unsigned int zero[2] = {0, 0};
+  if (e == cudaSuccess) e = b->words.upload(zero, 2);
+  if (e != cudaSuccess) return from_cuda(e);
+  p2m_status s = b->ensure(b->tune.sort_bits);
+  if (s) return s;
+  *out = b.release();
+  return P2M_OK;
+}
+
+p2m_status p2m_batch_run(p2m_batch *b, void *stream) {
+  if (!b) return P2M_ERR_INVALID_ARG;
+  if (b->scratch_bytes < p2m::batch_scratch_bytes(b->total, b->n, b->tune.sort_bits))
+    return P2M_ERR_INVALID_ARG;
+  return from_cuda(p2m::launch_batch(b->desc(), b->total, b->scratch, b->scratch_bytes, b->tune,
+                                     b->grid(), b->words.p, b->words.p + 1,
+                                     (cudaStream_t)stream));
+}
+
+p2m_status p2m_batch_get_tuning(const p2m_batch *b, p2m_batch_tuning *t) {
+  if (!b || !t) return P2M_ERR_INVALID_ARG;
+  t->sort_bits = b->tune.sort_bits;
+  t->tile = b->tune.tile;
+  t->block_threads = b->tune.block_threads;
+  t->grid_ctas = b->tune.grid_ctas;
+  return P2M_OK;
+}
+
+p2m_status p2m_batch_set_tuning(p2m_batch *b, const p2m_batch_tuning *t) {
+  if (!b || !t || t->sort_bits < 0 || t->sort_bits > 16 || t->grid_ctas < 0) return P2M_ERR_INVALID_ARG;
+  if (t->block_threads != 64 && t->block_threads != 128 && t->block_threads != 256 &&
+      t->block_threads != 512)
+    return P2M_ERR_INVALID_ARG;
+  if (t->tile <= 0 || t->tile % t->block_threads) return P2M_ERR_INVALID_ARG;
+  if (((int64_t)b->n << t->sort_bits) > ((int64_t)1 << 24)) return P2M_ERR_TOO_LARGE;
+  p2m_status s = b->ensure(t->sort_bits);
+  if (s) return s;
+  b->tune.sort_bits = t->sort_bits;
+  b->tune.tile = t->tile;
+  b->tune.block_threads = t->block_threads;
+  b->tune.grid_ctas = t->grid_ctas;
+  return P2M_OK;
+}
+
+p2m_status p2m_batch_check(p2m_batch *b, void *stream) {
+  if (!b) return P2M_ERR_INVALID_ARG;
+  unsigned int w[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpy(w, b->words.p, 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (w[1]) {
+    unsigned int zero = 0;
+    cudaMemcpy(b->words.p + 1, &zero, 4, cudaMemcpyHostToDevice);
+    return P2M_ERR_QUEUE_TIMEOUT;
+  }
+  return P2M_OK;
+}
+
+p2m_status p2m_batch_autotune(p2m_batch *b, int reps, void *stream, float *best_ms) {
+  if (!b || reps <= 0) return P2M_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return P2M_ERR_CUDA;
+  p2m::BatchTuning best = b->tune;
+  float bms = 1e30f;
+  const int bits_c[] = {8, 10, 12, 14};
+  const int tile_c[] = {256, 1024, 4096};
+  const int block_c[] = {128, 256};
+  p2m_status status = P2M_OK;
+  for (int bits : bits_c)
+    for (int tile : tile_c)
+      for (int bt : block_c) {
+        if (tile % bt) continue;
+        if (((int64_t)b->n << bits) > ((int64_t)1 << 22)) continue;
+        p2m_batch_tuning t{bits, tile, bt, 0};
+        if (p2m_batch_set_tuning(b, &t) != P2M_OK) continue;
+        if ((status = p2m_batch_run(b, st))) goto done;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+          if ((status = p2m_batch_run(b, st))) goto done;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < bms) {
+          bms = ms;
+          best = b->tune;
+        }
+      }
+done:
+  b->ensure(best.sort_bits);
+  b->tune = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms) *best_ms = bms;
+  return status;
+}
+
+void p2m_batch_destroy(p2m_batch *b) { delete b; }
+
+p2m_status p2m_query_batched(p2m_handle *const *meshes, const p2m_batch_io *io, int n_meshes,
+                             void *stream) {
+  p2m_batch *b = nullptr;
+  p2m_status s = p2m_batch_create(meshes, io, n_meshes, &b);
+  if (s) return s;
+  s = p2m_batch_run(b, stream);
+  if (s == P2M_OK) s = p2m_batch_check(b, stream);
+  p2m_batch_destroy(b);
+  return s;
+}
+
+p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void *stream,
+                        float *best_ms) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (!q || n <= 0 || reps <= 0) return P2M_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  float *dd = nullptr;
+  int32_t *dp = nullptr;
+  if (cudaMalloc((void **)&dd, 4 * n) != cudaSuccess) return P2M_ERR_OOM;
+  if (cudaMalloc((void **)&dp, 4 * n) != cudaSuccess) {
+    cudaFree(dd);
+    return P2M_ERR_OOM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  p2m::QueryTuning best = h->tune;
+  float bms = 1e30f;
+  const int bits_c[] = {0, 12, 15, 18, 21};
+  const int block_c[] = {128, 256, 512};
+  for (int bits : bits_c)
+    for (int bt : block_c) {
+      p2m_tuning t{bits, bt};
+      p2m_set_tuning(h, &t);
+      if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps; ++r)
+        if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < bms) {
+        bms = ms;
+        best = h->tune;
+      }
+    }
+done:
+  h->tune = best;
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(dd);
+  cudaFree(dp);
+  if (best_ms) *best_ms = bms;
+  return s;
+}
+
+// ---------------------------------------------------------------- save/load
+}  // extern "C"
+
+namespace {
+constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
+constexpr uint32_t kVersion = 1;
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+  const unsigned char *c = (const unsigned char *)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+template <class T>
+bool put_vec(FILE *f, const std::vector<T> &v, uint64_t &ck) {
+  uint64_t n = v.size();
+  ck = fnv1a(ck, &n, 8);
+  ck = fnv1a(ck, v.data(), n * sizeof(T));
+  return fwrite(&n, 8, 1, f) == 1 && (n == 0 || fwrite(v.data(), sizeof(T), n, f) == n);
+}
+template <class T>
+bool get_vec(FILE *f, std::vector<T> &v, uint64_t &ck) {
+  uint64_t n;
+  if (fread(&n, 8, 1, f) != 1 || n > ((uint64_t)1 << 40)) return false;
+  v.resize(n);
+  if (n && fread(v.data(), sizeof(T), n, f) != n) return false;
+  ck = fnv1a(ck, &n, 8);
+  ck = fnv1a(ck, v.data(), n * sizeof(T));
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+p2m_status p2m_save(const p2m_handle *h, const char *path) {
+  if (!h || !path) return P2M_ERR_INVALID_ARG;
+  FILE *f = fopen(path, "wb");
+  if (!f) return P2M_ERR_IO;
+  const Layout &L = h->L;
+  uint64_t ck = 1469598103934665603ull;
+  int64_t scal[12] = {L.nv, L.nf, L.ne, L.kd_depth, L.n_entries, L.max_list,
+                      L.neighbour_pairs, L.inspections, L.cert_rounds, L.cert_queries,
+                      L.n_degenerate, 0};
+  float fl[13];
+  std::memcpy(fl, L.dom, 24);
+  fl[6] = L.delta;
+  std::memcpy(fl + 7, L.kd_root, 24);
+  bool ok = fwrite(&kMagic, 8, 1, f) == 1 && fwrite(&kVersion, 4, 1, f) == 1 &&
+            fwrite(scal, 8, 12, f) == 12 && fwrite(fl, 4, 13, f) == 13;
+  ck = fnv1a(ck, scal, sizeof(scal));
+  ck = fnv1a(ck, fl, sizeof(fl));
+  ok = ok && put_vec(f, L.kd_nodes, ck) && put_vec(f, L.kd_points, ck) &&
+       put_vec(f, L.pos_of_vertex, ck) && put_vec(f, L.row_off, ck) && put_vec(f, L.entries, ck) &&
+       put_vec(f, L.edge_rec, ck) && put_vec(f, L.face_rec, ck) && put_vec(f, L.edges, ck) &&
+       put_vec(f, L.tris, ck);
+  ok = ok && fwrite(&ck, 8, 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  return ok ? P2M_OK : P2M_ERR_IO;
+}
+
+p2m_status p2m_load(const char *path, p2m_handle **out) {
+  if (!path || !out) return P2M_ERR_INVALID_ARG;
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) return P2M_ERR_IO;
+  std::unique_ptr<p2m_handle> h(new (std::nothrow) p2m_handle());
+  if (!h) {
+    fclose(f);
+    return P2M_ERR_OOM;
+  }
+  Layout &L = h->L;
+  uint64_t magic = 0, ck = 1469598103934665603ull, stored = 0;
+  uint32_t ver = 0;
+  int64_t scal[12];
+  float fl[13];
+  bool ok = fread(&magic, 8, 1, f) == 1 && magic == kMagic && fread(&ver, 4, 1, f) == 1 &&
+            ver == kVersion && fread(scal, 8, 12, f) == 12 && fread(fl, 4, 13, f) == 13;
+  if (ok) {
+    ck = fnv1a(ck, scal, sizeof(scal));
+    ck = fnv1a(ck, fl, sizeof(fl));
+    ok = get_vec(f, L.kd_nodes, ck) && get_vec(f, L.kd_points, ck) &&
+         get_vec(f, L.pos_of_vertex, ck) && get_vec(f, L.row_off, ck) &&
+         get_vec(f, L.entries, ck) && get_vec(f, L.edge_rec, ck) && get_vec(f, L.face_rec, ck) &&
+         get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && fread(&stored, 8, 1, f) == 1 &&
+         stored == ck;
+  }
+  fclose(f);
+  if (!ok) return P2M_ERR_IO;
+  L.nv = scal[0];
+  L.nf = scal[1];
+  L.ne = scal[2];
+  L.kd_depth = (int)scal[3];
+  L.n_entries = scal[4];
+  L.max_list = scal[5];
+  L.neighbour_pairs = scal[6];
+  L.inspections = scal[7];
+  L.cert_rounds = scal[8];
+  L.cert_queries = scal[9];
+  L.n_degenerate = scal[10];
+  std::memcpy(L.dom, fl, 24);
+  L.delta = fl[6];
+  std::memcpy(L.kd_root, fl + 7, 24);
+  if ((int64_t)L.row_off.size() != L.nv + 1 || (int64_t)L.kd_points.size() != 4 * L.nv ||
+      (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne)
+    return P2M_ERR_IO;
+  if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
+    cudaError_t e = h->upload_tree();
+    if (e == cudaSuccess) e = h->upload_rest();
+    if (e != cudaSuccess) return from_cuda(e);
+  } else {
+    h->device = -1;
+  }
+  *out = h.release();
+  return P2M_OK;
+}
+
+}  // extern "C"

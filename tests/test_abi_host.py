@@ -1,0 +1,164 @@
+"""The C ABI library on the CPU: it loads, exports every entry point that
+include/p2m.h declares, validates meshes, and its host builder produces the
+same interception table as the oracle (two independent implementations of
+Alg. A.1).  No compute call needs a GPU here."""
+import ctypes
+import os
+import re
+import tempfile
+
+import numpy as np
+import pytest
+
+import datagen as dg
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from paper_2308_16084_gb300 import build
+    build.build()
+    import paper_2308_16084_gb300 as m
+    return m
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "p2m.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(p2m_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(pg):
+    lib = ctypes.CDLL(pg.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2308_16084_gb300 import _lib
+    assert set(names) == set(_lib.EXPORTED)
+
+
+def test_status_strings(pg):
+    for code in range(10):
+        s = pg.lib.p2m_status_string(code)
+        assert s and s != b"unknown status"
+
+
+def _host(pg, m, **kw):
+    return pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
+                  device_assist=False, **kw)
+
+
+@pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 4}), (2, {"grid": 40}),
+                                    (3, {"level": 4})])
+def test_builder_tables_equal_oracle_tables(pg, idx, kw):
+    m = dg.workload(idx, n_queries=10, **kw)
+    h = _host(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    np.testing.assert_array_equal(h.edges(), o.edges())
+    st = h.stats()
+    assert st["n_entries"] == o.n_entries
+    assert st["neighbour_pairs"] == o.n_neighbor_pairs
+    off, tt, ii, bb = o.table()
+    delta = h.domain()[2]
+    assert abs(delta - o.delta) <= 1e-6 * o.delta
+    for v in range(o.nv):
+        t, i, b = h.interception_list(v)
+        a = set(zip(t.tolist(), i.tolist()))
+        r = set(zip(tt[off[v]:off[v + 1]].tolist(), ii[off[v]:off[v + 1]].tolist()))
+        assert a == r, v
+        # float32 Region boxes contain the oracle's FP64 boxes, up to the
+        # scatter of two independent computations of crossing points, which
+        # near tangential crossings is of order sqrt(eps) and stays far below
+        # the delta padding of every box
+        order_r = np.lexsort((ii[off[v]:off[v + 1]], tt[off[v]:off[v + 1]]))
+        order_a = np.lexsort((i, t))
+        ob = bb[off[v]:off[v + 1]][order_r]
+        hb = b[order_a].astype(np.float64)
+        tol = 1e-2 * delta
+        assert (hb[:, :3] <= ob[:, :3] + tol).all() and (hb[:, 3:] >= ob[:, 3:] - tol).all()
+
+
+def test_builder_thread_count_does_not_change_tables(pg):
+    m = dg.workload(3, n_queries=10, level=3)
+    a = _host(pg, m, host_threads=1)
+    b = _host(pg, m, host_threads=5)
+    for v in range(0, a.n_verts, 3):
+        ta, ia, ba = a.interception_list(v)
+        tb, ib, bb = b.interception_list(v)
+        np.testing.assert_array_equal(ta, tb)
+        np.testing.assert_array_equal(ia, ib)
+        np.testing.assert_array_equal(ba, bb)
+
+
+@pytest.mark.parametrize("case,code", [("index", 2), ("repeat", 2), ("dup", 3), ("unref", 2),
+                                       ("nan", 2), ("empty", 2)])
+def test_invalid_meshes_return_status(pg, case, code):
+    V, F = dg.octahedron()
+    V = V.astype(np.float32)
+    F = F.astype(np.int32)
+    if case == "index":
+        F = F.copy(); F[0, 0] = 99
+    elif case == "repeat":
+        F = F.copy(); F[0, 1] = F[0, 0]
+    elif case == "dup":
+        V = np.concatenate([V, V[:1]]); F = np.concatenate([F, [[6, 2, 4]]]).astype(np.int32)
+    elif case == "unref":
+        V = np.concatenate([V, [[5, 5, 5]]]).astype(np.float32)
+    elif case == "nan":
+        V = V.copy(); V[0, 0] = np.nan
+    elif case == "empty":
+        F = np.zeros((0, 3), np.int32)
+    with pytest.raises(pg.P2MError) as e:
+        pg.P2M(V, F, device_assist=False)
+    assert e.value.code == code
+
+
+def test_bad_options_rejected(pg):
+    V, F = dg.octahedron()
+    for kw in ({"domain_scale": 0.0}, {"leaf_size": 1}, {"leaf_size": 64}, {"delta_rel": -1.0}):
+        with pytest.raises(pg.P2MError) as e:
+            pg.P2M(V.astype(np.float32), F.astype(np.int32), device_assist=False, **kw)
+        assert e.value.code == 1
+
+
+def test_save_load_roundtrip_and_corruption(pg):
+    m = dg.workload(0, n_queries=10, level=2)
+    h = _host(pg, m)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "m.p2m")
+        h.save(p)
+        g = pg.P2M.load(p)
+        assert g.stats()["n_entries"] == h.stats()["n_entries"]
+        for v in range(h.n_verts):
+            for x, y in zip(h.interception_list(v), g.interception_list(v)):
+                np.testing.assert_array_equal(x, y)
+        raw = bytearray(open(p, "rb").read())
+        for pos in (3, 100, len(raw) // 2, len(raw) - 3):
+            bad = bytearray(raw)
+            bad[pos] ^= 0x5A
+            open(p, "wb").write(bad)
+            with pytest.raises(pg.P2MError) as e:
+                pg.P2M.load(p)
+            assert e.value.code == 7
+        open(p, "wb").write(raw[: len(raw) // 3])
+        with pytest.raises(pg.P2MError):
+            pg.P2M.load(p)
+    with pytest.raises(pg.P2MError):
+        pg.P2M.load("/nonexistent/file.p2m")
+
+
+def test_queries_on_host_only_handle_fail_loudly(pg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = dg.workload(0, n_queries=10, level=1)
+    h = _host(pg, m)
+    n = 4
+    dist = np.zeros(n, np.float32)
+    pid = np.zeros(n, np.int32)
+    with pytest.raises(pg.P2MError) as e:
+        h.query_host(np.zeros((n, 3), np.float32), dist, pid)
+    assert e.value.code == 8

@@ -1,0 +1,303 @@
+"""Parity of the CUDA query path (through the C ABI) against the FP64 oracle.
+
+Every case compares element by element on the same seeded inputs with the
+criterion of parity_util (tau = 1e-5 x bbox diagonal).  Sizes span many
+KD-tree leaves, many query tiles and a ragged tail; the full-size workloads
+are checked on sampled outputs the oracle computes one by one.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import datagen as dg
+import oracle
+from tests import parity_util as pu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    import paper_2308_16084_gb300 as m
+    return m
+
+
+def run(mesh, q_np, **kw):
+    q = torch.from_numpy(np.ascontiguousarray(q_np, np.float32)).cuda()
+    r = mesh.query(q, closest=True, prim_type=True, status=True, **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def build(pg, m, **kw):
+    return pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin, **kw)
+
+
+CASES = [(0, {}, None), (1, {"level": 5}, 60000), (2, {"grid": 128}, 60000),
+         (3, {"level": 5}, 60000), (1, {"level": 3}, 30001)]
+
+
+@pytest.mark.parametrize("idx,kw,n", CASES)
+def test_parity_workloads(pg, idx, kw, n):
+    m = dg.workload(idx, n_queries=n, **kw)
+    mesh = build(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    np.testing.assert_array_equal(mesh.edges(), o.edges())
+    ref = o.bruteforce(m.queries)
+    gpu = run(mesh, m.queries)
+    tau = pu.tolerance(m.verts)
+    s = pu.check(m.verts, o.edges(), m.tris, m.queries, gpu, ref, tau, f"workload {idx} {kw}")
+    assert s["prim_exact"] > 0.999
+    lo, hi, _ = mesh.domain()
+    outside = ((m.queries < lo) | (m.queries > hi)).any(1)
+    np.testing.assert_array_equal((gpu["status"] & 1) == 1, outside)
+
+
+def test_parity_against_paper_method(pg):
+    """The GPU agrees with the oracle's own P2M query (Alg. A.2) too, and the
+    product builder's interception lists equal the oracle's."""
+    m = dg.workload(3, n_queries=40000, level=4)
+    mesh = build(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    ref = o.query(m.queries, use_boxes=True)
+    ref["second"] = o.bruteforce(m.queries)["second"]
+    gpu = run(mesh, m.queries)
+    pu.check(m.verts, o.edges(), m.tris, m.queries, gpu, ref, pu.tolerance(m.verts), "P2M")
+    off, tt, ii, _ = o.table()
+    for v in range(0, o.nv, 7):
+        t, i, _ = mesh.interception_list(v)
+        assert set(zip(t.tolist(), i.tolist())) == \
+            set(zip(tt[off[v]:off[v + 1]].tolist(), ii[off[v]:off[v + 1]].tolist()))
+
+
+@pytest.mark.parametrize("bits", [0, 6, 12, 18, 24])
+@pytest.mark.parametrize("threads", [64, 128, 256, 512])
+def test_tunings_give_identical_results(pg, bits, threads):
+    m = dg.workload(0, n_queries=50001)
+    mesh = build(pg, m)
+    base = run(mesh, m.queries)
+    mesh.tuning = {"sort_bits": bits, "block_threads": threads}
+    got = run(mesh, m.queries)
+    for k in ("dist", "closest", "prim_id", "prim_type", "status"):
+        np.testing.assert_array_equal(got[k], base[k])
+
+
+def test_edge_cases(pg):
+    m = dg.workload(0, n_queries=10)
+    mesh = build(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    tau = pu.tolerance(m.verts)
+    # empty
+    q0 = torch.zeros(0, 3, device="cuda")
+    r0 = mesh.query(q0)
+    assert r0["dist"].numel() == 0
+    # single, ragged, exact vertex, exact edge midpoint, far away
+    V = m.verts.astype(np.float64)
+    E = o.edges()
+    special = np.concatenate([
+        m.verts[:5],
+        (0.5 * (V[E[:5, 0]] + V[E[:5, 1]])).astype(np.float32),
+        np.array([[50, 50, 50], [-3, 0.1, 0.2]], np.float32)])
+    for q in (special[:1], special, np.repeat(special, 37, 0)[:257]):
+        gpu = run(mesh, q)
+        ref = o.bruteforce(q)
+        pu.check(m.verts, E, m.tris, q, gpu, ref, tau, "special")
+    gpu = run(mesh, special)
+    assert (gpu["dist"][:5] == 0).all() and (gpu["prim_type"][:5] == pg.VERTEX).all()
+    np.testing.assert_array_equal(gpu["prim_id"][:5], np.arange(5))
+    assert (gpu["status"][-2] & pg.Q_OUTSIDE_DOMAIN)
+    # non-finite inputs: NaN outputs, id -1, status bit
+    bad = np.array([[np.nan, 0, 0], [0, np.inf, 0], [0.1, 0.2, 0.3]], np.float32)
+    gpu = run(mesh, bad)
+    assert np.isnan(gpu["dist"][:2]).all() and (gpu["prim_id"][:2] == -1).all()
+    assert (gpu["status"][:2] & pg.Q_NONFINITE).all() and np.isfinite(gpu["dist"][2])
+
+
+def test_determinism_and_save_load(pg):
+    m = dg.workload(2, n_queries=40000, grid=64)
+    mesh = build(pg, m)
+    a = run(mesh, m.queries)
+    b = run(mesh, m.queries)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "mesh.p2m")
+        mesh.save(path)
+        mesh2 = pg.P2M.load(path)
+        c = run(mesh2, m.queries)
+        for k in a:
+            np.testing.assert_array_equal(a[k], c[k])
+        with open(path, "r+b") as f:
+            f.seek(200)
+            byte = f.read(1)
+            f.seek(200)
+            f.write(bytes([byte[0] ^ 0xFF]))
+        with pytest.raises(pg.P2MError, match="I/O"):
+            pg.P2M.load(path)
+
+
+def test_host_api_matches_device_api(pg):
+    m = dg.workload(0, n_queries=30000)
+    mesh = build(pg, m)
+    dev = run(mesh, m.queries)
+    n = m.queries.shape[0]
+    dist = np.zeros(n, np.float32)
+    pid = np.zeros(n, np.int32)
+    cp = np.zeros((n, 3), np.float32)
+    pt = np.zeros(n, np.uint8)
+    mesh.query_host(m.queries, dist, pid, cp, pt)
+    np.testing.assert_array_equal(dist, dev["dist"])
+    np.testing.assert_array_equal(pid, dev["prim_id"])
+    np.testing.assert_array_equal(cp, dev["closest"])
+    np.testing.assert_array_equal(pt, dev["prim_type"])
+
+
+# ------------------------------------------------------------------ backward
+
+def test_backward_against_oracle_gradient(pg):
+    """grad_q = w (q-c)/d and grad_v_k = -w b_k (q-c)/d (Eq. of the
+    distance's derivative) against the oracle's FP64 analytic gradient."""
+    m = dg.workload(3, n_queries=50000, level=5)
+    mesh = build(pg, m)
+    q = torch.from_numpy(m.queries).cuda().requires_grad_(True)
+    verts = torch.from_numpy(m.verts).cuda().requires_grad_(True)
+    w = torch.from_numpy(m.weights).cuda()
+    d, pid = pg.distance(q, verts, mesh)
+    (w * d).sum().backward()
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries)
+    gq_ref, bv, gv = oracle.gradient(m.queries.astype(np.float64), ref, m.weights.astype(np.float64))
+    keep = (ref["dist"] > 1e-4) & (ref["second"] - ref["dist"] > 1e-4)
+    gq = q.grad.cpu().numpy()
+    assert np.abs(gq[keep] - gq_ref[keep]).max() < 2e-3
+    # vertex gradient: scatter the oracle's per-query contributions of the
+    # same (non-tie) queries and compare with a second GPU pass on them
+    qs = torch.from_numpy(m.queries[keep]).cuda()
+    ws = torch.from_numpy(m.weights[keep]).cuda()
+    v2 = torch.from_numpy(m.verts).cuda().requires_grad_(True)
+    d2, _ = pg.distance(qs, v2, mesh)
+    (ws * d2).sum().backward()
+    gv_ref = np.zeros((m.verts.shape[0], 3))
+    bvk, gvk = bv[keep], gv[keep]
+    for s in range(3):
+        ok = bvk[:, s] >= 0
+        np.add.at(gv_ref, bvk[ok, s], gvk[ok, s])
+    err = np.abs(v2.grad.cpu().numpy() - gv_ref).max()
+    assert err < 1e-3 * max(1.0, np.abs(gv_ref).max()), err
+
+
+def test_backward_against_finite_differences(pg):
+    """FP64 central differences (h = 1e-6) of the oracle's brute-force
+    distance on 1k points away from ties and from d = 0."""
+    m = dg.workload(3, n_queries=4000, level=4)
+    mesh = build(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries)
+    keep = np.nonzero((ref["dist"] > 1e-3) & (ref["second"] - ref["dist"] > 1e-3))[0][:1000]
+    qn = m.queries[keep]
+    q = torch.from_numpy(qn).cuda().requires_grad_(True)
+    verts = torch.from_numpy(m.verts).cuda()
+    d, _ = pg.distance(q, verts, mesh)
+    d.sum().backward()
+    gq = q.grad.cpu().numpy()
+    h = 1e-6
+    q64 = qn.astype(np.float64)
+    fd = np.zeros_like(q64)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd[:, k] = (o.bruteforce(q64 + e)["dist"] - o.bruteforce(q64 - e)["dist"]) / (2 * h)
+    assert np.abs(gq - fd).max() < 2e-3
+
+
+# ------------------------------------------------------------------- batched
+
+def _batch_meshes(pg, n_meshes=6):
+    ms = dg.batch_workload(n_meshes, tri_range=(1e3, 3e4), query_range=(1e3, 3e4))
+    meshes = [build(pg, m) for m in ms]
+    return ms, meshes
+
+
+def test_batched_matches_single_and_oracle(pg):
+    ms, meshes = _batch_meshes(pg)
+    qs = [torch.from_numpy(m.queries).cuda() for m in ms]
+    b = pg.P2MBatch(meshes, qs, closest=True, prim_type=True)
+    out = b.run()
+    b.check()
+    torch.cuda.synchronize()
+    for m, mesh, r in zip(ms, meshes, out):
+        single = run(mesh, m.queries)
+        np.testing.assert_array_equal(r["dist"].cpu().numpy(), single["dist"])
+        np.testing.assert_array_equal(r["prim_id"].cpu().numpy(), single["prim_id"])
+        o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+        sel = np.arange(0, m.queries.shape[0], 5)
+        ref = o.bruteforce(m.queries[sel])
+        got = {k: v.cpu().numpy()[sel] for k, v in r.items()}
+        pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts),
+                 m.name)
+
+
+def test_batched_autotune_and_graph_replay(pg):
+    ms, meshes = _batch_meshes(pg, 4)
+    qs = [torch.from_numpy(m.queries).cuda() for m in ms]
+    b = pg.P2MBatch(meshes, qs)
+    ref = [r["dist"].clone() for r in b.run()]
+    ms_best = b.autotune(reps=2)
+    assert ms_best > 0
+    for r in b.out:
+        r["dist"].zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    for r in b.out:
+        r["dist"].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    b.check()
+    for r, d0 in zip(b.out, ref):
+        assert torch.equal(r["dist"], d0)
+
+
+# ------------------------------------------------------- full-size workloads
+
+@pytest.fixture(scope="module")
+def full1(pg):
+    m = dg.workload(1)
+    mesh = build(pg, m)
+    return m, mesh
+
+
+def test_full_size_displaced_sphere_sampled(pg, full1):
+    """1.3M triangles, 10M queries in the launch configuration the benchmark
+    times: every output obeys the invariants, 3000 sampled outputs match the
+    brute-force oracle."""
+    m, mesh = full1
+    q = torch.from_numpy(m.queries).cuda()
+    r = mesh.query(q, closest=True, prim_type=True, save=True)
+    torch.cuda.synchronize()
+    d = r["dist"]
+    assert torch.isfinite(d).all()
+    assert torch.allclose(torch.linalg.norm(q - r["closest"], dim=1), d, atol=1e-5, rtol=1e-5)
+    wts = r["save"][:, 1:]
+    assert (wts >= -1e-6).all() and torch.allclose(wts.sum(1), torch.ones_like(d), atol=1e-5)
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(m.queries.shape[0], 3000, replace=False))
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries[sel])
+    got = {"dist": d.cpu().numpy()[sel], "prim_id": r["prim_id"].cpu().numpy()[sel],
+           "prim_type": r["prim_type"].cpu().numpy()[sel],
+           "closest": r["closest"].cpu().numpy()[sel]}
+    pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts), "full1")
+    # d <= distance to the nearest vertex (Alg. A.2 initialisation)
+    nn, _ = o.kdt_nn(m.queries[sel])
+    dv = np.linalg.norm(m.queries[sel].astype(np.float64) - m.verts[nn].astype(np.float64), axis=1)
+    assert (got["dist"] <= dv + pu.tolerance(m.verts)).all()
