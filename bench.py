@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--level", type=int, default=None, help="smaller mesh (profiling only)")
     ap.add_argument("--queries", type=int, default=None, help="fewer queries (profiling only)")
+    ap.add_argument("--layout", default=None,
+                    help="load the built layout from this file if it exists, else build and "
+                         "save it there")
     return ap.parse_args()
 
 
@@ -237,11 +240,15 @@ def run_ours(args):
     # build once (rank 0), share the layout file with the other replicas
     t0 = time.perf_counter()
     layout = os.path.join("/tmp", f"p2m_bench_{os.getpid() if world == 1 else 'shared'}.p2m")
-    if rank == 0:
+    if args.layout and os.path.exists(args.layout):
+        mesh = pg.P2M.load(args.layout)
+    elif rank == 0:
         mesh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
         if world > 1:
             mesh.save(layout)
-    if world > 1:
+        if args.layout:
+            mesh.save(args.layout)
+    if world > 1 and not (args.layout and os.path.exists(args.layout)):
         dist.barrier()
         if rank != 0:
             mesh = pg.P2M.load(layout)

@@ -115,6 +115,13 @@ p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, floa
                      int32_t *prim_id, uint8_t *prim_type, float *save, uint8_t *status,
                      void *stream);
 
+/* Nearest mesh vertex of each of n device points (the KD-tree search of
+ * Alg. A.2, first line): vertex[i] = original vertex id, -1 for a
+ * non-finite point.  Ties between equidistant vertices may go either way
+ * within float32 rounding.  Errors: INVALID_ARG, CUDA, TOO_LARGE. */
+p2m_status p2m_nearest_vertex(p2m_handle *h, const float *q, int64_t n, int32_t *vertex,
+                              void *stream);
+
 /* Same as p2m_query with HOST buffers: copies q in, runs, copies results out,
  * synchronises `stream` before returning (dist/prim_id required, others may
  * be NULL). */
@@ -124,10 +131,21 @@ p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist,
 /* Launch tuning of the query path (chosen by the autotuner or by hand).
  *   sort_bits      Morton bucket bits of the query sort, 0..24 (0 = no sort);
  *                  queries are grouped into 2^sort_bits spatial buckets
- *   block_threads  threads per CTA of the query kernel: 64, 128, 256 or 512 */
+ *   block_threads  threads per CTA of the query kernel: 64, 128, 256 or 512
+ *   warp_cooperative  0: one thread per query; 1: a warp answers 32 sorted
+ *                  queries together (shared KD-tree walk decided by ballots,
+ *                  each distinct interception list staged once through
+ *                  shared memory).  Results are identical.
+ *   nn_walk        nearest-vertex search: 0 = KD-tree descent with
+ *                  backtracking (Sec. 2.1); 1 = KD-tree descent to one leaf,
+ *                  then a walk over Voronoi neighbours to the nearest vertex
+ *                  (exact: a vertex nearer than all its Voronoi neighbours is
+ *                  the nearest; points outside D use backtracking). */
 typedef struct {
   int sort_bits;
   int block_threads;
+  int warp_cooperative;
+  int nn_walk;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);

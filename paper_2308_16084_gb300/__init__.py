@@ -32,7 +32,8 @@ class MeshDesc(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int)]
+    _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int)]
 
 
 class BatchIO(ctypes.Structure):
@@ -146,13 +147,15 @@ class P2M:
     def tuning(self):
         t = Tuning()
         check(lib.p2m_get_tuning(self._h, ctypes.byref(t)), "p2m_get_tuning")
-        return {"sort_bits": t.sort_bits, "block_threads": t.block_threads}
+        return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
+                "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
-        t = Tuning(cur["sort_bits"], cur["block_threads"])
+        t = Tuning(cur["sort_bits"], cur["block_threads"], cur["warp_cooperative"],
+                   cur["nn_walk"])
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):
@@ -208,6 +211,14 @@ class P2M:
                             _ptr(r["prim_id"]), _ptr(r.get("prim_type")), _ptr(r.get("save")),
                             _ptr(r.get("status")), _stream(stream)), "p2m_query")
         return r
+
+    def nearest_vertex(self, q, stream=None):
+        """Nearest vertex id of each point of a (N,3) float32 CUDA tensor."""
+        import torch
+        out = torch.empty(q.shape[0], dtype=torch.int32, device=q.device)
+        check(lib.p2m_nearest_vertex(self._h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)),
+              "p2m_nearest_vertex")
+        return out
 
     def query_host(self, q, dist, prim_id, closest=None, prim_type=None, stream=None):
         """End-to-end query on HOST buffers (numpy or pinned CPU tensors):

@@ -737,6 +737,11 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   cells.shrink_to_fit();
   int64_t npairs = 0;
   for (auto &nb : nbr) npairs += (int64_t)nb.size();
+  out.nb_off.assign(nv + 1, 0);
+  for (int64_t p = 0; p < nv; ++p) out.nb_off[p + 1] = out.nb_off[p] + (uint32_t)nbr[p].size();
+  out.nb.resize(npairs);
+  for (int64_t p = 0; p < nv; ++p)
+    for (size_t k = 0; k < nbr[p].size(); ++k) out.nb[out.nb_off[p] + k] = (uint32_t)nbr[p][k];
   const double t_flood = now_ms();
 
   // ---- flooding inspection (Alg. 1) over every edge and every face

@@ -46,6 +46,10 @@ struct Layout {
   std::vector<float> kd_points;   // nv * 4: x, y, z, original vertex id (int bits)
   float kd_root[6] = {0, 0, 0, 0, 0, 0};
   std::vector<int32_t> pos_of_vertex;   // original id -> tree position (= table row)
+  // Voronoi neighbours of every vertex, as tree positions (CSR by row): the
+  // generators of the bisector faces of its exact cell clipped to D
+  std::vector<uint32_t> nb_off;    // nv + 1
+  std::vector<uint32_t> nb;
   // interception table, rows in tree order
   std::vector<uint32_t> row_off;   // nv + 1
   // entry: {lo.x, lo.y, lo.z, typed id bits}, {hi.x, hi.y, hi.z, 0}

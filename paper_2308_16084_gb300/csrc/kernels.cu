@@ -125,6 +125,82 @@ __device__ __forceinline__ int nearest_pos(const DevView &m, float qx, float qy,
   return best;
 }
 
+
+// Nearest vertex by KD descent + Voronoi walk.  The descent follows the
+// child whose box is nearer to q down to one leaf and keeps its nearest
+// vertex.  The walk then moves to any Voronoi neighbour nearer to q (the
+// nearest of them), until none is: a vertex nearer to q than every Voronoi
+// neighbour is the nearest vertex, because the bisectors of its neighbours
+// bound its cell.  The neighbour graph holds inside the domain D only, so
+// points outside D, and walks that exceed the step cap, use the full
+// backtracking search instead.
+constexpr int kWalkCap = 256;
+
+template <bool COUNT = false>
+__device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy, float qz,
+                                            Work *wk = nullptr) {
+  const bool inside = qx >= m.dom_lo[0] && qy >= m.dom_lo[1] && qz >= m.dom_lo[2] &&
+                      qx <= m.dom_hi[0] && qy <= m.dom_hi[1] && qz <= m.dom_hi[2];
+  if (!inside) return nearest_pos<COUNT>(m, qx, qy, qz, wk);
+  const int64_t nleaf0 = m.L - 1;
+  int node = 0;
+  while (node < nleaf0) {
+    if (COUNT) ++wk->nodes;
+    const float4 A = __ldg(&m.kd_nodes[3 * node + 0]);
+    const float4 B = __ldg(&m.kd_nodes[3 * node + 1]);
+    const float4 C = __ldg(&m.kd_nodes[3 * node + 2]);
+    const float d0 = box_d2(qx, qy, qz, A.x, A.y, A.z, A.w, B.x, B.y);
+    const float d1 = box_d2(qx, qy, qz, B.z, B.w, C.x, C.y, C.z, C.w);
+    node = 2 * node + (d1 < d0 ? 2 : 1);
+  }
+  int best = -1, bid = 0x7fffffff;
+  float bx = 0.f, by = 0.f, bz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+  auto offer = [&](int p, float4 c) {
+    const int cid = __float_as_int(c.w);
+    bool take;
+    if (best < 0) {
+      take = true;
+    } else {
+      const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
+      const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
+      take = lhs > 0.f || (lhs == 0.f && cid < bid);
+    }
+    if (take) {
+      best = p;
+      bid = cid;
+      bx = c.x;
+      by = c.y;
+      bz = c.z;
+      wx = qx - bx;
+      wy = qy - by;
+      wz = qz - bz;
+    }
+  };
+  {
+    const int64_t j = node - nleaf0;
+    const int64_t p0 = leaf_first(m, j), p1 = leaf_first(m, j + 1);
+    if (COUNT) wk->points += (int)(p1 - p0);
+    for (int64_t p = p0; p < p1; ++p) offer((int)p, __ldg(&m.kd_points[p]));
+  }
+  for (int step = 0; step < kWalkCap; ++step) {
+    const int cur = best;
+    const uint32_t o0 = __ldg(&m.nb_off[cur]), o1 = __ldg(&m.nb_off[cur + 1]);
+    if (COUNT) wk->points += (int)(o1 - o0);
+    for (uint32_t k = o0; k < o1; ++k) {
+      const int w = (int)__ldg(&m.nb[k]);
+      offer(w, __ldg(&m.kd_points[w]));
+    }
+    if (best == cur) return best;
+  }
+  return nearest_pos<COUNT>(m, qx, qy, qz, wk);
+}
+
+template <bool COUNT = false>
+__device__ __forceinline__ int find_nearest(const DevView &m, bool walk, float qx, float qy,
+                                            float qz, Work *wk = nullptr) {
+  return walk ? nearest_walk<COUNT>(m, qx, qy, qz, wk) : nearest_pos<COUNT>(m, qx, qy, qz, wk);
+}
+
 // ------------------------------------------------------------------ a1
 __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   v &= 0x3ff;
@@ -220,8 +296,8 @@ struct Best {
 
 template <bool COUNT = false>
 __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
-                                          Best &r, Work *wk = nullptr) {
-  const int v = nearest_pos<COUNT>(m, qx, qy, qz, wk);
+                                          Best &r, Work *wk = nullptr, bool walk = true) {
+  const int v = find_nearest<COUNT>(m, walk, qx, qy, qz, wk);
   const float4 pv = __ldg(&m.kd_points[v]);
   {
     const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
@@ -325,7 +401,7 @@ __device__ __forceinline__ void store_result(int64_t o, const Best &r, bool ok, 
 
 __global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
                         float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
-                        uint8_t *status) {
+                        uint8_t *status, int walk) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 s = sq[i];
@@ -337,20 +413,250 @@ __global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, flo
     if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
         s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
       st |= 1;
-    query_one(m, s.x, s.y, s.z, r);
+    query_one(m, s.x, s.y, s.z, r, nullptr, walk != 0);
   }
+  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+}
+
+
+// ------------------------------------------------ a2..a8, warp-cooperative
+// One warp answers 32 Morton-adjacent queries together.  The KD-tree walk is
+// shared: a node is entered when any lane's pruning bound admits it
+// (ballots), so the warp never diverges on the tree; every lane keeps its own
+// best vertex.  The list scan visits each distinct nearest vertex of the
+// warp once: its entries are staged 32 at a time into shared memory with
+// coalesced loads, and the lanes whose nearest vertex it is test them.
+constexpr int kWarpStack = 48;
+struct WarpSmem {
+  int stack[kWarpStack];
+  float4 stage[64];
+};
+
+template <bool COUNT>
+__device__ __forceinline__ int warp_nearest(const DevView &m, float qx, float qy, float qz,
+                                            bool active, WarpSmem &ws, Work *wk) {
+  const unsigned full = 0xffffffffu;
+  int best = -1, bid = 0x7fffffff;
+  float bx = 0.f, by = 0.f, bz = 0.f, bd2 = FLT_MAX;
+  float wx = 0.f, wy = 0.f, wz = 0.f;
+  const int64_t nleaf0 = m.L - 1;
+  int sp = 0;
+  int node = 0;
+  for (;;) {
+    if (node >= nleaf0) {
+      const int64_t j = node - nleaf0;
+      const int64_t p0 = leaf_first(m, j), p1 = leaf_first(m, j + 1);
+      if (COUNT && active) wk->points += (int)(p1 - p0);
+      for (int64_t p = p0; p < p1; ++p) {
+        const float4 c = __ldg(&m.kd_points[p]);
+        const int cid = __float_as_int(c.w);
+        bool take;
+        if (best < 0) {
+          take = true;
+        } else {
+          const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
+          const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
+          take = lhs > 0.f || (lhs == 0.f && cid < bid);
+        }
+        if (take && active) {
+          best = (int)p;
+          bid = cid;
+          bx = c.x;
+          by = c.y;
+          bz = c.z;
+          wx = qx - bx;
+          wy = qy - by;
+          wz = qz - bz;
+          bd2 = wx * wx + wy * wy + wz * wz;
+        }
+      }
+    } else {
+      if (COUNT && active) ++wk->nodes;
+      const float4 A = __ldg(&m.kd_nodes[3 * node + 0]);
+      const float4 B = __ldg(&m.kd_nodes[3 * node + 1]);
+      const float4 C = __ldg(&m.kd_nodes[3 * node + 2]);
+      const float d0 = box_d2(qx, qy, qz, A.x, A.y, A.z, A.w, B.x, B.y);
+      const float d1 = box_d2(qx, qy, qz, B.z, B.w, C.x, C.y, C.z, C.w);
+      const float bound = bd2 * kPruneSlack;
+      const unsigned m0 = __ballot_sync(full, active && d0 <= bound);
+      const unsigned m1 = __ballot_sync(full, active && d1 <= bound);
+      if (m0 | m1) {
+        const int c0 = 2 * node + 1, c1 = c0 + 1;
+        if (m0 && m1) {
+          // go first where more lanes find the nearer child
+          const unsigned pref0 = __ballot_sync(full, active && d0 <= d1);
+          const bool first0 = __popc(pref0) * 2 >= __popc(m0 | m1);
+          if (sp < kWarpStack) {
+            if ((threadIdx.x & 31) == 0) ws.stack[sp] = first0 ? c1 : c0;
+            ++sp;
+          }
+          node = first0 ? c0 : c1;
+        } else {
+          node = m0 ? c0 : c1;
+        }
+        __syncwarp();
+        continue;
+      }
+    }
+    // pop the next subtree some lane still needs
+    bool more = false;
+    while (sp > 0) {
+      --sp;
+      __syncwarp();
+      const int c = ws.stack[sp];
+      const int par = (c - 1) >> 1;
+      const float4 A = __ldg(&m.kd_nodes[3 * par + 0]);
+      const float4 B = __ldg(&m.kd_nodes[3 * par + 1]);
+      const float4 C = __ldg(&m.kd_nodes[3 * par + 2]);
+      const float d = (c & 1) ? box_d2(qx, qy, qz, A.x, A.y, A.z, A.w, B.x, B.y)
+                              : box_d2(qx, qy, qz, B.z, B.w, C.x, C.y, C.z, C.w);
+      if (__any_sync(full, active && d <= bd2 * kPruneSlack)) {
+        node = c;
+        more = true;
+        break;
+      }
+    }
+    if (!more) break;
+  }
+  return best;
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy, float qz,
+                                           bool active, WarpSmem &ws, Best &r, Work *wk,
+                                           bool walk) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int v;
+  if (walk) {
+    v = active ? nearest_walk<COUNT>(m, qx, qy, qz, wk) : 0;
+    __syncwarp();
+  } else {
+    v = warp_nearest<COUNT>(m, qx, qy, qz, active, ws, wk);
+  }
+  if (active) {
+    const float4 pv = __ldg(&m.kd_points[v]);
+    const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
+    r.d2 = dx * dx + dy * dy + dz * dz;
+    r.cx = pv.x;
+    r.cy = pv.y;
+    r.cz = pv.z;
+    r.tid = (uint32_t)__float_as_int(pv.w);
+    r.w0 = 1.f;
+    r.w1 = 0.f;
+    r.w2 = 0.f;
+  }
+  unsigned todo = __ballot_sync(full, active);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int vv = __shfl_sync(full, v, leader);
+    const unsigned grp = __ballot_sync(full, active && v == vv) & todo;
+    todo &= ~grp;
+    const bool mine = (grp >> lane) & 1u;
+    const uint32_t j0 = __ldg(&m.row_off[vv]), j1 = __ldg(&m.row_off[vv + 1]);
+    if (COUNT && mine) wk->entries += (int)(j1 - j0);
+    for (uint32_t base = j0; base < j1; base += 32) {
+      const int cnt = (int)min(32u, j1 - base);
+      __syncwarp();
+      if (lane < cnt) {
+        ws.stage[2 * lane] = __ldg(&m.entries[2 * (size_t)(base + lane)]);
+        ws.stage[2 * lane + 1] = __ldg(&m.entries[2 * (size_t)(base + lane) + 1]);
+      }
+      __syncwarp();
+      if (mine) {
+        for (int k = 0; k < cnt; ++k) {
+          const float4 lo = ws.stage[2 * k];
+          if (qx < lo.x || qy < lo.y || qz < lo.z) continue;
+          const float4 hi = ws.stage[2 * k + 1];
+          if (qx > hi.x || qy > hi.y || qz > hi.z) continue;
+          const uint32_t tid = (uint32_t)__float_as_int(lo.w);
+          const uint32_t id = tid & 0x3fffffffu;
+          if ((tid >> 30) == 1u) {
+            if (COUNT) ++wk->edges;
+            const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
+            const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
+            const float ex = qx - a.x, ey = qy - a.y, ez = qz - a.z;
+            const float t = (ex * d.x + ey * d.y + ez * d.z) * a.w;
+            if (t > 0.f && t < 1.f) {
+              const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
+              const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
+              const float d2 = fx * fx + fy * fy + fz * fz;
+              if (d2 < r.d2) {
+                r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
+                r.w0 = 1.f - t; r.w1 = t; r.w2 = 0.f;
+              }
+            }
+          } else {
+            if (COUNT) ++wk->faces;
+            const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
+            const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
+            const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
+            const float ex = qx - a.x, ey = qy - a.y, ez = qz - a.z;
+            const float p1 = ex * e1.x + ey * e1.y + ez * e1.z;
+            const float p2 = ex * e2.x + ey * e2.y + ez * e2.z;
+            const float s = a.w * p1 - e1.w * p2;
+            const float t = e2.w * p2 - e1.w * p1;
+            if (s > 0.f && t > 0.f && s + t < 1.f) {
+              const float cx = a.x + s * e1.x + t * e2.x;
+              const float cy = a.y + s * e1.y + t * e2.y;
+              const float cz = a.z + s * e1.z + t * e2.z;
+              const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
+              const float d2 = fx * fx + fy * fy + fz * fz;
+              if (d2 < r.d2) {
+                r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
+                r.w0 = 1.f - s - t; r.w1 = s; r.w2 = t;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <bool COUNT>
+__global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
+                             float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
+                             uint8_t *status, unsigned long long *acc, int walk) {
+  extern __shared__ WarpSmem smem_w[];
+  WarpSmem &ws = smem_w[threadIdx.x >> 5];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // whole warps stay together; lanes past the end take part inactive
+  if (((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >= n) return;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < n) s = sq[i];
+  const bool ok = i < n && finite3(s.x, s.y, s.z);
+  Best r;
+  Work w = {0, 0, 0, 0, 0};
+  warp_query<COUNT>(m, s.x, s.y, s.z, ok, ws, r, &w, walk != 0);
+  if (COUNT) {
+    int v[5] = {w.nodes, w.points, w.entries, w.edges, w.faces};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      unsigned long long x = (unsigned long long)v[k];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], x);
+    }
+    return;
+  }
+  if (i >= n) return;
+  const int64_t o = __float_as_int(s.w);
+  uint8_t st = ok ? 0 : 2;
+  if (ok && (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
+             s.y > m.dom_hi[1] || s.z > m.dom_hi[2]))
+    st |= 1;
   store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
 }
 
 // Counting variant of the query (not timed): sums the per-query work.
 __global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t n,
-                              unsigned long long *__restrict__ acc) {
+                              unsigned long long *__restrict__ acc, int walk) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   Work w = {0, 0, 0, 0, 0};
   if (i < n) {
     const float4 s = sq[i];
     Best r;
-    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w);
+    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w, walk != 0);
   }
   int v[5] = {w.nodes, w.points, w.entries, w.edges, w.faces};
 #pragma unroll
@@ -362,11 +668,13 @@ __global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t 
 }
 
 __global__ void k_nearest(DevView m, const float *__restrict__ xyz, int64_t n,
-                          int32_t *__restrict__ out) {
+                          int32_t *__restrict__ out, int original_ids, int walk) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-  out[i] = finite3(x, y, z) ? nearest_pos(m, x, y, z) : -1;
+  int p = finite3(x, y, z) ? find_nearest(m, walk != 0, x, y, z) : -1;
+  if (original_ids && p >= 0) p = __float_as_int(__ldg(&m.kd_points[p]).w);
+  out[i] = p;
 }
 
 // ------------------------------------------------------------------ a9
@@ -561,21 +869,34 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   }
   const int bt = tune.block_threads;
   if (ev) cudaEventRecord(ev[1], stream);
+  const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
+  const int walk = (tune.nn_walk && m.nb_off) ? 1 : 0;
   if (counters) {
     cudaMemsetAsync(counters, 0, 5 * sizeof(unsigned long long), stream);
-    k_query_count<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, counters);
+    if (tune.warp_mode)
+      k_query_warp<true><<<blocks_for(n, bt), bt, wsm, stream>>>(m, sorted, n, nullptr, nullptr,
+                                                                 nullptr, nullptr, nullptr,
+                                                                 nullptr, counters, walk);
+    else
+      k_query_count<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, counters, walk);
+  } else if (tune.warp_mode) {
+    k_query_warp<false><<<blocks_for(n, bt), bt, wsm, stream>>>(m, sorted, n, dist, closest,
+                                                                prim_id, prim_type, save, status,
+                                                                nullptr, walk);
   } else {
     k_query<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, dist, closest, prim_id,
-                                                  prim_type, save, status);
+                                                  prim_type, save, status, walk);
   }
   if (ev) cudaEventRecord(ev[2], stream);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, bool original_ids, int nn_walk) {
   if (n <= 0) return cudaSuccess;
-  k_nearest<<<blocks_for(n, 128), 128, 0, stream>>>(m, xyz, n, out_pos);
+  if (nn_walk && !m.nb_off) return cudaErrorInvalidValue;
+  k_nearest<<<blocks_for(n, 128), 128, 0, stream>>>(m, xyz, n, out_pos, original_ids ? 1 : 0,
+                                                    nn_walk);
   return cudaGetLastError();
 }
 

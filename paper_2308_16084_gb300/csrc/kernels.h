@@ -17,6 +17,8 @@ struct DevView {
   const float4 *face_rec;   // 3 per face
   const int2 *edges;        // canonical edges
   const int4 *tris;         // faces (a, b, c, 0)
+  const uint32_t *nb_off;   // nv + 1: Voronoi neighbours of each row (CSR)
+  const uint32_t *nb;       // neighbour rows
   int64_t nv;
   int64_t L;                // KD-tree leaves (2^depth)
   int depth;
@@ -27,6 +29,8 @@ struct DevView {
 struct QueryTuning {
   int sort_bits = 18;
   int block_threads = 256;
+  int warp_mode = 0;  // 0: one thread per query, 1: warp-cooperative
+  int nn_walk = 1;    // 0: KD-tree backtracking, 1: KD descent + Voronoi walk
 };
 
 // Scratch needed by launch_query for n points, in bytes.
@@ -45,7 +49,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
 // Nearest vertex (KD-tree position) of each point: used by the builder to
 // certify Voronoi cells.
 cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
-                           cudaStream_t stream);
+                           cudaStream_t stream, bool original_ids = false, int nn_walk = 0);
 
 // Backward scatter (a9).
 cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,

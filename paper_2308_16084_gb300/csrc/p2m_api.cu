@@ -67,7 +67,7 @@ struct p2m_handle {
   int device = -1;          // -1: host-only handle (tables built, no queries)
   Layout L;                 // host copy of the layout
   DevBuf<float> kd_nodes, kd_points, entries, edge_rec, face_rec;
-  DevBuf<uint32_t> row_off;
+  DevBuf<uint32_t> row_off, nb_off, nb;
   DevBuf<int32_t> edges, tris;
   DevView view{};
   void *scratch = nullptr;  // query scratch arena
@@ -109,6 +109,8 @@ struct p2m_handle {
     view.face_rec = (const float4 *)face_rec.p;
     view.edges = (const int2 *)edges.p;
     view.tris = (const int4 *)tris.p;
+    view.nb_off = nb_off.p;
+    view.nb = nb.p;
     view.nv = L.nv;
     view.depth = L.kd_depth;
     view.L = (int64_t)1 << L.kd_depth;
@@ -132,9 +134,11 @@ struct p2m_handle {
     if (e == cudaSuccess) e = face_rec.upload(L.face_rec.data(), L.face_rec.size());
     if (e == cudaSuccess) e = edges.upload(L.edges.data(), L.edges.size());
     if (e == cudaSuccess) e = tris.upload(L.tris.data(), L.tris.size());
+    if (e == cudaSuccess && !L.nb_off.empty()) e = nb_off.upload(L.nb_off.data(), L.nb_off.size());
+    if (e == cudaSuccess && !L.nb.empty()) e = nb.upload(L.nb.data(), L.nb.size());
     make_view();
     device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
-                        row_off.n + edges.n + tris.n);
+                        row_off.n + edges.n + tris.n + nb_off.n + nb.n);
     return e;
   }
 };
@@ -262,6 +266,8 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   if (!h || !t) return P2M_ERR_INVALID_ARG;
   t->sort_bits = h->tune.sort_bits;
   t->block_threads = h->tune.block_threads;
+  t->warp_cooperative = h->tune.warp_mode;
+  t->nn_walk = h->tune.nn_walk;
   return P2M_OK;
 }
 
@@ -270,8 +276,12 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
   if (t->block_threads != 64 && t->block_threads != 128 && t->block_threads != 256 &&
       t->block_threads != 512)
     return P2M_ERR_INVALID_ARG;
+  if (t->warp_cooperative != 0 && t->warp_cooperative != 1) return P2M_ERR_INVALID_ARG;
+  if (t->nn_walk != 0 && t->nn_walk != 1) return P2M_ERR_INVALID_ARG;
+  h->tune.nn_walk = t->nn_walk;
   h->tune.sort_bits = t->sort_bits;
   h->tune.block_threads = t->block_threads;
+  h->tune.warp_mode = t->warp_cooperative;
   return P2M_OK;
 }
 
@@ -357,6 +367,18 @@ p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t 
   if (e != cudaSuccess) return from_cuda(e);
   for (int k = 0; k < 5; ++k) out[k] = (int64_t)c[k];
   return P2M_OK;
+}
+
+p2m_status p2m_nearest_vertex(p2m_handle *h, const float *q, int64_t n, int32_t *vertex,
+                              void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !vertex) return P2M_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  return from_cuda(p2m::launch_nearest(h->view, q, n, vertex, (cudaStream_t)stream, true,
+                                       h->tune.nn_walk && h->view.nb_off ? 1 : 0));
 }
 
 p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
@@ -670,11 +692,12 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   cudaEventCreate(&e1);
   p2m::QueryTuning best = h->tune;
   float bms = 1e30f;
-  const int bits_c[] = {0, 12, 15, 18, 21};
-  const int block_c[] = {128, 256, 512};
+  const int bits_c[] = {12, 15, 18, 21};
+  const int block_c[] = {128, 256};
+  for (int wm = 0; wm < 2; ++wm)
   for (int bits : bits_c)
     for (int bt : block_c) {
-      p2m_tuning t{bits, bt};
+      p2m_tuning t{bits, bt, wm, 1};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);
@@ -706,7 +729,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -758,7 +781,7 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
   ok = ok && put_vec(f, L.kd_nodes, ck) && put_vec(f, L.kd_points, ck) &&
        put_vec(f, L.pos_of_vertex, ck) && put_vec(f, L.row_off, ck) && put_vec(f, L.entries, ck) &&
        put_vec(f, L.edge_rec, ck) && put_vec(f, L.face_rec, ck) && put_vec(f, L.edges, ck) &&
-       put_vec(f, L.tris, ck);
+       put_vec(f, L.tris, ck) && put_vec(f, L.nb_off, ck) && put_vec(f, L.nb, ck);
   ok = ok && fwrite(&ck, 8, 1, f) == 1;
   ok = (fclose(f) == 0) && ok;
   return ok ? P2M_OK : P2M_ERR_IO;
@@ -787,8 +810,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
     ok = get_vec(f, L.kd_nodes, ck) && get_vec(f, L.kd_points, ck) &&
          get_vec(f, L.pos_of_vertex, ck) && get_vec(f, L.row_off, ck) &&
          get_vec(f, L.entries, ck) && get_vec(f, L.edge_rec, ck) && get_vec(f, L.face_rec, ck) &&
-         get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && fread(&stored, 8, 1, f) == 1 &&
-         stored == ck;
+         get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && get_vec(f, L.nb_off, ck) &&
+         get_vec(f, L.nb, ck) && fread(&stored, 8, 1, f) == 1 && stored == ck;
   }
   fclose(f);
   if (!ok) return P2M_ERR_IO;
@@ -807,7 +830,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
   L.delta = fl[6];
   std::memcpy(L.kd_root, fl + 7, 24);
   if ((int64_t)L.row_off.size() != L.nv + 1 || (int64_t)L.kd_points.size() != 4 * L.nv ||
-      (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne)
+      (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
+      (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back())
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
     cudaError_t e = h->upload_tree();

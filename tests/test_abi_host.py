@@ -18,8 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def pg():
-    from paper_2308_16084_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2308_16084_gb300 as m
     return m
 
