@@ -128,6 +128,29 @@ p2m_status p2m_nearest_vertex(p2m_handle *h, const float *q, int64_t n, int32_t 
 p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
                           int32_t *prim_id, uint8_t *prim_type, void *stream);
 
+/*
+ * p2m_query without any device allocation (the paper has no counterpart;
+ * this is a deployment variant of p2m_query).  For callers that must not
+ * call cudaMalloc while they run: processes whose GPU memory belongs to
+ * another allocator, real-time loops that cannot take the device-wide
+ * synchronisation of cudaMalloc/cudaFree, plugin hosts that forbid
+ * allocation after start-up.  The sort scratch is a static device array of
+ * about 24.5 MB that every GPU loading this library keeps until the process
+ * exits.  Arguments and outputs as in p2m_query (device pointers; closest
+ * and prim_type may be NULL; no save or status outputs).
+ *   - n may be at most 1,048,576 (2^20); larger n returns P2M_ERR_TOO_LARGE.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call on a device shares the one array, and each call clears the
+ *     part that must start at zero.  Calls whose GPU work overlaps (different
+ *     streams, or different host threads, without ordering between them)
+ *     race on the array and may return wrong results: order them.
+ * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * Errors: INVALID_ARG, NO_DEVICE, TOO_LARGE, CUDA.
+ */
+p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *dist,
+                             float *closest, int32_t *prim_id, uint8_t *prim_type, void *stream);
+
 /* Launch tuning of the query path (chosen by the autotuner or by hand).
  *   sort_bits      Morton bucket bits of the query sort, 0..24 (0 = no sort);
  *                  queries are grouped into 2^sort_bits spatial buckets

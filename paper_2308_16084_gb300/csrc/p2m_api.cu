@@ -845,3 +845,15 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
 }
 
 }  // extern "C"
+
+// Read-only access to a handle's device view and tuning for other
+// translation units of this library (not part of the C ABI).
+namespace p2m {
+bool handle_view(const p2m_handle *h, DevView *v, QueryTuning *t) {
+  if (!h || h->device < 0) return false;
+  *v = h->view;
+  *t = h->tune;
+  return true;
+}
+}  // namespace p2m
+
