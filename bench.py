@@ -216,11 +216,12 @@ def peaks():
 def bytes_per_query(c, n):
     """Algorithmic bytes one query touches (record sizes of the layout):
     query 12 B, outputs 21 B (dist, closest, id, type), 48 B per internal
-    KD node (two child boxes), 16 B per vertex examined, 8 B CSR range,
-    28 B per list entry scanned (Region box + typed id), 32 B per edge and
-    48 B per face tested."""
-    per = (12 + 21 + 8) * n + 48 * c["nodes"] + 16 * c["points"] + 28 * c["entries"] + \
-        32 * c["edges"] + 48 * c["faces"]
+    KD node (two child boxes), 16 B per vertex examined (leaf points and
+    Voronoi neighbours, + 4 B neighbour id), 8 B CSR range, 28 B per list
+    entry scanned (Region box + typed id), 28 B per chunk box tested, 32 B
+    per edge and 48 B per face tested."""
+    per = (12 + 21 + 8) * n + 48 * c["nodes"] + 20 * c["points"] + 28 * c["entries"] + \
+        28 * c.get("chunks", 0) + 32 * c["edges"] + 48 * c["faces"]
     return per / n
 
 

@@ -163,12 +163,18 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  backtracking (Sec. 2.1); 1 = KD-tree descent to one leaf,
  *                  then a walk over Voronoi neighbours to the nearest vertex
  *                  (exact: a vertex nearer than all its Voronoi neighbours is
- *                  the nearest; points outside D use backtracking). */
+ *                  the nearest; points outside D use backtracking); 2 = the
+ *                  walk starts from a seed grid over D whose cells hold the
+ *                  nearest vertex of their centres (default).
+ *   chunked        list scan: 0 = test the Region box of every entry; 1 =
+ *                  test the box of each chunk of 8 spatially ordered
+ *                  entries first (a one-level R-tree per list, Sec. 4.6). */
 typedef struct {
   int sort_bits;
   int block_threads;
   int warp_cooperative;
   int nn_walk;
+  int chunked;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
@@ -185,8 +191,9 @@ p2m_status p2m_timing_summary(p2m_handle *h, double out[3]);
 /* Work counters of a query batch (device q, n points): runs a counting
  * variant of the query kernel (outputs are not written) and returns the
  * totals of KD-tree internal nodes visited, vertices examined, list entries
- * scanned, edges tested and faces tested in out[0..4].  Synchronous. */
-p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[5],
+ * scanned, edges tested, faces tested and chunk boxes tested in out[0..5].
+ * Synchronous. */
+p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[6],
                               void *stream);
 
 /* Pre-size the handle's scratch arena for queries of up to n points, so that

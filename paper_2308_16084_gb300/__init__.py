@@ -33,7 +33,8 @@ class MeshDesc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int)]
+                ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int),
+                ("chunked", ctypes.c_int)]
 
 
 class BatchIO(ctypes.Structure):
@@ -148,14 +149,15 @@ class P2M:
         t = Tuning()
         check(lib.p2m_get_tuning(self._h, ctypes.byref(t)), "p2m_get_tuning")
         return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
-                "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk}
+                "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk,
+                "chunked": t.chunked}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
         t = Tuning(cur["sort_bits"], cur["block_threads"], cur["warp_cooperative"],
-                   cur["nn_walk"])
+                   cur["nn_walk"], cur["chunked"])
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):
@@ -176,11 +178,12 @@ class P2M:
 
     def counters(self, q, stream=None):
         """Work totals of a query batch: internal KD nodes visited, vertices
-        examined, list entries scanned, edges tested, faces tested."""
-        out = (ctypes.c_int64 * 5)()
+        examined, list entries scanned, edges tested, faces tested, chunk
+        boxes tested."""
+        out = (ctypes.c_int64 * 6)()
         check(lib.p2m_query_counters(self._h, _ptr(q), q.shape[0], out, _stream(stream)),
               "p2m_query_counters")
-        return dict(zip(["nodes", "points", "entries", "edges", "faces"], list(out)))
+        return dict(zip(["nodes", "points", "entries", "edges", "faces", "chunks"], list(out)))
 
     def reserve(self, n):
         check(lib.p2m_reserve(self._h, int(n)), "p2m_reserve")

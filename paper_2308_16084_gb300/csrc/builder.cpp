@@ -938,9 +938,39 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     }
   }
   tls.clear();
+  // spatial order inside every row (Morton code of the box centre within the
+  // union of the row's boxes), then chunks of kChunk consecutive entries
+  auto spread = [](uint32_t v) {
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000FF;
+    v = (v | (v << 8)) & 0x0300F00F;
+    v = (v | (v << 4)) & 0x030C30C3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+  };
   parallel_for(nv, threads, 1024, [&](int64_t p, int) {
-    std::sort(all.begin() + out.row_off[p], all.begin() + out.row_off[p + 1],
-              [](const Rec &a, const Rec &b) { return (uint32_t)a.tid < (uint32_t)b.tid; });
+    auto b = all.begin() + out.row_off[p], e = all.begin() + out.row_off[p + 1];
+    if (e - b < 2) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (auto it = b; it != e; ++it)
+      for (int d = 0; d < 3; ++d) {
+        float c = 0.5f * (it->box[d] + it->box[3 + d]);
+        lo[d] = std::min(lo[d], c);
+        hi[d] = std::max(hi[d], c);
+      }
+    auto key = [&](const Rec &r) {
+      uint32_t k[3];
+      for (int d = 0; d < 3; ++d) {
+        float ext = hi[d] - lo[d];
+        float u = ext > 0 ? (0.5f * (r.box[d] + r.box[3 + d]) - lo[d]) / ext : 0.f;
+        k[d] = (uint32_t)std::min(1023.f, std::max(0.f, u * 1024.f));
+      }
+      return spread(k[0]) | (spread(k[1]) << 1) | (spread(k[2]) << 2);
+    };
+    std::sort(b, e, [&](const Rec &x, const Rec &y) {
+      uint32_t kx = key(x), ky = key(y);
+      return kx < ky || (kx == ky && (uint32_t)x.tid < (uint32_t)y.tid);
+    });
   });
   out.entries.resize(8 * total);
   int64_t maxl = 0;
@@ -951,6 +981,31 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     o[0] = r.box[0]; o[1] = r.box[1]; o[2] = r.box[2];
     std::memcpy(&o[3], &r.tid, 4);
     o[4] = r.box[3]; o[5] = r.box[4]; o[6] = r.box[5]; o[7] = 0.f;
+  });
+
+  // ---- chunks of every row
+  out.chunk_off.assign(nv + 1, 0);
+  for (int64_t p = 0; p < nv; ++p) {
+    uint32_t len = out.row_off[p + 1] - out.row_off[p];
+    out.chunk_off[p + 1] = out.chunk_off[p] + (len + Layout::kChunk - 1) / Layout::kChunk;
+  }
+  out.chunks.resize(8 * (size_t)out.chunk_off[nv]);
+  parallel_for(nv, threads, 1024, [&](int64_t p, int) {
+    uint32_t c = out.chunk_off[p];
+    for (uint32_t j = out.row_off[p]; j < out.row_off[p + 1]; j += Layout::kChunk, ++c) {
+      uint32_t cnt = std::min<uint32_t>(Layout::kChunk, out.row_off[p + 1] - j);
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (uint32_t k = j; k < j + cnt; ++k)
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::min(lo[d], all[k].box[d]);
+          hi[d] = std::max(hi[d], all[k].box[3 + d]);
+        }
+      float *o = &out.chunks[8 * (size_t)c];
+      o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2];
+      std::memcpy(&o[3], &j, 4);
+      o[4] = hi[0]; o[5] = hi[1]; o[6] = hi[2];
+      std::memcpy(&o[7], &cnt, 4);
+    }
   });
 
   // ---- geometry records

@@ -55,6 +55,13 @@ struct Layout {
   // entry: {lo.x, lo.y, lo.z, typed id bits}, {hi.x, hi.y, hi.z, 0}
   //   typed id = type << 30 | id   (type 1 = edge, 2 = face)
   std::vector<float> entries;      // n_entries * 8
+  // entries of each row are in spatial (Morton) order of their box centres
+  // and grouped into chunks of up to kChunk; chunk c of row r:
+  //   {lo.x, lo.y, lo.z, first entry bits}, {hi.x, hi.y, hi.z, entry count bits}
+  // (the union of its entries' boxes: a one-level R-tree per list, Sec. 4.6)
+  static constexpr int kChunk = 8;
+  std::vector<uint32_t> chunk_off; // nv + 1
+  std::vector<float> chunks;       // n_chunks * 8
   // geometry records
   //   edge e: {a.x, a.y, a.z, 1/|b-a|^2}, {b.x-a.x, b.y-a.y, b.z-a.z, 0}
   //   face f: {a, A}, {b-a, B}, {c-a, C} with the projection weights

@@ -45,7 +45,7 @@ __device__ __forceinline__ int64_t leaf_first(const DevView &m, int64_t j) {
 // Work counters of one query (counting variant only): internal nodes
 // visited, points examined, list entries scanned, edges tested, faces tested.
 struct Work {
-  int nodes, points, entries, edges, faces;
+  int nodes, points, entries, edges, faces, chunks;
 };
 
 // Nearest vertex of q: returns the KD-tree position (= table row).
@@ -136,14 +136,28 @@ __device__ __forceinline__ int nearest_pos(const DevView &m, float qx, float qy,
 // backtracking search instead.
 constexpr int kWalkCap = 256;
 
+__device__ __forceinline__ int grid_cell(const DevView &m, float v, int a) {
+  const int G = 1 << m.grid_bits;
+  const float u = (v - m.dom_lo[a]) / (m.dom_hi[a] - m.dom_lo[a]);
+  return min(G - 1, max(0, (int)(u * (float)G)));
+}
+
 template <bool COUNT = false>
 __device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy, float qz,
-                                            Work *wk = nullptr) {
+                                            Work *wk = nullptr, bool grid = false) {
   const bool inside = qx >= m.dom_lo[0] && qy >= m.dom_lo[1] && qz >= m.dom_lo[2] &&
                       qx <= m.dom_hi[0] && qy <= m.dom_hi[1] && qz <= m.dom_hi[2];
   if (!inside) return nearest_pos<COUNT>(m, qx, qy, qz, wk);
   const int64_t nleaf0 = m.L - 1;
   int node = 0;
+  int seed = -1;
+  if (grid && m.seed) {
+    const int gb = m.grid_bits;
+    const size_t cell = ((size_t)grid_cell(m, qz, 2) << (2 * gb)) |
+                        ((size_t)grid_cell(m, qy, 1) << gb) | (size_t)grid_cell(m, qx, 0);
+    seed = (int)__ldg(&m.seed[cell]);
+    node = (int)nleaf0;  // skip the descent
+  }
   while (node < nleaf0) {
     if (COUNT) ++wk->nodes;
     const float4 A = __ldg(&m.kd_nodes[3 * node + 0]);
@@ -176,7 +190,10 @@ __device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy
       wz = qz - bz;
     }
   };
-  {
+  if (seed >= 0) {
+    if (COUNT) ++wk->points;
+    offer(seed, __ldg(&m.kd_points[seed]));
+  } else {
     const int64_t j = node - nleaf0;
     const int64_t p0 = leaf_first(m, j), p1 = leaf_first(m, j + 1);
     if (COUNT) wk->points += (int)(p1 - p0);
@@ -195,10 +212,12 @@ __device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy
   return nearest_pos<COUNT>(m, qx, qy, qz, wk);
 }
 
+// mode 0: backtracking, 1: descent + walk, 2: seed grid + walk
 template <bool COUNT = false>
-__device__ __forceinline__ int find_nearest(const DevView &m, bool walk, float qx, float qy,
+__device__ __forceinline__ int find_nearest(const DevView &m, int mode, float qx, float qy,
                                             float qz, Work *wk = nullptr) {
-  return walk ? nearest_walk<COUNT>(m, qx, qy, qz, wk) : nearest_pos<COUNT>(m, qx, qy, qz, wk);
+  return mode ? nearest_walk<COUNT>(m, qx, qy, qz, wk, mode == 2)
+              : nearest_pos<COUNT>(m, qx, qy, qz, wk);
 }
 
 // ------------------------------------------------------------------ a1
@@ -294,9 +313,73 @@ struct Best {
   float w0, w1, w2;
 };
 
+// a4 + a6/a7 for list entry j: Region-box test, then the gated distance.
+// Exact ties keep the lower typed id (vertex < edge < face, then lower id),
+// so the result does not depend on the order of the list.
+template <bool COUNT>
+__device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy, float qz,
+                                           uint32_t j, Best &r, Work *wk) {
+  const float4 lo = __ldg(&m.entries[2 * (size_t)j]);
+  if (qx < lo.x || qy < lo.y || qz < lo.z) return;
+  const float4 hi = __ldg(&m.entries[2 * (size_t)j + 1]);
+  if (qx > hi.x || qy > hi.y || qz > hi.z) return;
+  const uint32_t tid = (uint32_t)__float_as_int(lo.w);
+  const uint32_t id = tid & 0x3fffffffu;
+  if ((tid >> 30) == 1u) {
+    if (COUNT) ++wk->edges;
+    const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
+    const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
+    const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+    const float t = (wx * d.x + wy * d.y + wz * d.z) * a.w;
+    if (t > 0.f && t < 1.f) {
+      const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
+      const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
+      const float d2 = ex * ex + ey * ey + ez * ez;
+      if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
+        r.d2 = d2;
+        r.cx = cx;
+        r.cy = cy;
+        r.cz = cz;
+        r.tid = tid;
+        r.w0 = 1.f - t;
+        r.w1 = t;
+        r.w2 = 0.f;
+      }
+    }
+  } else {
+    if (COUNT) ++wk->faces;
+    const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
+    const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
+    const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
+    const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+    const float p1 = wx * e1.x + wy * e1.y + wz * e1.z;
+    const float p2 = wx * e2.x + wy * e2.y + wz * e2.z;
+    const float s = a.w * p1 - e1.w * p2;
+    const float t = e2.w * p2 - e1.w * p1;
+    if (s > 0.f && t > 0.f && s + t < 1.f) {
+      const float cx = a.x + s * e1.x + t * e2.x;
+      const float cy = a.y + s * e1.y + t * e2.y;
+      const float cz = a.z + s * e1.z + t * e2.z;
+      const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
+      const float d2 = ex * ex + ey * ey + ez * ez;
+      if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
+        r.d2 = d2;
+        r.cx = cx;
+        r.cy = cy;
+        r.cz = cz;
+        r.tid = tid;
+        r.w0 = 1.f - s - t;
+        r.w1 = s;
+        r.w2 = t;
+      }
+    }
+  }
+}
+
 template <bool COUNT = false>
 __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
-                                          Best &r, Work *wk = nullptr, bool walk = true) {
+                                          Best &r, Work *wk = nullptr, int walk = 2,
+                                          bool chunked = true) {
   const int v = find_nearest<COUNT>(m, walk, qx, qy, qz, wk);
   const float4 pv = __ldg(&m.kd_points[v]);
   {
@@ -311,63 +394,23 @@ __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, 
     r.w2 = 0.f;
   }
   const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
-  if (COUNT) wk->entries += (int)(j1 - j0);
-  for (uint32_t j = j0; j < j1; ++j) {
-    const float4 lo = __ldg(&m.entries[2 * (size_t)j]);
+  if (!chunked || !m.chunks) {
+    if (COUNT) wk->entries += (int)(j1 - j0);
+    for (uint32_t j = j0; j < j1; ++j) test_entry<COUNT>(m, qx, qy, qz, j, r, wk);
+    return;
+  }
+  // one-level R-tree: chunk boxes first, then the entries of the chunks
+  // whose box contains q
+  const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
+  if (COUNT) wk->chunks += (int)(c1 - c0);
+  for (uint32_t c = c0; c < c1; ++c) {
+    const float4 lo = __ldg(&m.chunks[2 * (size_t)c]);
     if (qx < lo.x || qy < lo.y || qz < lo.z) continue;
-    const float4 hi = __ldg(&m.entries[2 * (size_t)j + 1]);
+    const float4 hi = __ldg(&m.chunks[2 * (size_t)c + 1]);
     if (qx > hi.x || qy > hi.y || qz > hi.z) continue;
-    const uint32_t tid = (uint32_t)__float_as_int(lo.w);
-    const uint32_t id = tid & 0x3fffffffu;
-    if ((tid >> 30) == 1u) {
-      if (COUNT) ++wk->edges;
-      const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
-      const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
-      const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
-      const float t = (wx * d.x + wy * d.y + wz * d.z) * a.w;
-      if (t > 0.f && t < 1.f) {
-        const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
-        const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
-        const float d2 = ex * ex + ey * ey + ez * ez;
-        if (d2 < r.d2) {
-          r.d2 = d2;
-          r.cx = cx;
-          r.cy = cy;
-          r.cz = cz;
-          r.tid = tid;
-          r.w0 = 1.f - t;
-          r.w1 = t;
-          r.w2 = 0.f;
-        }
-      }
-    } else {
-      if (COUNT) ++wk->faces;
-      const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
-      const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
-      const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
-      const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
-      const float p1 = wx * e1.x + wy * e1.y + wz * e1.z;
-      const float p2 = wx * e2.x + wy * e2.y + wz * e2.z;
-      const float s = a.w * p1 - e1.w * p2;
-      const float t = e2.w * p2 - e1.w * p1;
-      if (s > 0.f && t > 0.f && s + t < 1.f) {
-        const float cx = a.x + s * e1.x + t * e2.x;
-        const float cy = a.y + s * e1.y + t * e2.y;
-        const float cz = a.z + s * e1.z + t * e2.z;
-        const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
-        const float d2 = ex * ex + ey * ey + ez * ez;
-        if (d2 < r.d2) {
-          r.d2 = d2;
-          r.cx = cx;
-          r.cy = cy;
-          r.cz = cz;
-          r.tid = tid;
-          r.w0 = 1.f - s - t;
-          r.w1 = s;
-          r.w2 = t;
-        }
-      }
-    }
+    const uint32_t first = (uint32_t)__float_as_int(lo.w), cnt = (uint32_t)__float_as_int(hi.w);
+    if (COUNT) wk->entries += (int)cnt;
+    for (uint32_t j = first; j < first + cnt; ++j) test_entry<COUNT>(m, qx, qy, qz, j, r, wk);
   }
 }
 
@@ -401,7 +444,7 @@ __device__ __forceinline__ void store_result(int64_t o, const Best &r, bool ok, 
 
 __global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
                         float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
-                        uint8_t *status, int walk) {
+                        uint8_t *status, int walk, int chunked) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 s = sq[i];
@@ -413,7 +456,7 @@ __global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, flo
     if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
         s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
       st |= 1;
-    query_one(m, s.x, s.y, s.z, r, nullptr, walk != 0);
+    query_one(m, s.x, s.y, s.z, r, nullptr, walk, chunked != 0);
   }
   store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
 }
@@ -524,12 +567,12 @@ __device__ __forceinline__ int warp_nearest(const DevView &m, float qx, float qy
 template <bool COUNT>
 __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy, float qz,
                                            bool active, WarpSmem &ws, Best &r, Work *wk,
-                                           bool walk) {
+                                           int walk) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   int v;
   if (walk) {
-    v = active ? nearest_walk<COUNT>(m, qx, qy, qz, wk) : 0;
+    v = active ? nearest_walk<COUNT>(m, qx, qy, qz, wk, walk == 2) : 0;
     __syncwarp();
   } else {
     v = warp_nearest<COUNT>(m, qx, qy, qz, active, ws, wk);
@@ -581,7 +624,7 @@ __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy,
               const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
               const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
               const float d2 = fx * fx + fy * fy + fz * fz;
-              if (d2 < r.d2) {
+              if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
                 r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
                 r.w0 = 1.f - t; r.w1 = t; r.w2 = 0.f;
               }
@@ -602,7 +645,7 @@ __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy,
               const float cz = a.z + s * e1.z + t * e2.z;
               const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
               const float d2 = fx * fx + fy * fy + fz * fz;
-              if (d2 < r.d2) {
+              if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
                 r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
                 r.w0 = 1.f - s - t; r.w1 = s; r.w2 = t;
               }
@@ -627,12 +670,12 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
   if (i < n) s = sq[i];
   const bool ok = i < n && finite3(s.x, s.y, s.z);
   Best r;
-  Work w = {0, 0, 0, 0, 0};
-  warp_query<COUNT>(m, s.x, s.y, s.z, ok, ws, r, &w, walk != 0);
+  Work w = {0, 0, 0, 0, 0, 0};
+  warp_query<COUNT>(m, s.x, s.y, s.z, ok, ws, r, &w, walk);
   if (COUNT) {
-    int v[5] = {w.nodes, w.points, w.entries, w.edges, w.faces};
+    int v[6] = {w.nodes, w.points, w.entries, w.edges, w.faces, w.chunks};
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
       unsigned long long x = (unsigned long long)v[k];
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
       if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], x);
@@ -650,17 +693,17 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
 
 // Counting variant of the query (not timed): sums the per-query work.
 __global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t n,
-                              unsigned long long *__restrict__ acc, int walk) {
+                              unsigned long long *__restrict__ acc, int walk, int chunked) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  Work w = {0, 0, 0, 0, 0};
+  Work w = {0, 0, 0, 0, 0, 0};
   if (i < n) {
     const float4 s = sq[i];
     Best r;
-    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w, walk != 0);
+    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w, walk, chunked != 0);
   }
-  int v[5] = {w.nodes, w.points, w.entries, w.edges, w.faces};
+  int v[6] = {w.nodes, w.points, w.entries, w.edges, w.faces, w.chunks};
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 6; ++k) {
     unsigned long long x = (unsigned long long)v[k];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(&acc[k], x);
@@ -672,9 +715,21 @@ __global__ void k_nearest(DevView m, const float *__restrict__ xyz, int64_t n,
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-  int p = finite3(x, y, z) ? find_nearest(m, walk != 0, x, y, z) : -1;
+  int p = finite3(x, y, z) ? find_nearest(m, walk, x, y, z) : -1;
   if (original_ids && p >= 0) p = __float_as_int(__ldg(&m.kd_points[p]).w);
   out[i] = p;
+}
+
+__global__ void k_seed_grid(DevView m, uint32_t *__restrict__ seed) {
+  const int gb = m.grid_bits;
+  const int64_t G = (int64_t)1 << gb;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= G * G * G) return;
+  const int ix = (int)(i & (G - 1)), iy = (int)((i >> gb) & (G - 1)), iz = (int)(i >> (2 * gb));
+  const float x = m.dom_lo[0] + (ix + 0.5f) * (m.dom_hi[0] - m.dom_lo[0]) / (float)G;
+  const float y = m.dom_lo[1] + (iy + 0.5f) * (m.dom_hi[1] - m.dom_lo[1]) / (float)G;
+  const float z = m.dom_lo[2] + (iz + 0.5f) * (m.dom_hi[2] - m.dom_lo[2]) / (float)G;
+  seed[i] = (uint32_t)nearest_pos(m, x, y, z);
 }
 
 // ------------------------------------------------------------------ a9
@@ -870,22 +925,23 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   const int bt = tune.block_threads;
   if (ev) cudaEventRecord(ev[1], stream);
   const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
-  const int walk = (tune.nn_walk && m.nb_off) ? 1 : 0;
+  const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
+  const int chunked = (tune.chunked && m.chunks) ? 1 : 0;
   if (counters) {
-    cudaMemsetAsync(counters, 0, 5 * sizeof(unsigned long long), stream);
+    cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), stream);
     if (tune.warp_mode)
       k_query_warp<true><<<blocks_for(n, bt), bt, wsm, stream>>>(m, sorted, n, nullptr, nullptr,
                                                                  nullptr, nullptr, nullptr,
                                                                  nullptr, counters, walk);
     else
-      k_query_count<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, counters, walk);
+      k_query_count<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, counters, walk, chunked);
   } else if (tune.warp_mode) {
     k_query_warp<false><<<blocks_for(n, bt), bt, wsm, stream>>>(m, sorted, n, dist, closest,
                                                                 prim_id, prim_type, save, status,
                                                                 nullptr, walk);
   } else {
     k_query<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, dist, closest, prim_id,
-                                                  prim_type, save, status, walk);
+                                                  prim_type, save, status, walk, chunked);
   }
   if (ev) cudaEventRecord(ev[2], stream);
   return cudaGetLastError();
@@ -895,8 +951,16 @@ cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_
                            cudaStream_t stream, bool original_ids, int nn_walk) {
   if (n <= 0) return cudaSuccess;
   if (nn_walk && !m.nb_off) return cudaErrorInvalidValue;
+  if (nn_walk == 2 && !m.seed) nn_walk = 1;
   k_nearest<<<blocks_for(n, 128), 128, 0, stream>>>(m, xyz, n, out_pos, original_ids ? 1 : 0,
                                                     nn_walk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_grid(const DevView &m, uint32_t *seed, cudaStream_t stream) {
+  if (m.grid_bits <= 0) return cudaSuccess;
+  const int64_t cells = (int64_t)1 << (3 * m.grid_bits);
+  k_seed_grid<<<blocks_for(cells, 128), 128, 0, stream>>>(m, seed);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,10 @@ struct DevView {
   const int4 *tris;         // faces (a, b, c, 0)
   const uint32_t *nb_off;   // nv + 1: Voronoi neighbours of each row (CSR)
   const uint32_t *nb;       // neighbour rows
+  const uint32_t *chunk_off;  // nv + 1: chunks of each row (CSR)
+  const float4 *chunks;       // 2 per chunk: {lo, first entry}, {hi, count}
+  const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre
+  int grid_bits;              // G = 2^grid_bits cells per axis over D (0 = no grid)
   int64_t nv;
   int64_t L;                // KD-tree leaves (2^depth)
   int depth;
@@ -30,7 +34,9 @@ struct QueryTuning {
   int sort_bits = 18;
   int block_threads = 256;
   int warp_mode = 0;  // 0: one thread per query, 1: warp-cooperative
-  int nn_walk = 1;    // 0: KD-tree backtracking, 1: KD descent + Voronoi walk
+  int nn_walk = 2;    // 0: KD-tree backtracking, 1: KD descent + Voronoi walk,
+                      // 2: seed-grid lookup + Voronoi walk
+  int chunked = 1;    // 0: scan every list entry, 1: test chunk boxes first
 };
 
 // Scratch needed by launch_query for n points, in bytes.
@@ -50,6 +56,10 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
 // certify Voronoi cells.
 cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
                            cudaStream_t stream, bool original_ids = false, int nn_walk = 0);
+
+// Fill the seed grid: nearest vertex (row) of every cell centre of the
+// G^3 grid over D (G = 2^view.grid_bits), by KD-tree backtracking.
+cudaError_t launch_seed_grid(const DevView &m, uint32_t *seed, cudaStream_t stream);
 
 // Backward scatter (a9).
 cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,

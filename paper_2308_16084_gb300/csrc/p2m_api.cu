@@ -67,7 +67,9 @@ struct p2m_handle {
   int device = -1;          // -1: host-only handle (tables built, no queries)
   Layout L;                 // host copy of the layout
   DevBuf<float> kd_nodes, kd_points, entries, edge_rec, face_rec;
-  DevBuf<uint32_t> row_off, nb_off, nb;
+  DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed;
+  int grid_bits = 0;
+  DevBuf<float> chunks;
   DevBuf<int32_t> edges, tris;
   DevView view{};
   void *scratch = nullptr;  // query scratch arena
@@ -111,6 +113,10 @@ struct p2m_handle {
     view.tris = (const int4 *)tris.p;
     view.nb_off = nb_off.p;
     view.nb = nb.p;
+    view.chunk_off = chunk_off.p;
+    view.chunks = (const float4 *)chunks.p;
+    view.seed = seed.p;
+    view.grid_bits = seed.p ? grid_bits : 0;
     view.nv = L.nv;
     view.depth = L.kd_depth;
     view.L = (int64_t)1 << L.kd_depth;
@@ -136,9 +142,35 @@ struct p2m_handle {
     if (e == cudaSuccess) e = tris.upload(L.tris.data(), L.tris.size());
     if (e == cudaSuccess && !L.nb_off.empty()) e = nb_off.upload(L.nb_off.data(), L.nb_off.size());
     if (e == cudaSuccess && !L.nb.empty()) e = nb.upload(L.nb.data(), L.nb.size());
+    if (e == cudaSuccess && !L.chunk_off.empty())
+      e = chunk_off.upload(L.chunk_off.data(), L.chunk_off.size());
+    if (e == cudaSuccess && !L.chunks.empty()) e = chunks.upload(L.chunks.data(), L.chunks.size());
     make_view();
+    if (e == cudaSuccess) e = make_seed_grid();
     device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
-                        row_off.n + edges.n + tris.n + nb_off.n + nb.n);
+                        row_off.n + edges.n + tris.n + nb_off.n + nb.n + chunk_off.n + chunks.n +
+                        seed.n);
+    return e;
+  }
+
+  // Seed grid of the Voronoi walk: G^3 cells over D with G = 2^k, about four
+  // cells per vertex (16 <= G <= 256); each cell holds the nearest vertex of
+  // its centre, computed on the device with the exact KD-tree search.
+  cudaError_t make_seed_grid() {
+    int k = 4;
+    while (k < 8 && ((int64_t)1 << (3 * (k + 1))) <= 4 * L.nv) ++k;
+    const size_t cells = (size_t)1 << (3 * k);
+    seed.reset();
+    cudaError_t e = cudaMalloc((void **)&seed.p, cells * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+      seed.p = nullptr;
+      return e;
+    }
+    seed.n = cells;
+    grid_bits = k;
+    make_view();
+    e = p2m::launch_seed_grid(view, seed.p, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
   }
 };
@@ -268,6 +300,7 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   t->block_threads = h->tune.block_threads;
   t->warp_cooperative = h->tune.warp_mode;
   t->nn_walk = h->tune.nn_walk;
+  t->chunked = h->tune.chunked;
   return P2M_OK;
 }
 
@@ -277,8 +310,10 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
       t->block_threads != 512)
     return P2M_ERR_INVALID_ARG;
   if (t->warp_cooperative != 0 && t->warp_cooperative != 1) return P2M_ERR_INVALID_ARG;
-  if (t->nn_walk != 0 && t->nn_walk != 1) return P2M_ERR_INVALID_ARG;
+  if (t->nn_walk < 0 || t->nn_walk > 2) return P2M_ERR_INVALID_ARG;
+  if (t->chunked != 0 && t->chunked != 1) return P2M_ERR_INVALID_ARG;
   h->tune.nn_walk = t->nn_walk;
+  h->tune.chunked = t->chunked;
   h->tune.sort_bits = t->sort_bits;
   h->tune.block_threads = t->block_threads;
   h->tune.warp_mode = t->warp_cooperative;
@@ -349,7 +384,7 @@ p2m_status p2m_timing_summary(p2m_handle *h, double out[3]) {
   return P2M_OK;
 }
 
-p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[5],
+p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t out[6],
                               void *stream) {
   p2m_status s = check_ready(h);
   if (s) return s;
@@ -361,11 +396,11 @@ p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t 
   cudaError_t e = p2m::launch_query(h->view, q, n, nullptr, nullptr, nullptr, nullptr, nullptr,
                                     nullptr, h->scratch, h->scratch_bytes, h->tune, st, nullptr,
                                     h->counters);
-  unsigned long long c[5];
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->counters, 40, cudaMemcpyDeviceToHost, st);
+  unsigned long long c[6];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c, h->counters, 48, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return from_cuda(e);
-  for (int k = 0; k < 5; ++k) out[k] = (int64_t)c[k];
+  for (int k = 0; k < 6; ++k) out[k] = (int64_t)c[k];
   return P2M_OK;
 }
 
@@ -378,7 +413,7 @@ p2m_status p2m_nearest_vertex(p2m_handle *h, const float *q, int64_t n, int32_t 
   if (!q || !vertex) return P2M_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
   return from_cuda(p2m::launch_nearest(h->view, q, n, vertex, (cudaStream_t)stream, true,
-                                       h->tune.nn_walk && h->view.nb_off ? 1 : 0));
+                                       h->view.nb_off ? h->tune.nn_walk : 0));
 }
 
 p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
@@ -692,12 +727,13 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   cudaEventCreate(&e1);
   p2m::QueryTuning best = h->tune;
   float bms = 1e30f;
-  const int bits_c[] = {12, 15, 18, 21};
+  const int bits_c[] = {9, 12, 15, 18};
   const int block_c[] = {128, 256};
+  for (int ch = 1; ch < 2; ++ch)
   for (int wm = 0; wm < 2; ++wm)
   for (int bits : bits_c)
     for (int bt : block_c) {
-      p2m_tuning t{bits, bt, wm, 1};
+      p2m_tuning t{bits, bt, wm, 2, ch};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);
@@ -729,7 +765,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -781,7 +817,8 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
   ok = ok && put_vec(f, L.kd_nodes, ck) && put_vec(f, L.kd_points, ck) &&
        put_vec(f, L.pos_of_vertex, ck) && put_vec(f, L.row_off, ck) && put_vec(f, L.entries, ck) &&
        put_vec(f, L.edge_rec, ck) && put_vec(f, L.face_rec, ck) && put_vec(f, L.edges, ck) &&
-       put_vec(f, L.tris, ck) && put_vec(f, L.nb_off, ck) && put_vec(f, L.nb, ck);
+       put_vec(f, L.tris, ck) && put_vec(f, L.nb_off, ck) && put_vec(f, L.nb, ck) &&
+       put_vec(f, L.chunk_off, ck) && put_vec(f, L.chunks, ck);
   ok = ok && fwrite(&ck, 8, 1, f) == 1;
   ok = (fclose(f) == 0) && ok;
   return ok ? P2M_OK : P2M_ERR_IO;
@@ -811,7 +848,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
          get_vec(f, L.pos_of_vertex, ck) && get_vec(f, L.row_off, ck) &&
          get_vec(f, L.entries, ck) && get_vec(f, L.edge_rec, ck) && get_vec(f, L.face_rec, ck) &&
          get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && get_vec(f, L.nb_off, ck) &&
-         get_vec(f, L.nb, ck) && fread(&stored, 8, 1, f) == 1 && stored == ck;
+         get_vec(f, L.nb, ck) && get_vec(f, L.chunk_off, ck) && get_vec(f, L.chunks, ck) &&
+         fread(&stored, 8, 1, f) == 1 && stored == ck;
   }
   fclose(f);
   if (!ok) return P2M_ERR_IO;
@@ -831,7 +869,9 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
   std::memcpy(L.kd_root, fl + 7, 24);
   if ((int64_t)L.row_off.size() != L.nv + 1 || (int64_t)L.kd_points.size() != 4 * L.nv ||
       (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
-      (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back())
+      (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back() ||
+      (int64_t)L.chunk_off.size() != L.nv + 1 ||
+      (int64_t)L.chunks.size() != 8 * (int64_t)L.chunk_off.back())
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
     cudaError_t e = h->upload_tree();

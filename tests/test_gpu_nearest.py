@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 6}), (2, {"grid": 128}),
                                     (3, {"level": 5})])
-@pytest.mark.parametrize("walk", [0, 1])
+@pytest.mark.parametrize("walk", [0, 1, 2])
 def test_nearest_vertex_matches_oracle(idx, kw, walk):
-    """Both searches: KD-tree backtracking, and KD descent + Voronoi walk
-    (queries outside D included: they fall back to backtracking)."""
+    """Every search: KD-tree backtracking, KD descent + Voronoi walk, seed
+    grid + Voronoi walk (queries outside D fall back to backtracking)."""
     import paper_2308_16084_gb300 as pg
     m = dg.workload(idx, n_queries=60000, **kw)
     mesh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin)

@@ -42,11 +42,12 @@ CASES = [(0, {}, None), (1, {"level": 5}, 60000), (2, {"grid": 128}, 60000),
 
 
 @pytest.mark.parametrize("idx,kw,n", CASES)
-@pytest.mark.parametrize("mode", [(0, 0), (1, 1), (0, 1)])
+@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 1, 1), (0, 1, 0), (1, 0, 1), (2, 0, 1),
+                                  (2, 1, 0)])
 def test_parity_workloads(pg, idx, kw, n, mode):
     m = dg.workload(idx, n_queries=n, **kw)
     mesh = build(pg, m)
-    mesh.tuning = {"nn_walk": mode[0], "warp_cooperative": mode[1]}
+    mesh.tuning = {"nn_walk": mode[0], "warp_cooperative": mode[1], "chunked": mode[2]}
     o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
     np.testing.assert_array_equal(mesh.edges(), o.edges())
     ref = o.bruteforce(m.queries)
@@ -81,13 +82,14 @@ def test_parity_against_paper_method(pg):
 @pytest.mark.parametrize("bits", [0, 12, 24])
 @pytest.mark.parametrize("threads", [64, 256, 512])
 @pytest.mark.parametrize("warp", [0, 1])
-@pytest.mark.parametrize("walk", [0, 1])
-def test_tunings_give_identical_results(pg, bits, threads, warp, walk):
+@pytest.mark.parametrize("walk", [0, 1, 2])
+@pytest.mark.parametrize("chunked", [0, 1])
+def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked):
     m = dg.workload(0, n_queries=50001)
     mesh = build(pg, m)
     base = run(mesh, m.queries)
     mesh.tuning = {"sort_bits": bits, "block_threads": threads, "warp_cooperative": warp,
-                   "nn_walk": walk}
+                   "nn_walk": walk, "chunked": chunked}
     got = run(mesh, m.queries)
     for k in ("dist", "closest", "prim_id", "prim_type", "status"):
         np.testing.assert_array_equal(got[k], base[k])
