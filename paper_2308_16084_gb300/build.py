@@ -44,13 +44,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include")]
+    extra = os.environ.get("P2M_EXTRA_NVCC_FLAGS", "").split()
     jobs = []
     for src, kind in _sources().items():
         obj = os.path.join(OUT, src + ".o")
         path = os.path.join(CSRC, src)
         if kind == "cu":
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", path, "-o", obj]
+                   "-Xptxas", "-v" if verbose else "-O3", *extra, *inc, "-c", path, "-o", obj]
         else:
             cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off",
                    *inc, "-I", "/usr/local/cuda/include", "-c", path, "-o", obj]

@@ -740,8 +740,14 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   out.nb_off.assign(nv + 1, 0);
   for (int64_t p = 0; p < nv; ++p) out.nb_off[p + 1] = out.nb_off[p] + (uint32_t)nbr[p].size();
   out.nb.resize(npairs);
+  out.nbp.resize(4 * npairs);
   for (int64_t p = 0; p < nv; ++p)
-    for (size_t k = 0; k < nbr[p].size(); ++k) out.nb[out.nb_off[p] + k] = (uint32_t)nbr[p][k];
+    for (size_t k = 0; k < nbr[p].size(); ++k) {
+      const uint32_t w = (uint32_t)nbr[p][k], j = out.nb_off[p] + (uint32_t)k;
+      out.nb[j] = w;
+      std::memcpy(&out.nbp[4 * (size_t)j], &out.kd_points[4 * (size_t)w], 12);
+      std::memcpy(&out.nbp[4 * (size_t)j + 3], &w, 4);
+    }
   const double t_flood = now_ms();
 
   // ---- flooding inspection (Alg. 1) over every edge and every face

@@ -50,6 +50,7 @@ struct Layout {
   // generators of the bisector faces of its exact cell clipped to D
   std::vector<uint32_t> nb_off;    // nv + 1
   std::vector<uint32_t> nb;
+  std::vector<float> nbp;          // per neighbour: x, y, z, row bits (parallel to nb)
   // interception table, rows in tree order
   std::vector<uint32_t> row_off;   // nv + 1
   // entry: {lo.x, lo.y, lo.z, typed id bits}, {hi.x, hi.y, hi.z, 0}

@@ -30,6 +30,16 @@ namespace {
 
 constexpr float kPruneSlack = 1.0f + 1.0f / (1 << 20);
 
+// compile-time variants of the query kernel (defaults are the tuned ones)
+#ifndef P2M_WALK_BATCH
+#define P2M_WALK_BATCH 0
+#endif
+// resident 512-thread CTAs per SM the query kernel is compiled for (caps
+// its registers); 1 leaves the register count to the compiler
+#ifndef P2M_QUERY_MIN_BLOCKS
+#define P2M_QUERY_MIN_BLOCKS 1
+#endif
+
 __device__ __forceinline__ float box_d2(float qx, float qy, float qz, float lx, float ly, float lz,
                                         float hx, float hy, float hz) {
   float dx = fmaxf(fmaxf(lx - qx, qx - hx), 0.f);
@@ -52,7 +62,7 @@ struct Work {
 template <bool COUNT = false>
 __device__ __forceinline__ int nearest_pos(const DevView &m, float qx, float qy, float qz,
                                            Work *wk = nullptr) {
-  int best = -1, bid = 0x7fffffff;
+  int best = -1;
   float bx = 0.f, by = 0.f, bz = 0.f, bd2 = FLT_MAX;
   float wx = 0.f, wy = 0.f, wz = 0.f;  // q - best
   int stk[48];
@@ -67,18 +77,16 @@ __device__ __forceinline__ int nearest_pos(const DevView &m, float qx, float qy,
       if (COUNT) wk->points += (int)(p1 - p0);
       for (int64_t p = p0; p < p1; ++p) {
         const float4 c = __ldg(&m.kd_points[p]);
-        const int cid = __float_as_int(c.w);
         bool take;
         if (best < 0) {
           take = true;
         } else {
           const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
           const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
-          take = lhs > 0.f || (lhs == 0.f && cid < bid);
+          take = lhs > 0.f || (lhs == 0.f && (int)p < best);
         }
         if (take) {
           best = (int)p;
-          bid = cid;
           bx = c.x;
           by = c.y;
           bz = c.z;
@@ -167,21 +175,20 @@ __device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy
     const float d1 = box_d2(qx, qy, qz, B.z, B.w, C.x, C.y, C.z, C.w);
     node = 2 * node + (d1 < d0 ? 2 : 1);
   }
-  int best = -1, bid = 0x7fffffff;
+  int best = -1;
   float bx = 0.f, by = 0.f, bz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+  // exact ties go to the lower KD-tree row, as in the backtracking search
   auto offer = [&](int p, float4 c) {
-    const int cid = __float_as_int(c.w);
     bool take;
     if (best < 0) {
       take = true;
     } else {
       const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
       const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
-      take = lhs > 0.f || (lhs == 0.f && cid < bid);
+      take = lhs > 0.f || (lhs == 0.f && p < best);
     }
     if (take) {
       best = p;
-      bid = cid;
       bx = c.x;
       by = c.y;
       bz = c.z;
@@ -203,9 +210,10 @@ __device__ __forceinline__ int nearest_walk(const DevView &m, float qx, float qy
     const int cur = best;
     const uint32_t o0 = __ldg(&m.nb_off[cur]), o1 = __ldg(&m.nb_off[cur + 1]);
     if (COUNT) wk->points += (int)(o1 - o0);
+    // the neighbour records carry their positions: one load per neighbour
     for (uint32_t k = o0; k < o1; ++k) {
-      const int w = (int)__ldg(&m.nb[k]);
-      offer(w, __ldg(&m.kd_points[w]));
+      const float4 c = __ldg(&m.nbp[k]);
+      offer(__float_as_int(c.w), c);
     }
     if (best == cur) return best;
   }
@@ -266,28 +274,99 @@ __global__ void k_bucket_count(const float *__restrict__ q, int64_t n, SortParam
   key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
 }
 
-// exclusive scan of hist[0..nb) into off[0..nb), one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) k_bucket_scan(const uint32_t *__restrict__ hist,
-                                                     uint32_t *__restrict__ off, int nb) {
-  __shared__ uint32_t part[1024];
-  const int t = threadIdx.x;
-  const int per = (nb + 1023) / 1024;
-  const int b0 = t * per, b1 = min(nb, b0 + per);
-  uint32_t s = 0;
-  for (int b = b0; b < b1; ++b) s += hist[b];
-  part[t] = s;
+// Exclusive scan of hist[0..nb) into off[0..nb) over many CTAs: every CTA
+// owns a tile of kScanTile buckets (16 per thread); pass 1 sums tiles, pass
+// 2 scans the tile sums in one CTA, pass 3 scans inside every tile and adds
+// the tile's offset.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
+constexpr int kScanTile = kScanThreads * kScanPer;
+constexpr int kMaxScanTiles = 4096;  // nb <= 2^24
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[wid] = inc;
   __syncthreads();
-  for (int d = 1; d < 1024; d <<= 1) {
-    uint32_t v = t >= d ? part[t - d] : 0u;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < kScanThreads / 32 ? wsum[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) wsum[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1 && total) *total = wi;
   }
-  uint32_t run = part[t] - s;
-  for (int b = b0; b < b1; ++b) {
-    off[b] = run;
-    run += hist[b];
+  __syncthreads();
+  const uint32_t r = inc - v + wsum[wid];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t *__restrict__ hist,
+                                                             uint32_t *__restrict__ tile_sum,
+                                                             int nb) {
+  const int64_t b0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (b0 + k < nb) s += hist[b0 + k];
+  __shared__ uint32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile_sums(uint32_t *__restrict__ tile_sum,
+                                                                 int ntiles) {
+  // exclusive scan in place, one CTA, kScanPer tiles per thread
+  const int t0 = threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = t0 + k < ntiles ? tile_sum[t0 + k] : 0u;
+    s += v[k];
   }
+  uint32_t run = block_exclusive_scan(s, nullptr);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (t0 + k < ntiles) tile_sum[t0 + k] = run;
+    run += v[k];
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t *__restrict__ hist,
+                                                             const uint32_t *__restrict__ tile_off,
+                                                             uint32_t *__restrict__ off, int nb) {
+  const int64_t b0 = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  uint32_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = b0 + k < nb ? hist[b0 + k] : 0u;
+    s += v[k];
+  }
+  uint32_t run = block_exclusive_scan(s, nullptr) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (b0 + k < nb) off[b0 + k] = run;
+    run += v[k];
+  }
+}
+
+// off = exclusive scan of hist (nb buckets); tiles: kMaxScanTiles u32 scratch
+inline void bucket_scan(const uint32_t *hist, uint32_t *off, uint32_t *tiles, int nb,
+                        cudaStream_t stream) {
+  const int ntiles = (nb + kScanTile - 1) / kScanTile;
+  k_scan_tiles<<<ntiles, kScanThreads, 0, stream>>>(hist, tiles, nb);
+  k_scan_tile_sums<<<1, kScanThreads, 0, stream>>>(tiles, ntiles);
+  k_scan_apply<<<ntiles, kScanThreads, 0, stream>>>(hist, tiles, off, nb);
 }
 
 __global__ void k_bucket_scatter(const float *__restrict__ q, int64_t n,
@@ -405,9 +484,8 @@ __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, 
   if (COUNT) wk->chunks += (int)(c1 - c0);
   for (uint32_t c = c0; c < c1; ++c) {
     const float4 lo = __ldg(&m.chunks[2 * (size_t)c]);
-    if (qx < lo.x || qy < lo.y || qz < lo.z) continue;
-    const float4 hi = __ldg(&m.chunks[2 * (size_t)c + 1]);
-    if (qx > hi.x || qy > hi.y || qz > hi.z) continue;
+    const float4 hi = __ldg(&m.chunks[2 * (size_t)c + 1]);  // same sector as lo
+    if (qx < lo.x || qy < lo.y || qz < lo.z || qx > hi.x || qy > hi.y || qz > hi.z) continue;
     const uint32_t first = (uint32_t)__float_as_int(lo.w), cnt = (uint32_t)__float_as_int(hi.w);
     if (COUNT) wk->entries += (int)cnt;
     for (uint32_t j = first; j < first + cnt; ++j) test_entry<COUNT>(m, qx, qy, qz, j, r, wk);
@@ -442,7 +520,8 @@ __device__ __forceinline__ void store_result(int64_t o, const Best &r, bool ok, 
   if (status) status[o] = st;
 }
 
-__global__ void k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
+__global__ void __launch_bounds__(512, P2M_QUERY_MIN_BLOCKS)
+k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
                         float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
                         uint8_t *status, int walk, int chunked) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,7 +558,7 @@ template <bool COUNT>
 __device__ __forceinline__ int warp_nearest(const DevView &m, float qx, float qy, float qz,
                                             bool active, WarpSmem &ws, Work *wk) {
   const unsigned full = 0xffffffffu;
-  int best = -1, bid = 0x7fffffff;
+  int best = -1;
   float bx = 0.f, by = 0.f, bz = 0.f, bd2 = FLT_MAX;
   float wx = 0.f, wy = 0.f, wz = 0.f;
   const int64_t nleaf0 = m.L - 1;
@@ -492,18 +571,16 @@ __device__ __forceinline__ int warp_nearest(const DevView &m, float qx, float qy
       if (COUNT && active) wk->points += (int)(p1 - p0);
       for (int64_t p = p0; p < p1; ++p) {
         const float4 c = __ldg(&m.kd_points[p]);
-        const int cid = __float_as_int(c.w);
         bool take;
         if (best < 0) {
           take = true;
         } else {
           const float ux = c.x - bx, uy = c.y - by, uz = c.z - bz;
           const float lhs = 2.f * (wx * ux + wy * uy + wz * uz) - (ux * ux + uy * uy + uz * uz);
-          take = lhs > 0.f || (lhs == 0.f && cid < bid);
+          take = lhs > 0.f || (lhs == 0.f && (int)p < best);
         }
         if (take && active) {
           best = (int)p;
-          bid = cid;
           bx = c.x;
           by = c.y;
           bz = c.z;
@@ -885,7 +962,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 size_t query_scratch_bytes(int64_t n, int sort_bits) {
   size_t nb = sort_bits > 0 ? ((size_t)1 << sort_bits) : 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + 256;
+  return al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + al(4 * kMaxScanTiles) + 256;
 }
 
 cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
@@ -908,6 +985,8 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     uint32_t *hist = (uint32_t *)base;
     base += al(4 * nb);
     uint32_t *off = (uint32_t *)base;
+    base += al(4 * nb);
+    uint32_t *tiles = (uint32_t *)base;
     SortParams sp;
     for (int d = 0; d < 3; ++d) {
       sp.lo[d] = m.dom_lo[d];
@@ -917,7 +996,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     sp.shift = 30 - tune.sort_bits;
     cudaMemsetAsync(hist, 0, 4 * nb, stream);
     k_bucket_count<<<blocks_for(n, T), T, 0, stream>>>(q, n, sp, hist, key_rank);
-    k_bucket_scan<<<1, 1024, 0, stream>>>(hist, off, (int)nb);
+    bucket_scan(hist, off, tiles, (int)nb, stream);
     k_bucket_scatter<<<blocks_for(n, T), T, 0, stream>>>(q, n, key_rank, off, sorted);
   } else {
     k_identity<<<blocks_for(n, T), T, 0, stream>>>(q, n, sorted);
@@ -976,7 +1055,8 @@ cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
 size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n_meshes << sort_bits;
-  return al(16 * (size_t)total) + al(8 * (size_t)total) + 2 * al(4 * nb) + 256;
+  return al(16 * (size_t)total) + al(8 * (size_t)total) + 2 * al(4 * nb) +
+         al(4 * kMaxScanTiles) + 256;
 }
 
 int batch_occupancy(int block_threads) {
@@ -1002,10 +1082,12 @@ cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_
   uint32_t *hist = (uint32_t *)base;
   base += al(4 * nb);
   uint32_t *off = (uint32_t *)base;
+  base += al(4 * nb);
+  uint32_t *tiles = (uint32_t *)base;
   const int T = 256;
   cudaMemsetAsync(hist, 0, 4 * nb, stream);
   k_batch_count<<<blocks_for(total, T), T, 0, stream>>>(d, total, t.sort_bits, hist, key_rank);
-  k_bucket_scan<<<1, 1024, 0, stream>>>(hist, off, (int)nb);
+  bucket_scan(hist, off, tiles, (int)nb, stream);
   k_batch_scatter<<<blocks_for(total, T), T, 0, stream>>>(d, total, key_rank, off, sorted);
   cudaMemsetAsync(queue_head, 0, sizeof(unsigned int), stream);
   k_batch_query<<<grid, t.block_threads, 0, stream>>>(d, sorted, total, t.tile, queue_head,

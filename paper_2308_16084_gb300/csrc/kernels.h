@@ -19,6 +19,7 @@ struct DevView {
   const int4 *tris;         // faces (a, b, c, 0)
   const uint32_t *nb_off;   // nv + 1: Voronoi neighbours of each row (CSR)
   const uint32_t *nb;       // neighbour rows
+  const float4 *nbp;        // neighbour positions, parallel to nb: x, y, z, row bits
   const uint32_t *chunk_off;  // nv + 1: chunks of each row (CSR)
   const float4 *chunks;       // 2 per chunk: {lo, first entry}, {hi, count}
   const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre

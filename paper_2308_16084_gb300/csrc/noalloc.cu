@@ -26,9 +26,10 @@ constexpr int64_t kNoallocMaxQueries = (int64_t)1 << 20;
 constexpr int kNoallocSortBits = 16;
 // layout of launch_query's scratch for kNoallocMaxQueries points and
 // 2^kNoallocSortBits buckets: sorted float4 + (bucket, rank) pairs +
-// histogram + offsets, each 256-byte aligned, plus the alignment slack
+// histogram + offsets + 4096 scan-tile sums, each 256-byte aligned, plus the
+// alignment slack
 constexpr size_t kNoallocBytes = (size_t)16 * kNoallocMaxQueries + (size_t)8 * kNoallocMaxQueries +
-                                 2 * ((size_t)4 << kNoallocSortBits) + 256;
+                                 2 * ((size_t)4 << kNoallocSortBits) + (size_t)4 * 4096 + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 

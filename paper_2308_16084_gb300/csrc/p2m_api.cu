@@ -17,6 +17,10 @@
 #include "builder.h"
 #include "kernels.h"
 
+#ifndef P2M_GRID_PER_VERTEX
+#define P2M_GRID_PER_VERTEX 32
+#endif
+
 namespace {
 
 using p2m::DevView;
@@ -69,7 +73,7 @@ struct p2m_handle {
   DevBuf<float> kd_nodes, kd_points, entries, edge_rec, face_rec;
   DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed;
   int grid_bits = 0;
-  DevBuf<float> chunks;
+  DevBuf<float> chunks, nbp;
   DevBuf<int32_t> edges, tris;
   DevView view{};
   void *scratch = nullptr;  // query scratch arena
@@ -113,6 +117,7 @@ struct p2m_handle {
     view.tris = (const int4 *)tris.p;
     view.nb_off = nb_off.p;
     view.nb = nb.p;
+    view.nbp = (const float4 *)nbp.p;
     view.chunk_off = chunk_off.p;
     view.chunks = (const float4 *)chunks.p;
     view.seed = seed.p;
@@ -142,6 +147,7 @@ struct p2m_handle {
     if (e == cudaSuccess) e = tris.upload(L.tris.data(), L.tris.size());
     if (e == cudaSuccess && !L.nb_off.empty()) e = nb_off.upload(L.nb_off.data(), L.nb_off.size());
     if (e == cudaSuccess && !L.nb.empty()) e = nb.upload(L.nb.data(), L.nb.size());
+    if (e == cudaSuccess && !L.nbp.empty()) e = nbp.upload(L.nbp.data(), L.nbp.size());
     if (e == cudaSuccess && !L.chunk_off.empty())
       e = chunk_off.upload(L.chunk_off.data(), L.chunk_off.size());
     if (e == cudaSuccess && !L.chunks.empty()) e = chunks.upload(L.chunks.data(), L.chunks.size());
@@ -149,16 +155,17 @@ struct p2m_handle {
     if (e == cudaSuccess) e = make_seed_grid();
     device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
                         row_off.n + edges.n + tris.n + nb_off.n + nb.n + chunk_off.n + chunks.n +
-                        seed.n);
+                        seed.n + nbp.n);
     return e;
   }
 
-  // Seed grid of the Voronoi walk: G^3 cells over D with G = 2^k, about four
-  // cells per vertex (16 <= G <= 256); each cell holds the nearest vertex of
-  // its centre, computed on the device with the exact KD-tree search.
+  // Seed grid of the Voronoi walk: G^3 cells over D with G = 2^k, up to
+  // P2M_GRID_PER_VERTEX cells per vertex (16 <= G <= 256); each cell holds
+  // the nearest vertex of its centre, computed on the device with the exact
+  // KD-tree search.
   cudaError_t make_seed_grid() {
     int k = 4;
-    while (k < 8 && ((int64_t)1 << (3 * (k + 1))) <= 4 * L.nv) ++k;
+    while (k < 8 && ((int64_t)1 << (3 * (k + 1))) <= P2M_GRID_PER_VERTEX * L.nv) ++k;
     const size_t cells = (size_t)1 << (3 * k);
     seed.reset();
     cudaError_t e = cudaMalloc((void **)&seed.p, cells * sizeof(uint32_t));
@@ -727,7 +734,7 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   cudaEventCreate(&e1);
   p2m::QueryTuning best = h->tune;
   float bms = 1e30f;
-  const int bits_c[] = {9, 12, 15, 18};
+  const int bits_c[] = {12, 15, 18, 21, 24};
   const int block_c[] = {128, 256};
   for (int ch = 1; ch < 2; ++ch)
   for (int wm = 0; wm < 2; ++wm)
@@ -765,7 +772,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -818,7 +825,7 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
        put_vec(f, L.pos_of_vertex, ck) && put_vec(f, L.row_off, ck) && put_vec(f, L.entries, ck) &&
        put_vec(f, L.edge_rec, ck) && put_vec(f, L.face_rec, ck) && put_vec(f, L.edges, ck) &&
        put_vec(f, L.tris, ck) && put_vec(f, L.nb_off, ck) && put_vec(f, L.nb, ck) &&
-       put_vec(f, L.chunk_off, ck) && put_vec(f, L.chunks, ck);
+       put_vec(f, L.chunk_off, ck) && put_vec(f, L.chunks, ck) && put_vec(f, L.nbp, ck);
   ok = ok && fwrite(&ck, 8, 1, f) == 1;
   ok = (fclose(f) == 0) && ok;
   return ok ? P2M_OK : P2M_ERR_IO;
@@ -849,7 +856,7 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
          get_vec(f, L.entries, ck) && get_vec(f, L.edge_rec, ck) && get_vec(f, L.face_rec, ck) &&
          get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && get_vec(f, L.nb_off, ck) &&
          get_vec(f, L.nb, ck) && get_vec(f, L.chunk_off, ck) && get_vec(f, L.chunks, ck) &&
-         fread(&stored, 8, 1, f) == 1 && stored == ck;
+         get_vec(f, L.nbp, ck) && fread(&stored, 8, 1, f) == 1 && stored == ck;
   }
   fclose(f);
   if (!ok) return P2M_ERR_IO;
@@ -871,7 +878,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
       (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
       (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back() ||
       (int64_t)L.chunk_off.size() != L.nv + 1 ||
-      (int64_t)L.chunks.size() != 8 * (int64_t)L.chunk_off.back())
+      (int64_t)L.chunks.size() != 8 * (int64_t)L.chunk_off.back() ||
+      L.nbp.size() != 4 * L.nb.size())
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
     cudaError_t e = h->upload_tree();
