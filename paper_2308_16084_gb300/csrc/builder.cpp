@@ -12,6 +12,7 @@
 // puts just outside the exact cell of its nearest vertex therefore still
 // finds its primitive in the list of the vertex the kernel picks.
 #include "builder.h"
+#include "quant.h"
 
 #include <algorithm>
 #include <atomic>
@@ -978,24 +979,28 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       return kx < ky || (kx == ky && (uint32_t)x.tid < (uint32_t)y.tid);
     });
   });
-  out.entries.resize(8 * total);
   int64_t maxl = 0;
   for (int64_t p = 0; p < nv; ++p) maxl = std::max<int64_t>(maxl, out.row_off[p + 1] - out.row_off[p]);
-  parallel_for(total, threads, 1 << 16, [&](int64_t j, int) {
-    float *o = &out.entries[8 * j];
-    const Rec &r = all[j];
-    o[0] = r.box[0]; o[1] = r.box[1]; o[2] = r.box[2];
-    std::memcpy(&o[3], &r.tid, 4);
-    o[4] = r.box[3]; o[5] = r.box[4]; o[6] = r.box[5]; o[7] = 0.f;
-  });
 
-  // ---- chunks of every row
+  // ---- chunks of every row, and the 16-bit boxes
+  for (int d = 0; d < 3; ++d) {
+    float flo = (float)(Dlo[d] - 4 * delta), fhi = (float)(Dhi[d] + 4 * delta);
+    out.qframe_lo[d] = flo;
+    out.qframe_step[d] = q_step(flo, fhi);
+  }
   out.chunk_off.assign(nv + 1, 0);
   for (int64_t p = 0; p < nv; ++p) {
     uint32_t len = out.row_off[p + 1] - out.row_off[p];
     out.chunk_off[p + 1] = out.chunk_off[p] + (len + Layout::kChunk - 1) / Layout::kChunk;
   }
-  out.chunks.resize(8 * (size_t)out.chunk_off[nv]);
+  out.chunks.assign(4 * (size_t)out.chunk_off[nv], 0u);
+  out.entries.assign(4 * (size_t)total, 0u);
+  std::atomic<int64_t> bad_boxes{0};
+  auto pack = [](const uint32_t *q, uint32_t *w) {
+    w[0] = q[0] | q[1] << 16;
+    w[1] = q[2] | q[3] << 16;
+    w[2] = q[4] | q[5] << 16;
+  };
   parallel_for(nv, threads, 1024, [&](int64_t p, int) {
     uint32_t c = out.chunk_off[p];
     for (uint32_t j = out.row_off[p]; j < out.row_off[p + 1]; j += Layout::kChunk, ++c) {
@@ -1006,13 +1011,38 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
           lo[d] = std::min(lo[d], all[k].box[d]);
           hi[d] = std::max(hi[d], all[k].box[3 + d]);
         }
-      float *o = &out.chunks[8 * (size_t)c];
-      o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2];
-      std::memcpy(&o[3], &j, 4);
-      o[4] = hi[0]; o[5] = hi[1]; o[6] = hi[2];
-      std::memcpy(&o[7], &cnt, 4);
+      uint32_t q[6];
+      for (int d = 0; d < 3; ++d) {
+        q[d] = q_enc_lo(lo[d], out.qframe_lo[d], out.qframe_step[d]);
+        q[3 + d] = q_enc_hi(hi[d], out.qframe_lo[d], out.qframe_step[d]);
+      }
+      uint32_t *cw = &out.chunks[4 * (size_t)c];
+      pack(q, cw);
+      float clo[3], chi[3], cstep[3];
+      q_unpack(cw[0], cw[1], cw[2], out.qframe_lo, out.qframe_step, clo, chi);
+      for (int d = 0; d < 3; ++d) {
+        if (clo[d] > lo[d] || chi[d] < hi[d]) ++bad_boxes;
+        cstep[d] = q_step(clo[d], chi[d]);
+      }
+      for (uint32_t k = j; k < j + cnt; ++k) {
+        uint32_t *ew = &out.entries[4 * (size_t)k];
+        ew[0] = (uint32_t)all[k].tid;
+        for (int d = 0; d < 3; ++d) {
+          q[d] = q_enc_lo(all[k].box[d], clo[d], cstep[d]);
+          q[3 + d] = q_enc_hi(all[k].box[3 + d], clo[d], cstep[d]);
+        }
+        pack(q, ew + 1);
+        float elo[3], ehi[3];
+        q_unpack(ew[1], ew[2], ew[3], clo, cstep, elo, ehi);
+        for (int d = 0; d < 3; ++d)
+          if (elo[d] > all[k].box[d] || ehi[d] < all[k].box[3 + d]) ++bad_boxes;
+      }
     }
   });
+  if (bad_boxes.load()) {
+    err = "internal error: a quantised Region box does not contain its box";
+    return 5;
+  }
 
   // ---- geometry records
   out.edges = M.E;

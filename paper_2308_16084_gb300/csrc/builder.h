@@ -53,16 +53,20 @@ struct Layout {
   std::vector<float> nbp;          // per neighbour: x, y, z, row bits (parallel to nb)
   // interception table, rows in tree order
   std::vector<uint32_t> row_off;   // nv + 1
-  // entry: {lo.x, lo.y, lo.z, typed id bits}, {hi.x, hi.y, hi.z, 0}
-  //   typed id = type << 30 | id   (type 1 = edge, 2 = face)
-  std::vector<float> entries;      // n_entries * 8
-  // entries of each row are in spatial (Morton) order of their box centres
-  // and grouped into chunks of up to kChunk; chunk c of row r:
-  //   {lo.x, lo.y, lo.z, first entry bits}, {hi.x, hi.y, hi.z, entry count bits}
-  // (the union of its entries' boxes: a one-level R-tree per list, Sec. 4.6)
+  // Entries of each row are in spatial (Morton) order of their Region-box
+  // centres and grouped into chunks of up to kChunk consecutive entries (a
+  // one-level R-tree per list, Sec. 4.6).  Boxes are 16-bit (quant.h):
+  //   chunk c: {lo.x | lo.y<<16, lo.z | hi.x<<16, hi.y | hi.z<<16, 0}
+  //            in the frame qframe (D widened by 4 delta)
+  //   entry j: {typed id, lo.x | lo.y<<16, lo.z | hi.x<<16, hi.y | hi.z<<16}
+  //            in the decoded box of its chunk; typed id = type << 30 | id
+  //            (type 1 = edge, 2 = face)
+  // Entry j of row r belongs to chunk chunk_off[r] + (j - row_off[r]) / kChunk.
   static constexpr int kChunk = 8;
+  std::vector<uint32_t> entries;   // n_entries * 4
   std::vector<uint32_t> chunk_off; // nv + 1
-  std::vector<float> chunks;       // n_chunks * 8
+  std::vector<uint32_t> chunks;    // n_chunks * 4
+  float qframe_lo[3] = {0, 0, 0}, qframe_step[3] = {0, 0, 0};
   // geometry records
   //   edge e: {a.x, a.y, a.z, 1/|b-a|^2}, {b.x-a.x, b.y-a.y, b.z-a.z, 0}
   //   face f: {a, A}, {b-a, B}, {c-a, C} with the projection weights

@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "quant.h"
 
 namespace p2m {
 namespace {
@@ -392,17 +393,19 @@ struct Best {
   float w0, w1, w2;
 };
 
-// a4 + a6/a7 for list entry j: Region-box test, then the gated distance.
-// Exact ties keep the lower typed id (vertex < edge < face, then lower id),
-// so the result does not depend on the order of the list.
+// a4 + a6/a7 for list entry j: Region-box test (box decoded in its chunk's
+// frame clo/cstep), then the gated distance.  Exact ties keep the lower
+// typed id (vertex < edge < face, then lower id), so the result does not
+// depend on the order of the list.
 template <bool COUNT>
 __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy, float qz,
-                                           uint32_t j, Best &r, Work *wk) {
-  const float4 lo = __ldg(&m.entries[2 * (size_t)j]);
-  if (qx < lo.x || qy < lo.y || qz < lo.z) return;
-  const float4 hi = __ldg(&m.entries[2 * (size_t)j + 1]);
-  if (qx > hi.x || qy > hi.y || qz > hi.z) return;
-  const uint32_t tid = (uint32_t)__float_as_int(lo.w);
+                                           uint32_t j, const float *clo, const float *cstep,
+                                           Best &r, Work *wk) {
+  const uint4 e = __ldg(&m.entries[j]);
+  float lo[3], hi[3];
+  q_unpack(e.y, e.z, e.w, clo, cstep, lo, hi);
+  if (qx < lo[0] || qy < lo[1] || qz < lo[2] || qx > hi[0] || qy > hi[1] || qz > hi[2]) return;
+  const uint32_t tid = e.x;
   const uint32_t id = tid & 0x3fffffffu;
   if ((tid >> 30) == 1u) {
     if (COUNT) ++wk->edges;
@@ -455,6 +458,31 @@ __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy,
   }
 }
 
+// a3..a8 for a query whose nearest vertex is row v (r already holds v).
+// chunked: test each chunk box first (one-level R-tree of the list,
+// Sec. 4.6); otherwise test the Region box of every entry.
+template <bool COUNT>
+__device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, float qz, int v,
+                                          bool chunked, Best &r, Work *wk) {
+  const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
+  const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
+  if (COUNT) wk->chunks += chunked ? (int)(c1 - c0) : 0;
+  uint32_t first = j0;
+  for (uint32_t c = c0; c < c1; ++c, first += 8) {
+    const uint4 cw = __ldg(&m.chunks[c]);
+    float clo[3], chi[3];
+    q_unpack(cw.x, cw.y, cw.z, m.qlo, m.qstep, clo, chi);
+    if (chunked &&
+        (qx < clo[0] || qy < clo[1] || qz < clo[2] || qx > chi[0] || qy > chi[1] || qz > chi[2]))
+      continue;
+    const float cstep[3] = {q_step(clo[0], chi[0]), q_step(clo[1], chi[1]),
+                            q_step(clo[2], chi[2])};
+    const uint32_t last = min(first + 8u, j1);
+    if (COUNT) wk->entries += (int)(last - first);
+    for (uint32_t j = first; j < last; ++j) test_entry<COUNT>(m, qx, qy, qz, j, clo, cstep, r, wk);
+  }
+}
+
 template <bool COUNT = false>
 __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
                                           Best &r, Work *wk = nullptr, int walk = 2,
@@ -472,24 +500,7 @@ __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, 
     r.w1 = 0.f;
     r.w2 = 0.f;
   }
-  const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
-  if (!chunked || !m.chunks) {
-    if (COUNT) wk->entries += (int)(j1 - j0);
-    for (uint32_t j = j0; j < j1; ++j) test_entry<COUNT>(m, qx, qy, qz, j, r, wk);
-    return;
-  }
-  // one-level R-tree: chunk boxes first, then the entries of the chunks
-  // whose box contains q
-  const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
-  if (COUNT) wk->chunks += (int)(c1 - c0);
-  for (uint32_t c = c0; c < c1; ++c) {
-    const float4 lo = __ldg(&m.chunks[2 * (size_t)c]);
-    const float4 hi = __ldg(&m.chunks[2 * (size_t)c + 1]);  // same sector as lo
-    if (qx < lo.x || qy < lo.y || qz < lo.z || qx > hi.x || qy > hi.y || qz > hi.z) continue;
-    const uint32_t first = (uint32_t)__float_as_int(lo.w), cnt = (uint32_t)__float_as_int(hi.w);
-    if (COUNT) wk->entries += (int)cnt;
-    for (uint32_t j = first; j < first + cnt; ++j) test_entry<COUNT>(m, qx, qy, qz, j, r, wk);
-  }
+  scan_list<COUNT>(m, qx, qy, qz, v, chunked, r, wk);
 }
 
 __device__ __forceinline__ bool finite3(float x, float y, float z) {
@@ -545,13 +556,10 @@ k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
 // One warp answers 32 Morton-adjacent queries together.  The KD-tree walk is
 // shared: a node is entered when any lane's pruning bound admits it
 // (ballots), so the warp never diverges on the tree; every lane keeps its own
-// best vertex.  The list scan visits each distinct nearest vertex of the
-// warp once: its entries are staged 32 at a time into shared memory with
-// coalesced loads, and the lanes whose nearest vertex it is test them.
+// best vertex and then scans its own list.
 constexpr int kWarpStack = 48;
 struct WarpSmem {
   int stack[kWarpStack];
-  float4 stage[64];
 };
 
 template <bool COUNT>
@@ -645,8 +653,6 @@ template <bool COUNT>
 __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy, float qz,
                                            bool active, WarpSmem &ws, Best &r, Work *wk,
                                            int walk) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
   int v;
   if (walk) {
     v = active ? nearest_walk<COUNT>(m, qx, qy, qz, wk, walk == 2) : 0;
@@ -666,72 +672,7 @@ __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy,
     r.w1 = 0.f;
     r.w2 = 0.f;
   }
-  unsigned todo = __ballot_sync(full, active);
-  while (todo) {
-    const int leader = __ffs(todo) - 1;
-    const int vv = __shfl_sync(full, v, leader);
-    const unsigned grp = __ballot_sync(full, active && v == vv) & todo;
-    todo &= ~grp;
-    const bool mine = (grp >> lane) & 1u;
-    const uint32_t j0 = __ldg(&m.row_off[vv]), j1 = __ldg(&m.row_off[vv + 1]);
-    if (COUNT && mine) wk->entries += (int)(j1 - j0);
-    for (uint32_t base = j0; base < j1; base += 32) {
-      const int cnt = (int)min(32u, j1 - base);
-      __syncwarp();
-      if (lane < cnt) {
-        ws.stage[2 * lane] = __ldg(&m.entries[2 * (size_t)(base + lane)]);
-        ws.stage[2 * lane + 1] = __ldg(&m.entries[2 * (size_t)(base + lane) + 1]);
-      }
-      __syncwarp();
-      if (mine) {
-        for (int k = 0; k < cnt; ++k) {
-          const float4 lo = ws.stage[2 * k];
-          if (qx < lo.x || qy < lo.y || qz < lo.z) continue;
-          const float4 hi = ws.stage[2 * k + 1];
-          if (qx > hi.x || qy > hi.y || qz > hi.z) continue;
-          const uint32_t tid = (uint32_t)__float_as_int(lo.w);
-          const uint32_t id = tid & 0x3fffffffu;
-          if ((tid >> 30) == 1u) {
-            if (COUNT) ++wk->edges;
-            const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
-            const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
-            const float ex = qx - a.x, ey = qy - a.y, ez = qz - a.z;
-            const float t = (ex * d.x + ey * d.y + ez * d.z) * a.w;
-            if (t > 0.f && t < 1.f) {
-              const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
-              const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
-              const float d2 = fx * fx + fy * fy + fz * fz;
-              if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
-                r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
-                r.w0 = 1.f - t; r.w1 = t; r.w2 = 0.f;
-              }
-            }
-          } else {
-            if (COUNT) ++wk->faces;
-            const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
-            const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
-            const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
-            const float ex = qx - a.x, ey = qy - a.y, ez = qz - a.z;
-            const float p1 = ex * e1.x + ey * e1.y + ez * e1.z;
-            const float p2 = ex * e2.x + ey * e2.y + ez * e2.z;
-            const float s = a.w * p1 - e1.w * p2;
-            const float t = e2.w * p2 - e1.w * p1;
-            if (s > 0.f && t > 0.f && s + t < 1.f) {
-              const float cx = a.x + s * e1.x + t * e2.x;
-              const float cy = a.y + s * e1.y + t * e2.y;
-              const float cz = a.z + s * e1.z + t * e2.z;
-              const float fx = qx - cx, fy = qy - cy, fz = qz - cz;
-              const float d2 = fx * fx + fy * fy + fz * fz;
-              if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
-                r.d2 = d2; r.cx = cx; r.cy = cy; r.cz = cz; r.tid = tid;
-                r.w0 = 1.f - s - t; r.w1 = s; r.w2 = t;
-              }
-            }
-          }
-        }
-      }
-    }
-  }
+  if (active) scan_list<COUNT>(m, qx, qy, qz, v, true, r, wk);
 }
 
 template <bool COUNT>

@@ -12,7 +12,7 @@ struct DevView {
   const float4 *kd_nodes;   // (L-1) * 3: child boxes of every internal node
   const float4 *kd_points;  // nv: x, y, z, original vertex id bits
   const uint32_t *row_off;  // nv + 1
-  const float4 *entries;    // 2 per entry: {lo, typed id bits}, {hi, 0}
+  const uint4 *entries;     // per entry: typed id + 16-bit box in its chunk's box
   const float4 *edge_rec;   // 2 per edge
   const float4 *face_rec;   // 3 per face
   const int2 *edges;        // canonical edges
@@ -21,7 +21,8 @@ struct DevView {
   const uint32_t *nb;       // neighbour rows
   const float4 *nbp;        // neighbour positions, parallel to nb: x, y, z, row bits
   const uint32_t *chunk_off;  // nv + 1: chunks of each row (CSR)
-  const float4 *chunks;       // 2 per chunk: {lo, first entry}, {hi, count}
+  const uint4 *chunks;        // per chunk: 16-bit box in the frame below
+  float qlo[3], qstep[3];     // frame of the chunk boxes (quant.h)
   const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre
   int grid_bits;              // G = 2^grid_bits cells per axis over D (0 = no grid)
   int64_t nv;
@@ -34,7 +35,7 @@ struct DevView {
 struct QueryTuning {
   int sort_bits = 18;
   int block_threads = 256;
-  int warp_mode = 0;  // 0: one thread per query, 1: warp-cooperative
+  int warp_mode = 0;  // 0: one thread per query, 1: warp-cooperative KD walk
   int nn_walk = 2;    // 0: KD-tree backtracking, 1: KD descent + Voronoi walk,
                       // 2: seed-grid lookup + Voronoi walk
   int chunked = 1;    // 0: scan every list entry, 1: test chunk boxes first

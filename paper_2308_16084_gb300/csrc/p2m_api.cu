@@ -16,6 +16,7 @@
 #include "../../include/p2m.h"
 #include "builder.h"
 #include "kernels.h"
+#include "quant.h"
 
 #ifndef P2M_GRID_PER_VERTEX
 #define P2M_GRID_PER_VERTEX 32
@@ -70,10 +71,12 @@ bool have_device() {
 struct p2m_handle {
   int device = -1;          // -1: host-only handle (tables built, no queries)
   Layout L;                 // host copy of the layout
-  DevBuf<float> kd_nodes, kd_points, entries, edge_rec, face_rec;
+  DevBuf<float> kd_nodes, kd_points, edge_rec, face_rec;
+  DevBuf<uint32_t> entries;
   DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed;
   int grid_bits = 0;
-  DevBuf<float> chunks, nbp;
+  DevBuf<uint32_t> chunks;
+  DevBuf<float> nbp;
   DevBuf<int32_t> edges, tris;
   DevView view{};
   void *scratch = nullptr;  // query scratch arena
@@ -110,7 +113,7 @@ struct p2m_handle {
     view.kd_nodes = (const float4 *)kd_nodes.p;
     view.kd_points = (const float4 *)kd_points.p;
     view.row_off = row_off.p;
-    view.entries = (const float4 *)entries.p;
+    view.entries = (const uint4 *)entries.p;
     view.edge_rec = (const float4 *)edge_rec.p;
     view.face_rec = (const float4 *)face_rec.p;
     view.edges = (const int2 *)edges.p;
@@ -119,7 +122,11 @@ struct p2m_handle {
     view.nb = nb.p;
     view.nbp = (const float4 *)nbp.p;
     view.chunk_off = chunk_off.p;
-    view.chunks = (const float4 *)chunks.p;
+    view.chunks = (const uint4 *)chunks.p;
+    for (int d = 0; d < 3; ++d) {
+      view.qlo[d] = L.qframe_lo[d];
+      view.qstep[d] = L.qframe_step[d];
+    }
     view.seed = seed.p;
     view.grid_bits = seed.p ? grid_bits : 0;
     view.nv = L.nv;
@@ -518,14 +525,19 @@ p2m_status p2m_get_list(const p2m_handle *h, int32_t vertex, int32_t *types, int
   const int64_t b = L.row_off[row], e = L.row_off[row + 1];
   *len = e - b;
   for (int64_t j = b; j < e && j - b < cap; ++j) {
-    uint32_t tid;
-    std::memcpy(&tid, &L.entries[8 * j + 3], 4);
-    if (types) types[j - b] = (int32_t)(tid >> 30);
-    if (ids) ids[j - b] = (int32_t)(tid & 0x3fffffffu);
+    const uint32_t *w = &L.entries[4 * (size_t)j];
+    if (types) types[j - b] = (int32_t)(w[0] >> 30);
+    if (ids) ids[j - b] = (int32_t)(w[0] & 0x3fffffffu);
     if (boxes) {
+      // decode exactly as the query kernel does: chunk box, then entry box
+      const uint32_t *cw = &L.chunks[4 * (size_t)(L.chunk_off[row] + (j - b) / Layout::kChunk)];
+      float clo[3], chi[3], cstep[3], lo[3], hi[3];
+      p2m::q_unpack(cw[0], cw[1], cw[2], L.qframe_lo, L.qframe_step, clo, chi);
+      for (int d = 0; d < 3; ++d) cstep[d] = p2m::q_step(clo[d], chi[d]);
+      p2m::q_unpack(w[1], w[2], w[3], clo, cstep, lo, hi);
       for (int d = 0; d < 3; ++d) {
-        boxes[6 * (j - b) + d] = L.entries[8 * j + d];
-        boxes[6 * (j - b) + 3 + d] = L.entries[8 * j + 4 + d];
+        boxes[6 * (j - b) + d] = lo[d];
+        boxes[6 * (j - b) + 3 + d] = hi[d];
       }
     }
   }
@@ -772,7 +784,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 4;
+constexpr uint32_t kVersion = 5;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -813,12 +825,14 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
   int64_t scal[12] = {L.nv, L.nf, L.ne, L.kd_depth, L.n_entries, L.max_list,
                       L.neighbour_pairs, L.inspections, L.cert_rounds, L.cert_queries,
                       L.n_degenerate, 0};
-  float fl[13];
+  float fl[19];
   std::memcpy(fl, L.dom, 24);
   fl[6] = L.delta;
   std::memcpy(fl + 7, L.kd_root, 24);
+  std::memcpy(fl + 13, L.qframe_lo, 12);
+  std::memcpy(fl + 16, L.qframe_step, 12);
   bool ok = fwrite(&kMagic, 8, 1, f) == 1 && fwrite(&kVersion, 4, 1, f) == 1 &&
-            fwrite(scal, 8, 12, f) == 12 && fwrite(fl, 4, 13, f) == 13;
+            fwrite(scal, 8, 12, f) == 12 && fwrite(fl, 4, 19, f) == 19;
   ck = fnv1a(ck, scal, sizeof(scal));
   ck = fnv1a(ck, fl, sizeof(fl));
   ok = ok && put_vec(f, L.kd_nodes, ck) && put_vec(f, L.kd_points, ck) &&
@@ -845,9 +859,9 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
   uint64_t magic = 0, ck = 1469598103934665603ull, stored = 0;
   uint32_t ver = 0;
   int64_t scal[12];
-  float fl[13];
+  float fl[19];
   bool ok = fread(&magic, 8, 1, f) == 1 && magic == kMagic && fread(&ver, 4, 1, f) == 1 &&
-            ver == kVersion && fread(scal, 8, 12, f) == 12 && fread(fl, 4, 13, f) == 13;
+            ver == kVersion && fread(scal, 8, 12, f) == 12 && fread(fl, 4, 19, f) == 19;
   if (ok) {
     ck = fnv1a(ck, scal, sizeof(scal));
     ck = fnv1a(ck, fl, sizeof(fl));
@@ -874,11 +888,13 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
   std::memcpy(L.dom, fl, 24);
   L.delta = fl[6];
   std::memcpy(L.kd_root, fl + 7, 24);
+  std::memcpy(L.qframe_lo, fl + 13, 12);
+  std::memcpy(L.qframe_step, fl + 16, 12);
   if ((int64_t)L.row_off.size() != L.nv + 1 || (int64_t)L.kd_points.size() != 4 * L.nv ||
-      (int64_t)L.entries.size() != 8 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
+      (int64_t)L.entries.size() != 4 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
       (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back() ||
       (int64_t)L.chunk_off.size() != L.nv + 1 ||
-      (int64_t)L.chunks.size() != 8 * (int64_t)L.chunk_off.back() ||
+      (int64_t)L.chunks.size() != 4 * (int64_t)L.chunk_off.back() ||
       L.nbp.size() != 4 * L.nb.size())
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
