@@ -168,7 +168,9 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  nearest vertex of their centres (default).
  *   chunked        list scan: 0 = test the Region box of every entry; 1 =
  *                  test the box of each chunk of 8 spatially ordered
- *                  entries first (a one-level R-tree per list, Sec. 4.6). */
+ *                  entries first; 2 = test the box of each group of 8
+ *                  chunks first, then chunk boxes (a two-level R-tree per
+ *                  list, Sec. 4.6; default). */
 typedef struct {
   int sort_bits;
   int block_threads;

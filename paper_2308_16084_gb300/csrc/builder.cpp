@@ -1039,6 +1039,40 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       }
     }
   });
+  // second level: boxes of every kChunk consecutive chunks of a row
+  out.super_off.assign(nv + 1, 0);
+  for (int64_t p = 0; p < nv; ++p) {
+    uint32_t nc = out.chunk_off[p + 1] - out.chunk_off[p];
+    out.super_off[p + 1] = out.super_off[p] + (nc + Layout::kChunk - 1) / Layout::kChunk;
+  }
+  out.supers.assign(4 * (size_t)out.super_off[nv], 0u);
+  parallel_for(nv, threads, 1024, [&](int64_t p, int) {
+    uint32_t sidx = out.super_off[p];
+    for (uint32_t c = out.chunk_off[p]; c < out.chunk_off[p + 1]; c += Layout::kChunk, ++sidx) {
+      uint32_t ce = std::min<uint32_t>(c + Layout::kChunk, out.chunk_off[p + 1]);
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (uint32_t k = c; k < ce; ++k) {
+        const uint32_t *cw = &out.chunks[4 * (size_t)k];
+        float clo[3], chi[3];
+        q_unpack(cw[0], cw[1], cw[2], out.qframe_lo, out.qframe_step, clo, chi);
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::min(lo[d], clo[d]);
+          hi[d] = std::max(hi[d], chi[d]);
+        }
+      }
+      uint32_t q[6];
+      for (int d = 0; d < 3; ++d) {
+        q[d] = q_enc_lo(lo[d], out.qframe_lo[d], out.qframe_step[d]);
+        q[3 + d] = q_enc_hi(hi[d], out.qframe_lo[d], out.qframe_step[d]);
+      }
+      uint32_t *sw = &out.supers[4 * (size_t)sidx];
+      pack(q, sw);
+      float slo[3], shi[3];
+      q_unpack(sw[0], sw[1], sw[2], out.qframe_lo, out.qframe_step, slo, shi);
+      for (int d = 0; d < 3; ++d)
+        if (slo[d] > lo[d] || shi[d] < hi[d]) ++bad_boxes;
+    }
+  });
   if (bad_boxes.load()) {
     err = "internal error: a quantised Region box does not contain its box";
     return 5;

@@ -66,6 +66,11 @@ struct Layout {
   std::vector<uint32_t> entries;   // n_entries * 4
   std::vector<uint32_t> chunk_off; // nv + 1
   std::vector<uint32_t> chunks;    // n_chunks * 4
+  // second level: super-chunk s of row r covers chunks
+  // chunk_off[r] + kChunk*(s - super_off[r]) ... (up to kChunk of them); its
+  // box (same 16-bit frame as the chunks) contains their decoded boxes
+  std::vector<uint32_t> super_off; // nv + 1
+  std::vector<uint32_t> supers;    // n_supers * 4
   float qframe_lo[3] = {0, 0, 0}, qframe_step[3] = {0, 0, 0};
   // geometry records
   //   edge e: {a.x, a.y, a.z, 1/|b-a|^2}, {b.x-a.x, b.y-a.y, b.z-a.z, 0}

@@ -458,35 +458,60 @@ __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy,
   }
 }
 
-// a3..a8 for a query whose nearest vertex is row v (r already holds v).
-// chunked: test each chunk box first (one-level R-tree of the list,
-// Sec. 4.6); otherwise test the Region box of every entry.
+// entries of chunk c (entries first .. last-1) once its box admits q
+template <bool COUNT>
+__device__ __forceinline__ void scan_chunk(const DevView &m, float qx, float qy, float qz,
+                                           uint32_t c, uint32_t first, uint32_t last, bool test,
+                                           Best &r, Work *wk) {
+  const uint4 cw = __ldg(&m.chunks[c]);
+  float clo[3], chi[3];
+  q_unpack(cw.x, cw.y, cw.z, m.qlo, m.qstep, clo, chi);
+  if (test && (qx < clo[0] || qy < clo[1] || qz < clo[2] || qx > chi[0] || qy > chi[1] ||
+               qz > chi[2]))
+    return;
+  const float cstep[3] = {q_step(clo[0], chi[0]), q_step(clo[1], chi[1]), q_step(clo[2], chi[2])};
+  if (COUNT) wk->entries += (int)(last - first);
+  for (uint32_t j = first; j < last; ++j) test_entry<COUNT>(m, qx, qy, qz, j, clo, cstep, r, wk);
+}
+
+// a3..a8 for a query whose nearest vertex is row v (r already holds v): the
+// list as a two-level R-tree (Sec. 4.6).  mode 2: super-chunk boxes, then
+// chunk boxes, then entry boxes; mode 1: chunk boxes, then entry boxes;
+// mode 0: every entry box.
 template <bool COUNT>
 __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, float qz, int v,
-                                          bool chunked, Best &r, Work *wk) {
+                                          int mode, Best &r, Work *wk) {
   const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
   const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
-  if (COUNT) wk->chunks += chunked ? (int)(c1 - c0) : 0;
-  uint32_t first = j0;
-  for (uint32_t c = c0; c < c1; ++c, first += 8) {
-    const uint4 cw = __ldg(&m.chunks[c]);
-    float clo[3], chi[3];
-    q_unpack(cw.x, cw.y, cw.z, m.qlo, m.qstep, clo, chi);
-    if (chunked &&
-        (qx < clo[0] || qy < clo[1] || qz < clo[2] || qx > chi[0] || qy > chi[1] || qz > chi[2]))
-      continue;
-    const float cstep[3] = {q_step(clo[0], chi[0]), q_step(clo[1], chi[1]),
-                            q_step(clo[2], chi[2])};
-    const uint32_t last = min(first + 8u, j1);
-    if (COUNT) wk->entries += (int)(last - first);
-    for (uint32_t j = first; j < last; ++j) test_entry<COUNT>(m, qx, qy, qz, j, clo, cstep, r, wk);
+  if (mode == 2 && m.supers) {
+    const uint32_t s0 = __ldg(&m.super_off[v]), s1 = __ldg(&m.super_off[v + 1]);
+    for (uint32_t s = s0; s < s1; ++s) {
+      if (COUNT) ++wk->chunks;
+      const uint4 sw = __ldg(&m.supers[s]);
+      float slo[3], shi[3];
+      q_unpack(sw.x, sw.y, sw.z, m.qlo, m.qstep, slo, shi);
+      if (qx < slo[0] || qy < slo[1] || qz < slo[2] || qx > shi[0] || qy > shi[1] || qz > shi[2])
+        continue;
+      const uint32_t cb = c0 + 8 * (s - s0), ce = min(cb + 8u, c1);
+      if (COUNT) wk->chunks += (int)(ce - cb);
+      for (uint32_t c = cb; c < ce; ++c) {
+        const uint32_t first = j0 + 8 * (c - c0);
+        scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), true, r, wk);
+      }
+    }
+    return;
+  }
+  if (COUNT && mode == 1) wk->chunks += (int)(c1 - c0);
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t first = j0 + 8 * (c - c0);
+    scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), mode != 0, r, wk);
   }
 }
 
 template <bool COUNT = false>
 __device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
                                           Best &r, Work *wk = nullptr, int walk = 2,
-                                          bool chunked = true) {
+                                          int chunked = 2) {
   const int v = find_nearest<COUNT>(m, walk, qx, qy, qz, wk);
   const float4 pv = __ldg(&m.kd_points[v]);
   {
@@ -546,7 +571,7 @@ k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
     if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
         s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
       st |= 1;
-    query_one(m, s.x, s.y, s.z, r, nullptr, walk, chunked != 0);
+    query_one(m, s.x, s.y, s.z, r, nullptr, walk, chunked);
   }
   store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
 }
@@ -672,7 +697,7 @@ __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy,
     r.w1 = 0.f;
     r.w2 = 0.f;
   }
-  if (active) scan_list<COUNT>(m, qx, qy, qz, v, true, r, wk);
+  if (active) scan_list<COUNT>(m, qx, qy, qz, v, 2, r, wk);
 }
 
 template <bool COUNT>
@@ -717,7 +742,7 @@ __global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t 
   if (i < n) {
     const float4 s = sq[i];
     Best r;
-    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w, walk, chunked != 0);
+    if (finite3(s.x, s.y, s.z)) query_one<true>(m, s.x, s.y, s.z, r, &w, walk, chunked);
   }
   int v[6] = {w.nodes, w.points, w.entries, w.edges, w.faces, w.chunks};
 #pragma unroll
@@ -946,7 +971,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   if (ev) cudaEventRecord(ev[1], stream);
   const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
   const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
-  const int chunked = (tune.chunked && m.chunks) ? 1 : 0;
+  const int chunked = tune.chunked;
   if (counters) {
     cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), stream);
     if (tune.warp_mode)

@@ -22,6 +22,8 @@ struct DevView {
   const float4 *nbp;        // neighbour positions, parallel to nb: x, y, z, row bits
   const uint32_t *chunk_off;  // nv + 1: chunks of each row (CSR)
   const uint4 *chunks;        // per chunk: 16-bit box in the frame below
+  const uint32_t *super_off;  // nv + 1: super-chunks (8 chunks each) of each row
+  const uint4 *supers;        // per super-chunk: 16-bit box in the same frame
   float qlo[3], qstep[3];     // frame of the chunk boxes (quant.h)
   const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre
   int grid_bits;              // G = 2^grid_bits cells per axis over D (0 = no grid)
@@ -38,7 +40,8 @@ struct QueryTuning {
   int warp_mode = 0;  // 0: one thread per query, 1: warp-cooperative KD walk
   int nn_walk = 2;    // 0: KD-tree backtracking, 1: KD descent + Voronoi walk,
                       // 2: seed-grid lookup + Voronoi walk
-  int chunked = 1;    // 0: scan every list entry, 1: test chunk boxes first
+  int chunked = 2;    // 0: scan every list entry, 1: chunk boxes first,
+                      // 2: super-chunk boxes, then chunk boxes
 };
 
 // Scratch needed by launch_query for n points, in bytes.

@@ -75,7 +75,7 @@ struct p2m_handle {
   DevBuf<uint32_t> entries;
   DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed;
   int grid_bits = 0;
-  DevBuf<uint32_t> chunks;
+  DevBuf<uint32_t> chunks, super_off, supers;
   DevBuf<float> nbp;
   DevBuf<int32_t> edges, tris;
   DevView view{};
@@ -123,6 +123,8 @@ struct p2m_handle {
     view.nbp = (const float4 *)nbp.p;
     view.chunk_off = chunk_off.p;
     view.chunks = (const uint4 *)chunks.p;
+    view.super_off = super_off.p;
+    view.supers = (const uint4 *)supers.p;
     for (int d = 0; d < 3; ++d) {
       view.qlo[d] = L.qframe_lo[d];
       view.qstep[d] = L.qframe_step[d];
@@ -158,11 +160,14 @@ struct p2m_handle {
     if (e == cudaSuccess && !L.chunk_off.empty())
       e = chunk_off.upload(L.chunk_off.data(), L.chunk_off.size());
     if (e == cudaSuccess && !L.chunks.empty()) e = chunks.upload(L.chunks.data(), L.chunks.size());
+    if (e == cudaSuccess && !L.super_off.empty())
+      e = super_off.upload(L.super_off.data(), L.super_off.size());
+    if (e == cudaSuccess && !L.supers.empty()) e = supers.upload(L.supers.data(), L.supers.size());
     make_view();
     if (e == cudaSuccess) e = make_seed_grid();
     device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
                         row_off.n + edges.n + tris.n + nb_off.n + nb.n + chunk_off.n + chunks.n +
-                        seed.n + nbp.n);
+                        seed.n + nbp.n + super_off.n + supers.n);
     return e;
   }
 
@@ -325,7 +330,7 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
     return P2M_ERR_INVALID_ARG;
   if (t->warp_cooperative != 0 && t->warp_cooperative != 1) return P2M_ERR_INVALID_ARG;
   if (t->nn_walk < 0 || t->nn_walk > 2) return P2M_ERR_INVALID_ARG;
-  if (t->chunked != 0 && t->chunked != 1) return P2M_ERR_INVALID_ARG;
+  if (t->chunked < 0 || t->chunked > 2) return P2M_ERR_INVALID_ARG;
   h->tune.nn_walk = t->nn_walk;
   h->tune.chunked = t->chunked;
   h->tune.sort_bits = t->sort_bits;
@@ -748,7 +753,7 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   float bms = 1e30f;
   const int bits_c[] = {12, 15, 18, 21, 24};
   const int block_c[] = {128, 256};
-  for (int ch = 1; ch < 2; ++ch)
+  for (int ch = 1; ch < 3; ++ch)
   for (int wm = 0; wm < 2; ++wm)
   for (int bits : bits_c)
     for (int bt : block_c) {
@@ -784,7 +789,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 5;
+constexpr uint32_t kVersion = 6;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -839,7 +844,8 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
        put_vec(f, L.pos_of_vertex, ck) && put_vec(f, L.row_off, ck) && put_vec(f, L.entries, ck) &&
        put_vec(f, L.edge_rec, ck) && put_vec(f, L.face_rec, ck) && put_vec(f, L.edges, ck) &&
        put_vec(f, L.tris, ck) && put_vec(f, L.nb_off, ck) && put_vec(f, L.nb, ck) &&
-       put_vec(f, L.chunk_off, ck) && put_vec(f, L.chunks, ck) && put_vec(f, L.nbp, ck);
+       put_vec(f, L.chunk_off, ck) && put_vec(f, L.chunks, ck) && put_vec(f, L.nbp, ck) &&
+       put_vec(f, L.super_off, ck) && put_vec(f, L.supers, ck);
   ok = ok && fwrite(&ck, 8, 1, f) == 1;
   ok = (fclose(f) == 0) && ok;
   return ok ? P2M_OK : P2M_ERR_IO;
@@ -870,7 +876,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
          get_vec(f, L.entries, ck) && get_vec(f, L.edge_rec, ck) && get_vec(f, L.face_rec, ck) &&
          get_vec(f, L.edges, ck) && get_vec(f, L.tris, ck) && get_vec(f, L.nb_off, ck) &&
          get_vec(f, L.nb, ck) && get_vec(f, L.chunk_off, ck) && get_vec(f, L.chunks, ck) &&
-         get_vec(f, L.nbp, ck) && fread(&stored, 8, 1, f) == 1 && stored == ck;
+         get_vec(f, L.nbp, ck) && get_vec(f, L.super_off, ck) && get_vec(f, L.supers, ck) &&
+         fread(&stored, 8, 1, f) == 1 && stored == ck;
   }
   fclose(f);
   if (!ok) return P2M_ERR_IO;
@@ -895,7 +902,8 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
       (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back() ||
       (int64_t)L.chunk_off.size() != L.nv + 1 ||
       (int64_t)L.chunks.size() != 4 * (int64_t)L.chunk_off.back() ||
-      L.nbp.size() != 4 * L.nb.size())
+      L.nbp.size() != 4 * L.nb.size() || (int64_t)L.super_off.size() != L.nv + 1 ||
+      L.supers.size() != 4 * (size_t)L.super_off.back())
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
     cudaError_t e = h->upload_tree();

@@ -42,7 +42,7 @@ CASES = [(0, {}, None), (1, {"level": 5}, 60000), (2, {"grid": 128}, 60000),
 
 
 @pytest.mark.parametrize("idx,kw,n", CASES)
-@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 1, 1), (0, 1, 0), (1, 0, 1), (2, 0, 1),
+@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 1, 1), (0, 1, 0), (1, 0, 1), (2, 0, 2),
                                   (2, 1, 0)])
 def test_parity_workloads(pg, idx, kw, n, mode):
     m = dg.workload(idx, n_queries=n, **kw)
@@ -83,7 +83,7 @@ def test_parity_against_paper_method(pg):
 @pytest.mark.parametrize("threads", [64, 256, 512])
 @pytest.mark.parametrize("warp", [0, 1])
 @pytest.mark.parametrize("walk", [0, 1, 2])
-@pytest.mark.parametrize("chunked", [0, 1])
+@pytest.mark.parametrize("chunked", [0, 1, 2])
 def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked):
     m = dg.workload(0, n_queries=50001)
     mesh = build(pg, m)
