@@ -170,13 +170,18 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  test the box of each chunk of 8 spatially ordered
  *                  entries first; 2 = test the box of each group of 8
  *                  chunks first, then chunk boxes (a two-level R-tree per
- *                  list, Sec. 4.6; default). */
+ *                  list, Sec. 4.6; default).
+ *   group_by_vertex  1 = two passes: nearest vertex of every query, a
+ *                  counting sort of the queries by that vertex, then the
+ *                  list scans, so the lanes of a warp share interception
+ *                  lists (default); 0 = one fused kernel. */
 typedef struct {
   int sort_bits;
   int block_threads;
   int warp_cooperative;
   int nn_walk;
   int chunked;
+  int group_by_vertex;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);

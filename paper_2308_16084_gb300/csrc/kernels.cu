@@ -734,6 +734,80 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
   store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
 }
 
+
+// ------------------------------------------- two-pass query, grouped lists
+// Pass 1: nearest vertex of every Morton-sorted query (nv marks a
+// non-finite query).  The queries are then regrouped by that vertex with a
+// counting sort, so that the lanes of a warp mostly share one interception
+// list in pass 2 (uniform loops, broadcast loads).
+__global__ void k_nn_pass(DevView m, const float4 *__restrict__ sq, int64_t n, int walk,
+                          uint32_t *__restrict__ vout) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 s = sq[i];
+  vout[i] = finite3(s.x, s.y, s.z) ? (uint32_t)find_nearest(m, walk, s.x, s.y, s.z)
+                                   : (uint32_t)m.nv;
+}
+
+__global__ void k_vertex_count(const uint32_t *__restrict__ vin, int64_t n,
+                               uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t b = vin[i];
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, b);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&hist[b], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+}
+
+__global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
+                                 const uint2 *__restrict__ key_rank,
+                                 const uint32_t *__restrict__ off, float4 *__restrict__ out,
+                                 uint32_t *__restrict__ vout) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 kr = key_rank[i];
+  const uint32_t pos = off[kr.x] + kr.y;
+  out[pos] = sq[i];
+  vout[pos] = kr.x;
+}
+
+// Pass 2: the list of each query's nearest vertex (regrouped stream).
+__global__ void k_list_pass(DevView m, const float4 *__restrict__ gq,
+                            const uint32_t *__restrict__ gv, int64_t n, int chunked,
+                            float *dist, float *closest, int32_t *prim_id, uint8_t *prim_type,
+                            float4 *save, uint8_t *status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 s = gq[i];
+  const int64_t o = __float_as_int(s.w);
+  const bool ok = finite3(s.x, s.y, s.z);
+  uint8_t st = ok ? 0 : 2;
+  Best r;
+  if (ok) {
+    const int v = (int)gv[i];
+    if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
+        s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
+      st |= 1;
+    const float4 pv = __ldg(&m.kd_points[v]);
+    const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
+    r.d2 = dx * dx + dy * dy + dz * dz;
+    r.cx = pv.x;
+    r.cy = pv.y;
+    r.cz = pv.z;
+    r.tid = (uint32_t)__float_as_int(pv.w);
+    r.w0 = 1.f;
+    r.w1 = 0.f;
+    r.w2 = 0.f;
+    scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr);
+  }
+  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+}
+
 // Counting variant of the query (not timed): sums the per-query work.
 __global__ void k_query_count(DevView m, const float4 *__restrict__ sq, int64_t n,
                               unsigned long long *__restrict__ acc, int walk, int chunked) {
@@ -925,10 +999,14 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-size_t query_scratch_bytes(int64_t n, int sort_bits) {
+size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv) {
   size_t nb = sort_bits > 0 ? ((size_t)1 << sort_bits) : 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + al(4 * kMaxScanTiles) + 256;
+  size_t base = al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + al(4 * kMaxScanTiles);
+  if (nv > 0)  // regrouping: vertex per query (twice), second float4 stream, vertex
+               // histogram and offsets
+    base += 2 * al(4 * (size_t)n) + al(16 * (size_t)n) + 2 * al(4 * (size_t)(nv + 1));
+  return base + 256;
 }
 
 cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
@@ -969,6 +1047,34 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   }
   const int bt = tune.block_threads;
   if (ev) cudaEventRecord(ev[1], stream);
+  if (tune.group_by_vertex && !counters && !tune.warp_mode && m.nv + 1 <= (int64_t)kScanTile * kMaxScanTiles) {
+    // regroup by nearest vertex: buffers after the sort's own scratch
+    if (scratch_bytes < query_scratch_bytes(n, tune.sort_bits, m.nv)) return cudaErrorInvalidValue;
+    const size_t nbm = tune.sort_bits > 0 ? ((size_t)1 << tune.sort_bits) : 0;
+    char *b2 = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) + al(16 * (size_t)n) +
+               al(8 * (size_t)n) + 2 * al(4 * nbm) + al(4 * kMaxScanTiles);
+    uint32_t *vbuf = (uint32_t *)b2;
+    b2 += al(4 * (size_t)n);
+    uint32_t *gv = (uint32_t *)b2;
+    b2 += al(4 * (size_t)n);
+    float4 *grouped = (float4 *)b2;
+    b2 += al(16 * (size_t)n);
+    uint32_t *vhist = (uint32_t *)b2;
+    b2 += al(4 * (size_t)(m.nv + 1));
+    uint32_t *voff = (uint32_t *)b2;
+    uint32_t *tiles2 = (uint32_t *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) +
+                       (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
+    const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
+    k_nn_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, walk, vbuf);
+    cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
+    k_vertex_count<<<blocks_for(n, T), T, 0, stream>>>(vbuf, n, vhist, key_rank);
+    bucket_scan(vhist, voff, tiles2, (int)(m.nv + 1), stream);
+    k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped, gv);
+    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped, gv, n, tune.chunked, dist,
+                                                      closest, prim_id, prim_type, save, status);
+    if (ev) cudaEventRecord(ev[2], stream);
+    return cudaGetLastError();
+  }
   const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
   const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
   const int chunked = tune.chunked;

@@ -42,10 +42,13 @@ struct QueryTuning {
                       // 2: seed-grid lookup + Voronoi walk
   int chunked = 2;    // 0: scan every list entry, 1: chunk boxes first,
                       // 2: super-chunk boxes, then chunk boxes
+  int group_by_vertex = 1;  // 1: nearest-vertex pass, regroup queries by
+                            // vertex, then the list pass (two kernels)
 };
 
-// Scratch needed by launch_query for n points, in bytes.
-size_t query_scratch_bytes(int64_t n, int sort_bits);
+// Scratch needed by launch_query for n points, in bytes (nv: vertices of
+// the mesh, for the regrouping by nearest vertex; 0 = no regrouping).
+size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv = 0);
 
 // Morton bucket sort (a1) + fused query (a2..a8).  All pointers device.
 // ev (3 events or NULL) brackets the sort and the query kernel; with

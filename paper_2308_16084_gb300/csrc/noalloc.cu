@@ -73,6 +73,7 @@ extern "C" p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n
   if (n == 0) return P2M_OK;
   if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
   if (tune.sort_bits > kNoallocSortBits) tune.sort_bits = kNoallocSortBits;
+  tune.group_by_vertex = 0;  // the static array holds the one-pass scratch only
   if (p2m::query_scratch_bytes(n, tune.sort_bits) > kNoallocBytes) return P2M_ERR_TOO_LARGE;
   void *scratch = nullptr;
   p2m_status s = scratch_address(&scratch);

@@ -320,6 +320,7 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   t->warp_cooperative = h->tune.warp_mode;
   t->nn_walk = h->tune.nn_walk;
   t->chunked = h->tune.chunked;
+  t->group_by_vertex = h->tune.group_by_vertex;
   return P2M_OK;
 }
 
@@ -331,6 +332,8 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
   if (t->warp_cooperative != 0 && t->warp_cooperative != 1) return P2M_ERR_INVALID_ARG;
   if (t->nn_walk < 0 || t->nn_walk > 2) return P2M_ERR_INVALID_ARG;
   if (t->chunked < 0 || t->chunked > 2) return P2M_ERR_INVALID_ARG;
+  if (t->group_by_vertex != 0 && t->group_by_vertex != 1) return P2M_ERR_INVALID_ARG;
+  h->tune.group_by_vertex = t->group_by_vertex;
   h->tune.nn_walk = t->nn_walk;
   h->tune.chunked = t->chunked;
   h->tune.sort_bits = t->sort_bits;
@@ -344,7 +347,7 @@ p2m_status p2m_reserve(p2m_handle *h, int64_t n) {
   if (s) return s;
   if (n < 0) return P2M_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
-  return h->ensure_scratch(p2m::query_scratch_bytes(n, 24) + 24 * (size_t)n + 4096);
+  return h->ensure_scratch(p2m::query_scratch_bytes(n, 24, h->L.nv) + 24 * (size_t)n + 4096);
 }
 
 p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
@@ -356,7 +359,8 @@ p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, floa
   if (n == 0) return P2M_OK;
   if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
-  size_t need = p2m::query_scratch_bytes(n, h->tune.sort_bits);
+  size_t need = p2m::query_scratch_bytes(n, h->tune.sort_bits,
+                                         h->tune.group_by_vertex ? h->L.nv : 0);
   if ((s = h->ensure_scratch(need))) return s;
   cudaEvent_t *ev = nullptr;
   if (!h->ring.empty()) {
@@ -445,7 +449,8 @@ p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist,
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
   // device staging lives in the scratch arena after the query's own part
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  size_t need_q = p2m::query_scratch_bytes(n, h->tune.sort_bits);
+  size_t need_q = p2m::query_scratch_bytes(n, h->tune.sort_bits,
+                                           h->tune.group_by_vertex ? h->L.nv : 0);
   size_t io = al(12 * (size_t)n) + al(4 * (size_t)n) + al(12 * (size_t)n) + al(4 * (size_t)n) +
               al((size_t)n);
   if ((s = h->ensure_scratch(al(need_q) + io + 256))) return s;
@@ -753,11 +758,12 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   float bms = 1e30f;
   const int bits_c[] = {12, 15, 18, 21, 24};
   const int block_c[] = {128, 256};
-  for (int ch = 1; ch < 3; ++ch)
-  for (int wm = 0; wm < 2; ++wm)
+  for (int gv = 0; gv < 2; ++gv)
+  for (int ch = 2; ch < 3; ++ch)
+  for (int wm = 0; wm < 1; ++wm)
   for (int bits : bits_c)
     for (int bt : block_c) {
-      p2m_tuning t{bits, bt, wm, 2, ch};
+      p2m_tuning t{bits, bt, wm, 2, ch, gv};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);

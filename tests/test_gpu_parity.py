@@ -42,12 +42,13 @@ CASES = [(0, {}, None), (1, {"level": 5}, 60000), (2, {"grid": 128}, 60000),
 
 
 @pytest.mark.parametrize("idx,kw,n", CASES)
-@pytest.mark.parametrize("mode", [(0, 0, 0), (1, 1, 1), (0, 1, 0), (1, 0, 1), (2, 0, 2),
-                                  (2, 1, 0)])
+@pytest.mark.parametrize("mode", [(0, 0, 0, 0), (1, 1, 1, 0), (0, 1, 0, 0), (1, 0, 1, 1),
+                                  (2, 0, 2, 1), (2, 0, 2, 0), (2, 1, 0, 0)])
 def test_parity_workloads(pg, idx, kw, n, mode):
     m = dg.workload(idx, n_queries=n, **kw)
     mesh = build(pg, m)
-    mesh.tuning = {"nn_walk": mode[0], "warp_cooperative": mode[1], "chunked": mode[2]}
+    mesh.tuning = {"nn_walk": mode[0], "warp_cooperative": mode[1], "chunked": mode[2],
+                   "group_by_vertex": mode[3]}
     o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
     np.testing.assert_array_equal(mesh.edges(), o.edges())
     ref = o.bruteforce(m.queries)
@@ -80,16 +81,17 @@ def test_parity_against_paper_method(pg):
 
 
 @pytest.mark.parametrize("bits", [0, 12, 24])
-@pytest.mark.parametrize("threads", [64, 256, 512])
+@pytest.mark.parametrize("threads", [64, 512])
 @pytest.mark.parametrize("warp", [0, 1])
 @pytest.mark.parametrize("walk", [0, 1, 2])
 @pytest.mark.parametrize("chunked", [0, 1, 2])
-def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked):
+@pytest.mark.parametrize("group", [0, 1])
+def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked, group):
     m = dg.workload(0, n_queries=50001)
     mesh = build(pg, m)
     base = run(mesh, m.queries)
     mesh.tuning = {"sort_bits": bits, "block_threads": threads, "warp_cooperative": warp,
-                   "nn_walk": walk, "chunked": chunked}
+                   "nn_walk": walk, "chunked": chunked, "group_by_vertex": group}
     got = run(mesh, m.queries)
     for k in ("dist", "closest", "prim_id", "prim_type", "status"):
         np.testing.assert_array_equal(got[k], base[k])
