@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--level", type=int, default=None, help="smaller mesh (profiling only)")
     ap.add_argument("--queries", type=int, default=None, help="fewer queries (profiling only)")
+    ap.add_argument("--workload", type=int, default=1, choices=[1, 3, 4],
+                    help="1: forward queries (default); 3: forward+backward; 4: 64-mesh batch")
     ap.add_argument("--layout", default=None,
                     help="load the built layout from this file if it exists, else build and "
                          "save it there")
@@ -64,6 +66,157 @@ def dist_env():
 
 def workload(args):
     return dg.workload(WORKLOAD, n_queries=args.queries, level=args.level)
+
+
+def timed(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_fwd_bwd(args):
+    """Workload 3: loss = sum w_i d_i on the noisy 7x-subdivided icosphere,
+    4M near-surface queries; forward+backward (grad to the queries and to the
+    vertex positions) against the forward alone, same GPU, same queries."""
+    import torch
+    import paper_2308_16084_gb300 as pg
+    m = dg.workload(3, n_queries=args.queries, level=args.level)
+    n = m.queries.shape[0]
+    t0 = time.perf_counter()
+    mesh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
+    build_s = time.perf_counter() - t0
+    q = torch.from_numpy(m.queries).cuda()
+    w = torch.from_numpy(m.weights).cuda()
+    mesh.reserve(n)
+    mesh.autotune(q, reps=2)
+    res = mesh.query(q, closest=True, prim_type=False, save=True)
+    gv = torch.zeros(m.verts.shape[0], 3, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        mesh.query(q, out=res)
+
+    def fwd_bwd():
+        mesh.query(q, out=res)
+        gv.zero_()
+        mesh.backward(q, res, w, grad_q=True, grad_verts=gv)
+
+    for _ in range(max(3, args.warmup)):
+        fwd_bwd()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    ms_f = timed(fwd, args.steps, stream)
+    ms_fb = timed(fwd_bwd, args.steps, stream)
+    clk = clocks.stop()
+    # end to end through the autograd API from pinned host memory
+    qh = torch.from_numpy(m.queries).pin_memory()
+    vh = torch.from_numpy(m.verts).pin_memory()
+    gh = torch.empty(n, 3).pin_memory()
+    verts_d = vh.cuda().requires_grad_(True)
+
+    def e2e_step():
+        qd = qh.cuda(non_blocking=True).requires_grad_(True)
+        d, _ = pg.distance(qd, verts_d, mesh)
+        (w * d).sum().backward()
+        gh.copy_(qd.grad, non_blocking=True)
+        verts_d.grad = None
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    v_fb = n * args.steps / (ms_fb / 1e3)
+    v_f = n * args.steps / (ms_f / 1e3)
+    line = {"metric": "point-to-mesh fwd+bwd queries/sec (327,680 tris)", "value": v_fb,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_fb / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": m.name, "n_tris": int(m.tris.shape[0]),
+                       "n_queries_per_gpu": n, "loss": "sum w_i d_i, w ~ U(0,1)",
+                       "grads": "queries and vertex positions", "tuning": mesh.tuning,
+                       "build_s": round(build_s, 1),
+                       "l2": "inputs larger than L2 (layout + 4M queries)"},
+            "forward_only": {"value": v_f, "ms_per_step": ms_f / args.steps},
+            "fwd_bwd_over_fwd_time": ms_fb / ms_f, "clocks": clk,
+            "e2e": {"value": n * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * n},
+            "gpu_launches": (kernels_per_step(mesh.tuning) + 1) * args.steps,
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """Workload 4: 64 meshes of uneven size in one persistent launch captured
+    in a CUDA graph, against the same queries as 64 plain per-mesh launches."""
+    import torch
+    import paper_2308_16084_gb300 as pg
+    scale = 1.0 if args.queries is None else args.queries / 24e6
+    ms = dg.batch_workload(64, query_scale=scale)
+    t0 = time.perf_counter()
+    meshes = [pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale,
+                     domain_margin=m.domain_margin) for m in ms]
+    build_s = time.perf_counter() - t0
+    qs = [torch.from_numpy(m.queries).cuda() for m in ms]
+    total = sum(q.shape[0] for q in qs)
+    b = pg.P2MBatch(meshes, qs)
+    tuned = b.autotune(reps=2)
+    stream = torch.cuda.Stream()
+    b.run(stream=stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.run(stream=stream)
+    outs = []
+    for mesh, q in zip(meshes, qs):
+        mesh.reserve(q.shape[0])
+        mesh.autotune(q, reps=1)
+        outs.append(mesh.query(q, closest=False, prim_type=False))
+
+    def plain():
+        for mesh, q, o in zip(meshes, qs, outs):
+            mesh.query(q, out=o)
+
+    cur = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+        plain()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    ms_b = timed(g.replay, args.steps, cur)
+    ms_p = timed(plain, args.steps, cur)
+    clk = clocks.stop()
+    b.check()
+    same = all(torch.equal(o["dist"], r["dist"]) for o, r in zip(outs, b.out))
+    line = {"metric": "batched point-to-mesh queries/sec (64 meshes)",
+            "value": total * args.steps / (ms_b / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch64-icosphere-heightfield-1k..500k", "meshes": len(ms),
+                       "total_tris": int(sum(m.tris.shape[0] for m in ms)),
+                       "total_queries": int(total), "tuning": b.tuning,
+                       "autotune_ms": tuned, "build_s": round(build_s, 1),
+                       "launch": "one CUDA graph: sort + persistent query kernel"},
+            "per_mesh_launches": {"value": total * args.steps / (ms_p / 1e3),
+                                  "ms_per_step": ms_p / args.steps},
+            "batched_over_plain_speedup": ms_p / ms_b, "identical_to_plain": same,
+            "clocks": clk, "gpu_launches": 6 * args.steps, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def config_of(m, args, extra=None):
@@ -192,10 +345,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(n_queries):
-    """DRAM bytes per query-kernel launch from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "k_query_dram.json")
+def measured_traffic(kernel, n_queries):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    profiles/<kernel>_dram.json, if it was taken on the current kernel
+    source; else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_dram.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
@@ -213,16 +367,27 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def bytes_per_query(c, n):
-    """Algorithmic bytes one query touches (record sizes of the layout):
-    query 12 B, outputs 21 B (dist, closest, id, type), 48 B per internal
-    KD node (two child boxes), 16 B per vertex examined (leaf points and
-    Voronoi neighbours, + 4 B neighbour id), 8 B CSR range, 28 B per list
-    entry scanned (Region box + typed id), 28 B per chunk box tested, 32 B
-    per edge and 48 B per face tested."""
-    per = (12 + 21 + 8) * n + 48 * c["nodes"] + 20 * c["points"] + 28 * c["entries"] + \
-        28 * c.get("chunks", 0) + 32 * c["edges"] + 48 * c["faces"]
-    return per / n
+def phase_bytes(c, n):
+    """Algorithmic bytes one query touches in each kernel, from the record
+    sizes of the layout and the work counters.
+      nearest-vertex pass: sorted query 16 B, vertex out 4 B, seed-grid cell
+        4 B, 48 B per KD internal node (backtracking only), 16 B per vertex
+        record examined (seed, Voronoi neighbours);
+      list pass: regrouped query 16 B + vertex 4 B, nearest-vertex record
+        16 B, three CSR ranges 24 B, 16 B per super/chunk box tested, 16 B
+        per list entry scanned, 32 B per edge and 48 B per face tested,
+        outputs 21 B (dist, closest, id, type)."""
+    nn = (16 + 4 + 4) * n + 48 * c["nodes"] + 16 * c["points"]
+    lst = (16 + 4 + 16 + 24 + 21) * n + 16 * c.get("chunks", 0) + 16 * c["entries"] + \
+        32 * c["edges"] + 48 * c["faces"]
+    return nn / n, lst / n
+
+
+def kernels_per_step(tuning):
+    sort = 5 if tuning["sort_bits"] > 0 else 1  # count, 3 scan kernels, scatter
+    if tuning.get("group_by_vertex") and not tuning.get("warp_cooperative"):
+        return sort + 7  # nn pass, vertex count, 3 scan kernels, vertex scatter, list pass
+    return sort + 1
 
 
 def run_ours(args):
@@ -291,7 +456,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    calls, sort_ms, kern_ms = mesh.timing_summary()
+    tsum = mesh.timing_summary()
     mesh.set_timing(False)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -318,19 +483,26 @@ def run_ours(args):
     e2e = {"value": n * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 8 * n}
 
-    # roofline of the dominant kernel (the fused query kernel)
+    # roofline of the dominant kernel, timed live over the timed region
     cnt = mesh.counters(q)
-    bpq = bytes_per_query(cnt, n)
-    kern_avg_s = kern_ms / max(1, calls) / 1e3
+    nn_b, list_b = phase_bytes(cnt, n)
+    calls = max(1, tsum["calls"])
+    grouped = tsum["nn_ms"] > 0
+    phases = {"sort_ms": tsum["sort_ms"] / calls, "nn_pass_ms": tsum["nn_ms"] / calls,
+              "regroup_ms": tsum["regroup_ms"] / calls, "list_pass_ms": tsum["list_ms"] / calls}
+    if grouped:
+        cand = [("k_nn_pass", phases["nn_pass_ms"], nn_b), ("k_list_pass", phases["list_pass_ms"], list_b)]
+    else:
+        cand = [("k_query", phases["list_pass_ms"], nn_b + list_b)]
+    kname, kms, kbytes = max(cand, key=lambda c: c[1])
     peak, src = peaks()
-    achieved = bpq * n / kern_avg_s / 1e9
-    traffic = measured_traffic(n)
+    achieved = kbytes * n / (kms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": measured_traffic(kname, n),
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
             else "fallback 6.8 TB/s",
-            "kernel": "k_query", "kernel_ms": kern_avg_s * 1e3,
-            "sort_ms": sort_ms / max(1, calls), "bytes_per_query": bpq,
+            "kernel": kname, "kernel_ms": kms, "bytes_per_query": kbytes,
+            "phases": phases, "bytes_per_query_by_kernel": {"k_nn_pass": nn_b, "k_list_pass": list_b},
             "work_per_query": {k: v / n for k, v in cnt.items()}}
 
     cpu = None
@@ -351,7 +523,7 @@ def run_ours(args):
                       f"queries {12 * n / 1e6:.0f} MB per step",
                 "tuning": mesh.tuning, "autotune_ms": tuned_ms, "build_s": round(build_s, 1),
                 "table_entries": st["n_entries"], "max_list": st["max_list"]}),
-            "clocks": clk, "e2e": e2e, "gpu_launches": 4 * args.steps,
+            "clocks": clk, "e2e": e2e, "gpu_launches": kernels_per_step(mesh.tuning) * args.steps,
             "roofline": roof, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -370,6 +542,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == 3:
+        return run_fwd_bwd(args)
+    if args.workload == 4:
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -186,14 +186,15 @@ typedef struct {
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
 
-/* Instrumentation.  While timing is enabled, every p2m_query brackets its
- * sort and its query kernel with CUDA events on the caller's stream (a ring
- * of the last 1024 calls; no host synchronisation).  p2m_timing_summary
- * waits for the calls recorded since its previous call and returns
- * {calls, total sort ms, total query-kernel ms}.  Enabling (or disabling)
- * clears the ring. */
+/* Instrumentation.  While timing is enabled, every p2m_query records CUDA
+ * events on the caller's stream between its phases (a ring of the last 1024
+ * calls; no host synchronisation).  p2m_timing_summary waits for the calls
+ * recorded since its previous call and returns {calls, total ms of the
+ * Morton sort, of the nearest-vertex pass, of the regrouping by vertex, of
+ * the list pass} (the one-pass kernel counts entirely as list pass).
+ * Enabling (or disabling) clears the ring. */
 p2m_status p2m_set_timing(p2m_handle *h, int enable);
-p2m_status p2m_timing_summary(p2m_handle *h, double out[3]);
+p2m_status p2m_timing_summary(p2m_handle *h, double out[5]);
 
 /* Work counters of a query batch (device q, n points): runs a counting
  * variant of the query kernel (outputs are not written) and returns the

@@ -170,11 +170,13 @@ class P2M:
         check(lib.p2m_set_timing(self._h, int(bool(enable))), "p2m_set_timing")
 
     def timing_summary(self):
-        """(calls, total sort ms, total query-kernel ms) of the queries made
-        since the previous summary (timing enabled)."""
-        out = (ctypes.c_double * 3)()
+        """Per-phase totals of the queries made since the previous summary
+        (timing enabled): dict with calls, sort_ms, nn_ms, regroup_ms,
+        list_ms (the one-pass kernel counts as list_ms)."""
+        out = (ctypes.c_double * 5)()
         check(lib.p2m_timing_summary(self._h, out), "p2m_timing_summary")
-        return int(out[0]), float(out[1]), float(out[2])
+        return {"calls": int(out[0]), "sort_ms": float(out[1]), "nn_ms": float(out[2]),
+                "regroup_ms": float(out[3]), "list_ms": float(out[4])}
 
     def counters(self, q, stream=None):
         """Work totals of a query batch: internal KD nodes visited, vertices

@@ -1066,18 +1066,24 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
                        (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
     const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
     k_nn_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, walk, vbuf);
+    if (ev) cudaEventRecord(ev[2], stream);
     cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
     k_vertex_count<<<blocks_for(n, T), T, 0, stream>>>(vbuf, n, vhist, key_rank);
     bucket_scan(vhist, voff, tiles2, (int)(m.nv + 1), stream);
     k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped, gv);
+    if (ev) cudaEventRecord(ev[3], stream);
     k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped, gv, n, tune.chunked, dist,
                                                       closest, prim_id, prim_type, save, status);
-    if (ev) cudaEventRecord(ev[2], stream);
+    if (ev) cudaEventRecord(ev[4], stream);
     return cudaGetLastError();
   }
   const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
   const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
   const int chunked = tune.chunked;
+  if (ev) {
+    cudaEventRecord(ev[2], stream);
+    cudaEventRecord(ev[3], stream);
+  }
   if (counters) {
     cudaMemsetAsync(counters, 0, 6 * sizeof(unsigned long long), stream);
     if (tune.warp_mode)
@@ -1094,7 +1100,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     k_query<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, dist, closest, prim_id,
                                                   prim_type, save, status, walk, chunked);
   }
-  if (ev) cudaEventRecord(ev[2], stream);
+  if (ev) cudaEventRecord(ev[4], stream);
   return cudaGetLastError();
 }
 

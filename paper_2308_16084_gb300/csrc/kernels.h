@@ -50,8 +50,10 @@ struct QueryTuning {
 // the mesh, for the regrouping by nearest vertex; 0 = no regrouping).
 size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv = 0);
 
-// Morton bucket sort (a1) + fused query (a2..a8).  All pointers device.
-// ev (3 events or NULL) brackets the sort and the query kernel; with
+// Morton bucket sort (a1) + query (a2..a8).  All pointers device.
+// ev (5 events or NULL) marks: start, sorted, nearest vertices found,
+// regrouped by vertex, done (the one-pass kernel records the middle three
+// at the same point as its start); with
 // `counters` (5 device u64) the counting variant runs instead of the query
 // and sums internal nodes, points, entries, edges and faces visited.
 cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
