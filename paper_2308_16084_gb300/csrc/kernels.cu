@@ -776,8 +776,15 @@ __global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
   vout[pos] = kr.x;
 }
 
+// three resident 512-thread CTAs per SM: caps k_list_pass at 40 registers
+// (75 % occupancy instead of 50 %), measured 3 % faster on the 1.3M-triangle
+// workload than the uncapped 56 registers
+#ifndef P2M_LIST_MIN_BLOCKS
+#define P2M_LIST_MIN_BLOCKS 3
+#endif
+
 // Pass 2: the list of each query's nearest vertex (regrouped stream).
-__global__ void k_list_pass(DevView m, const float4 *__restrict__ gq,
+__global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS) k_list_pass(DevView m, const float4 *__restrict__ gq,
                             const uint32_t *__restrict__ gv, int64_t n, int chunked,
                             float *dist, float *closest, int32_t *prim_id, uint8_t *prim_type,
                             float4 *save, uint8_t *status) {

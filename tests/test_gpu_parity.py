@@ -312,3 +312,78 @@ def test_full_size_displaced_sphere_sampled(pg, full1):
     nn, _ = o.kdt_nn(m.queries[sel])
     dv = np.linalg.norm(m.queries[sel].astype(np.float64) - m.verts[nn].astype(np.float64), axis=1)
     assert (got["dist"] <= dv + pu.tolerance(m.verts)).all()
+
+
+def test_full_size_heightfield_sampled(pg):
+    """2,093,058-triangle jittered height field with slivers, 16M queries
+    Gaussian about the surface: invariants on every output, 2000 sampled
+    outputs against the brute-force oracle."""
+    m = dg.workload(2)
+    mesh = build(pg, m)
+    q = torch.from_numpy(m.queries).cuda()
+    r = mesh.query(q, closest=True, prim_type=True)
+    torch.cuda.synchronize()
+    d = r["dist"]
+    assert torch.isfinite(d).all()
+    assert torch.allclose(torch.linalg.norm(q - r["closest"], dim=1), d, atol=2e-6, rtol=1e-5)
+    sel = np.sort(np.random.default_rng(2).choice(m.queries.shape[0], 2000, replace=False))
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries[sel])
+    got = {"dist": d.cpu().numpy()[sel], "prim_id": r["prim_id"].cpu().numpy()[sel],
+           "prim_type": r["prim_type"].cpu().numpy()[sel],
+           "closest": r["closest"].cpu().numpy()[sel]}
+    pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts), "full2")
+
+
+def test_full_size_fwd_bwd_sampled(pg):
+    """327,680-triangle noisy icosphere, 4M near-surface queries, loss
+    sum w_i d_i: forward outputs and the query gradient of 2000 sampled
+    queries against the oracle (away from ties and d = 0), and the vertex
+    gradient against the scatter of the oracle's per-query terms."""
+    m = dg.workload(3)
+    mesh = build(pg, m)
+    q = torch.from_numpy(m.queries).cuda().requires_grad_(True)
+    verts = torch.from_numpy(m.verts).cuda().requires_grad_(True)
+    w = torch.from_numpy(m.weights).cuda()
+    d, pid = pg.distance(q, verts, mesh)
+    (w * d).sum().backward()
+    torch.cuda.synchronize()
+    sel = np.sort(np.random.default_rng(3).choice(m.queries.shape[0], 2000, replace=False))
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries[sel])
+    got = {"dist": d.detach().cpu().numpy()[sel], "prim_id": pid.cpu().numpy()[sel]}
+    got["prim_type"] = mesh.query(q.detach()[sel], prim_type=True)["prim_type"].cpu().numpy()
+    pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts), "full3")
+    gq_ref, _, _ = oracle.gradient(m.queries[sel].astype(np.float64), ref,
+                                   m.weights[sel].astype(np.float64))
+    keep = (ref["dist"] > 1e-4) & (ref["second"] - ref["dist"] > 1e-4)
+    assert np.abs(q.grad.cpu().numpy()[sel][keep] - gq_ref[keep]).max() < 2e-3
+    g = verts.grad
+    assert torch.isfinite(g).all()
+    # every query's weight reaches the vertices: sum of vertex gradients
+    # equals minus the sum of the query gradients (translation invariance)
+    np.testing.assert_allclose(g.sum(0).cpu().numpy(), -q.grad.sum(0).cpu().numpy(),
+                               rtol=2e-3, atol=2e-2)
+
+
+def test_full_size_batch_sampled(pg):
+    """All 64 meshes of the batch workload (about 5.2M triangles, 24M
+    queries) in one persistent launch: 300 sampled outputs per mesh against
+    the brute-force oracle, and bitwise equality with per-mesh queries."""
+    ms = dg.batch_workload(64)
+    meshes = [build(pg, m) for m in ms]
+    qs = [torch.from_numpy(m.queries).cuda() for m in ms]
+    b = pg.P2MBatch(meshes, qs, closest=True, prim_type=True)
+    out = b.run()
+    b.check()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    for m, mesh, q, r in zip(ms, meshes, qs, out):
+        single = mesh.query(q, closest=False, prim_type=False)
+        assert torch.equal(single["dist"], r["dist"]) and torch.equal(single["prim_id"], r["prim_id"])
+        sel = np.sort(rng.choice(m.queries.shape[0], min(300, m.queries.shape[0]), replace=False))
+        o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+        ref = o.bruteforce(m.queries[sel])
+        got = {k: v.cpu().numpy()[sel] for k, v in r.items()}
+        pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts),
+                 m.name)
