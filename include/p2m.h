@@ -191,10 +191,11 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
  * calls; no host synchronisation).  p2m_timing_summary waits for the calls
  * recorded since its previous call and returns {calls, total ms of the
  * Morton sort, of the nearest-vertex pass, of the regrouping by vertex, of
- * the list pass} (the one-pass kernel counts entirely as list pass).
- * Enabling (or disabling) clears the ring. */
+ * the list pass, of the output write} (the one-pass kernel counts entirely
+ * as list pass; its output write is part of it and counts 0).  Enabling (or
+ * disabling) clears the ring. */
 p2m_status p2m_set_timing(p2m_handle *h, int enable);
-p2m_status p2m_timing_summary(p2m_handle *h, double out[5]);
+p2m_status p2m_timing_summary(p2m_handle *h, double out[6]);
 
 /* Work counters of a query batch (device q, n points): runs a counting
  * variant of the query kernel (outputs are not written) and returns the

@@ -172,11 +172,12 @@ class P2M:
     def timing_summary(self):
         """Per-phase totals of the queries made since the previous summary
         (timing enabled): dict with calls, sort_ms, nn_ms, regroup_ms,
-        list_ms (the one-pass kernel counts as list_ms)."""
-        out = (ctypes.c_double * 5)()
+        list_ms, output_ms (the one-pass kernel counts as list_ms)."""
+        out = (ctypes.c_double * 6)()
         check(lib.p2m_timing_summary(self._h, out), "p2m_timing_summary")
         return {"calls": int(out[0]), "sort_ms": float(out[1]), "nn_ms": float(out[2]),
-                "regroup_ms": float(out[3]), "list_ms": float(out[4])}
+                "regroup_ms": float(out[3]), "list_ms": float(out[4]),
+                "output_ms": float(out[5])}
 
     def counters(self, q, stream=None):
         """Work totals of a query batch: internal KD nodes visited, vertices

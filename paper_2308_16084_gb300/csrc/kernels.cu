@@ -737,23 +737,13 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
 
 // ------------------------------------------- two-pass query, grouped lists
 // Pass 1: nearest vertex of every Morton-sorted query (nv marks a
-// non-finite query).  The queries are then regrouped by that vertex with a
-// counting sort, so that the lanes of a warp mostly share one interception
-// list in pass 2 (uniform loops, broadcast loads).
-__global__ void k_nn_pass(DevView m, const float4 *__restrict__ sq, int64_t n, int walk,
-                          uint32_t *__restrict__ vout) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 s = sq[i];
-  vout[i] = finite3(s.x, s.y, s.z) ? (uint32_t)find_nearest(m, walk, s.x, s.y, s.z)
-                                   : (uint32_t)m.nv;
-}
-
-__global__ void k_vertex_count(const uint32_t *__restrict__ vin, int64_t n,
-                               uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t b = vin[i];
+// non-finite query), counted straight into the per-vertex histogram: the
+// lanes that found the same vertex add their count with one atomic, and each
+// keeps its rank inside that vertex's bucket.  The queries are then
+// regrouped by vertex with a counting sort, so that the lanes of a warp
+// mostly share one interception list in pass 2 (uniform loops, broadcast
+// loads).
+__device__ __forceinline__ uint2 count_key(uint32_t b, uint32_t *__restrict__ hist) {
   const unsigned act = __activemask();
   const unsigned peers = __match_any_sync(act, b);
   const int lane = threadIdx.x & 31;
@@ -761,7 +751,17 @@ __global__ void k_vertex_count(const uint32_t *__restrict__ vin, int64_t n,
   uint32_t base = 0;
   if (lane == leader) base = atomicAdd(&hist[b], (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
-  key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+  return make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+}
+
+__global__ void k_nn_pass(DevView m, const float4 *__restrict__ sq, int64_t n, int walk,
+                          uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 s = sq[i];
+  const uint32_t v = finite3(s.x, s.y, s.z) ? (uint32_t)find_nearest(m, walk, s.x, s.y, s.z)
+                                            : (uint32_t)m.nv;
+  key_rank[i] = count_key(v, hist);
 }
 
 __global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
@@ -783,36 +783,67 @@ __global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
 #define P2M_LIST_MIN_BLOCKS 3
 #endif
 
-// Pass 2: the list of each query's nearest vertex (regrouped stream).
-__global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS) k_list_pass(DevView m, const float4 *__restrict__ gq,
-                            const uint32_t *__restrict__ gv, int64_t n, int chunked,
-                            float *dist, float *closest, int32_t *prim_id, uint8_t *prim_type,
-                            float4 *save, uint8_t *status) {
+// Pass 2: the list of each query's nearest vertex (regrouped stream).  The
+// result goes out as one 32-byte record in the caller's order, rec[2o] =
+// (closest xyz, distance), rec[2o+1] = (type << 30 | id, w1, w2, status):
+// a whole sector per query, where separate outputs would each dirty part of
+// one.  k_unpack then streams the records into the requested outputs.
+__global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS)
+k_list_pass(DevView m, const float4 *__restrict__ gq, const uint32_t *__restrict__ gv, int64_t n,
+            int chunked, float4 *__restrict__ rec) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float4 s = gq[i];
   const int64_t o = __float_as_int(s.w);
   const bool ok = finite3(s.x, s.y, s.z);
-  uint8_t st = ok ? 0 : 2;
-  Best r;
-  if (ok) {
-    const int v = (int)gv[i];
-    if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
-        s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
-      st |= 1;
-    const float4 pv = __ldg(&m.kd_points[v]);
-    const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
-    r.d2 = dx * dx + dy * dy + dz * dz;
-    r.cx = pv.x;
-    r.cy = pv.y;
-    r.cz = pv.z;
-    r.tid = (uint32_t)__float_as_int(pv.w);
-    r.w0 = 1.f;
-    r.w1 = 0.f;
-    r.w2 = 0.f;
-    scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr);
+  uint32_t st = ok ? 0u : 2u;
+  if (!ok) {
+    const float nan = __int_as_float(0x7fc00000);
+    rec[2 * o] = make_float4(nan, nan, nan, nan);
+    rec[2 * o + 1] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, __uint_as_float(st));
+    return;
   }
-  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+  const int v = (int)gv[i];
+  if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
+      s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
+    st |= 1u;
+  Best r;
+  const float4 pv = __ldg(&m.kd_points[v]);
+  const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
+  r.d2 = dx * dx + dy * dy + dz * dz;
+  r.cx = pv.x;
+  r.cy = pv.y;
+  r.cz = pv.z;
+  r.tid = (uint32_t)__float_as_int(pv.w);
+  r.w0 = 1.f;
+  r.w1 = 0.f;
+  r.w2 = 0.f;
+  scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr);
+  rec[2 * o] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
+  rec[2 * o + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(st));
+}
+
+// Records (caller order) -> the requested outputs, coalesced.  w0 is rebuilt
+// as (1 - w1) - w2, the same operations the list pass evaluated it with
+// (face: 1 - s - t; edge: 1 - t with w2 = 0; vertex: 1 with w1 = w2 = 0).
+__global__ void k_unpack(const float4 *__restrict__ rec, int64_t n, float *dist, float *closest,
+                         int32_t *prim_id, uint8_t *prim_type, float4 *save, uint8_t *status) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = __ldcs(&rec[2 * i]);
+  const float4 b = __ldcs(&rec[2 * i + 1]);
+  const uint32_t tid = __float_as_uint(b.x);
+  const bool ok = tid != 0xffffffffu;
+  dist[i] = a.w;
+  if (closest) {
+    closest[3 * i] = a.x;
+    closest[3 * i + 1] = a.y;
+    closest[3 * i + 2] = a.z;
+  }
+  prim_id[i] = ok ? (int32_t)(tid & 0x3fffffffu) : -1;
+  if (prim_type) prim_type[i] = ok ? (uint8_t)(tid >> 30) : (uint8_t)0xff;
+  if (save) save[i] = make_float4(b.x, ok ? (1.f - b.y) - b.z : 0.f, b.y, b.z);
+  if (status) status[i] = (uint8_t)__float_as_uint(b.w);
 }
 
 // Counting variant of the query (not timed): sums the per-query work.
@@ -1010,9 +1041,10 @@ size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv) {
   size_t nb = sort_bits > 0 ? ((size_t)1 << sort_bits) : 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t base = al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + al(4 * kMaxScanTiles);
-  if (nv > 0)  // regrouping: vertex per query (twice), second float4 stream, vertex
-               // histogram and offsets
-    base += 2 * al(4 * (size_t)n) + al(16 * (size_t)n) + 2 * al(4 * (size_t)(nv + 1));
+  if (nv > 0)  // regrouping: vertex per query, second float4 stream, 32-byte result
+               // records, vertex histogram and offsets
+    base += al(4 * (size_t)n) + al(16 * (size_t)n) + al(32 * (size_t)n) +
+            2 * al(4 * (size_t)(nv + 1));
   return base + 256;
 }
 
@@ -1060,28 +1092,29 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     const size_t nbm = tune.sort_bits > 0 ? ((size_t)1 << tune.sort_bits) : 0;
     char *b2 = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) + al(16 * (size_t)n) +
                al(8 * (size_t)n) + 2 * al(4 * nbm) + al(4 * kMaxScanTiles);
-    uint32_t *vbuf = (uint32_t *)b2;
-    b2 += al(4 * (size_t)n);
     uint32_t *gv = (uint32_t *)b2;
     b2 += al(4 * (size_t)n);
     float4 *grouped = (float4 *)b2;
     b2 += al(16 * (size_t)n);
+    float4 *rec = (float4 *)b2;
+    b2 += al(32 * (size_t)n);
     uint32_t *vhist = (uint32_t *)b2;
     b2 += al(4 * (size_t)(m.nv + 1));
     uint32_t *voff = (uint32_t *)b2;
     uint32_t *tiles2 = (uint32_t *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) +
                        (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
     const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
-    k_nn_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, walk, vbuf);
-    if (ev) cudaEventRecord(ev[2], stream);
     cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
-    k_vertex_count<<<blocks_for(n, T), T, 0, stream>>>(vbuf, n, vhist, key_rank);
+    k_nn_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, walk, vhist, key_rank);
+    if (ev) cudaEventRecord(ev[2], stream);
     bucket_scan(vhist, voff, tiles2, (int)(m.nv + 1), stream);
     k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped, gv);
     if (ev) cudaEventRecord(ev[3], stream);
-    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped, gv, n, tune.chunked, dist,
-                                                      closest, prim_id, prim_type, save, status);
+    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped, gv, n, tune.chunked, rec);
     if (ev) cudaEventRecord(ev[4], stream);
+    k_unpack<<<blocks_for(n, T), T, 0, stream>>>(rec, n, dist, closest, prim_id, prim_type, save,
+                                                 status);
+    if (ev) cudaEventRecord(ev[5], stream);
     return cudaGetLastError();
   }
   const size_t wsm = (size_t)(bt / 32) * sizeof(WarpSmem);
@@ -1107,7 +1140,10 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     k_query<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, dist, closest, prim_id,
                                                   prim_type, save, status, walk, chunked);
   }
-  if (ev) cudaEventRecord(ev[4], stream);
+  if (ev) {
+    cudaEventRecord(ev[4], stream);
+    cudaEventRecord(ev[5], stream);
+  }
   return cudaGetLastError();
 }
 

@@ -51,11 +51,11 @@ struct QueryTuning {
 size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv = 0);
 
 // Morton bucket sort (a1) + query (a2..a8).  All pointers device.
-// ev (5 events or NULL) marks: start, sorted, nearest vertices found,
-// regrouped by vertex, done (the one-pass kernel records the middle three
-// at the same point as its start); with
-// `counters` (5 device u64) the counting variant runs instead of the query
-// and sums internal nodes, points, entries, edges and faces visited.
+// ev (6 events or NULL) marks: start, sorted, nearest vertices found,
+// regrouped by vertex, list pass done, outputs written (the one-pass kernel
+// records events 2 and 3 where it starts and 4 and 5 where it ends); with
+// `counters` (6 device u64) the counting variant runs instead of the query
+// and sums internal nodes, points, entries, edges, faces and chunk boxes.
 cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dist,
                          float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
                          uint8_t *status, void *scratch, size_t scratch_bytes,

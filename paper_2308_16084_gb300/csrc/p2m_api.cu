@@ -83,8 +83,9 @@ struct p2m_handle {
   size_t scratch_bytes = 0;
   p2m::QueryTuning tune;
   size_t device_bytes = 0;
-  // timing ring: 5 events per recorded p2m_query
+  // timing ring: kEv events per recorded p2m_query
   static constexpr int kRing = 1024;
+  static constexpr int kEv = 6;
   std::vector<cudaEvent_t> ring;
   int64_t ring_next = 0, ring_read = 0;
   unsigned long long *counters = nullptr;
@@ -364,7 +365,7 @@ p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, floa
   if ((s = h->ensure_scratch(need))) return s;
   cudaEvent_t *ev = nullptr;
   if (!h->ring.empty()) {
-    ev = &h->ring[5 * (h->ring_next % p2m_handle::kRing)];
+    ev = &h->ring[p2m_handle::kEv * (h->ring_next % p2m_handle::kRing)];
     ++h->ring_next;
   }
   return from_cuda(p2m::launch_query(h->view, q, n, dist, closest, prim_id, prim_type,
@@ -379,25 +380,26 @@ p2m_status p2m_set_timing(p2m_handle *h, int enable) {
   h->ring.clear();
   h->ring_next = h->ring_read = 0;
   if (enable) {
-    h->ring.resize(5 * p2m_handle::kRing, nullptr);
+    h->ring.resize(p2m_handle::kEv * p2m_handle::kRing, nullptr);
     for (auto &e : h->ring)
       if (cudaEventCreate(&e) != cudaSuccess) return P2M_ERR_CUDA;
   }
   return P2M_OK;
 }
 
-p2m_status p2m_timing_summary(p2m_handle *h, double out[5]) {
+p2m_status p2m_timing_summary(p2m_handle *h, double out[6]) {
   p2m_status s = check_ready(h);
   if (s) return s;
   if (!out || h->ring.empty()) return P2M_ERR_INVALID_ARG;
-  for (int k = 0; k < 5; ++k) out[k] = 0.0;
+  constexpr int E = p2m_handle::kEv;
+  for (int k = 0; k < E; ++k) out[k] = 0.0;
   int64_t first = std::max(h->ring_read, h->ring_next - (int64_t)p2m_handle::kRing);
   for (int64_t k = first; k < h->ring_next; ++k) {
-    cudaEvent_t *ev = &h->ring[5 * (k % p2m_handle::kRing)];
-    cudaError_t e = cudaEventSynchronize(ev[4]);
+    cudaEvent_t *ev = &h->ring[E * (k % p2m_handle::kRing)];
+    cudaError_t e = cudaEventSynchronize(ev[E - 1]);
     if (e != cudaSuccess) return from_cuda(e);
     out[0] += 1.0;
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < E - 1; ++p) {
       float ms = 0;
       e = cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
       if (e != cudaSuccess) return from_cuda(e);
