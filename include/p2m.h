@@ -128,6 +128,28 @@ p2m_status p2m_nearest_vertex(p2m_handle *h, const float *q, int64_t n, int32_t 
 p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
                           int32_t *prim_id, uint8_t *prim_type, void *stream);
 
+/* Pipelined host-buffer queries (the paper queries one point at a time and
+ * has no counterpart; this is p2m_query_host for a stream of batches).  A
+ * pipe holds `depth` (1..8) slots, each with its own CUDA stream and device
+ * scratch sized for batches of up to max_n queries (about 110 B per query
+ * plus the handle's per-vertex histogram); p2m_pipe_create allocates them
+ * (synchronous).  p2m_pipe_submit enqueues one batch on the next slot:
+ * copy q (n x 3 host floats) in, run the query with the handle's current
+ * tuning, copy dist and prim_id (and closest, prim_type when not NULL) out
+ * to the given host buffers, and returns without waiting, except for the
+ * slot's previous batch.  The host buffers must stay untouched until
+ * p2m_pipe_wait returns (or the slot comes round again); they should be
+ * pinned (cudaHostAlloc / torch pin_memory) for the copies to overlap the
+ * kernels of the other slots.  The handle must outlive the pipe.
+ * Errors: INVALID_ARG, OOM, CUDA, TOO_LARGE (n > max_n, max_n >= 2^31). */
+typedef struct p2m_pipe p2m_pipe;
+p2m_status p2m_pipe_create(p2m_handle *h, int64_t max_n, int depth, p2m_pipe **out);
+p2m_status p2m_pipe_submit(p2m_pipe *p, const float *q, int64_t n, float *dist, float *closest,
+                           int32_t *prim_id, uint8_t *prim_type);
+/* Waits for every submitted batch; their host outputs are then complete. */
+p2m_status p2m_pipe_wait(p2m_pipe *p);
+void p2m_pipe_destroy(p2m_pipe *p);
+
 /*
  * p2m_query without any device allocation (the paper has no counterpart;
  * this is a deployment variant of p2m_query).  For callers that must not
@@ -242,12 +264,17 @@ typedef struct {
  *              keyed by (mesh, bucket))
  *   tile       queries per work-queue item, a multiple of block_threads
  *   block_threads, grid_ctas  persistent launch shape (grid_ctas 0 = one
- *              wave: SM count x resident CTAs per SM) */
+ *              wave: SM count x resident CTAs per SM)
+ *   group_by_vertex  1: nearest-vertex pass over all meshes, regroup the
+ *              queries by (mesh, nearest vertex), then the persistent list
+ *              pass (needs sum of (vertex count + 1) <= 2^24); 0: one
+ *              persistent pass per query */
 typedef struct {
   int sort_bits;
   int tile;
   int block_threads;
   int grid_ctas;
+  int group_by_vertex;
 } p2m_batch_tuning;
 
 typedef struct p2m_batch p2m_batch;
@@ -257,9 +284,10 @@ typedef struct p2m_batch p2m_batch;
  * p2m_batch_create checks the slices, allocates the batch's scratch and
  * uploads the mesh descriptors (synchronous; allocates).  p2m_batch_run then
  * enqueues, on `stream`: one Morton sort of all queries keyed by (mesh,
- * bucket), and one persistent query kernel whose CTAs take tiles of the
- * sorted queries from a device work queue (a single atomic counter, so no
- * CTA ever waits on another).  p2m_batch_run allocates nothing and does not
+ * bucket), the nearest-vertex pass and the regrouping by (mesh, vertex),
+ * one persistent list kernel whose CTAs take tiles of the regrouped queries
+ * from a device work queue (a single atomic counter, so no CTA ever waits
+ * on another), then the output write.  p2m_batch_run allocates nothing and does not
  * synchronise, so it can be captured into a CUDA graph.  The handles and
  * the io buffers must stay alive while the batch is used.
  * Errors: INVALID_ARG, OOM, CUDA, TOO_LARGE (total queries >= 2^31),

@@ -45,7 +45,8 @@ class BatchIO(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("sort_bits", ctypes.c_int), ("tile", ctypes.c_int),
-                ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int)]
+                ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
+                ("group_by_vertex", ctypes.c_int)]
 
 
 def _stream(stream=None):
@@ -238,6 +239,11 @@ class P2M:
         check(lib.p2m_query_host(self._h, p(q), int(q.shape[0]), p(dist), p(closest),
                                  p(prim_id), p(prim_type), _stream(stream)), "p2m_query_host")
 
+    def pipeline(self, max_n, depth=2):
+        """A P2MPipe of `depth` slots for host-buffer batches of up to max_n
+        queries."""
+        return P2MPipe(self, max_n, depth)
+
     def backward(self, q, res, grad_dist, grad_q=True, grad_verts=None, stream=None):
         """Gradients of sum(grad_dist * dist): returns (grad_q, grad_verts);
         grad_verts is accumulated into the given (V,3) tensor if passed."""
@@ -293,6 +299,48 @@ def distance(q, verts, mesh):
     return _autograd_cls.apply(q, verts, mesh)
 
 
+def _host_ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class P2MPipe:
+    """Pipelined queries on HOST buffers: each submit() copies a batch in,
+    queries it and copies the results out on the next of `depth` slots
+    (own stream and scratch), without waiting for the other slots, so the
+    copies of one batch overlap the kernels of another.  Buffers should be
+    pinned; they belong to the pipe until wait()."""
+
+    def __init__(self, mesh, max_n, depth=2):
+        self.mesh = mesh  # keeps the handle alive
+        p = ctypes.c_void_p()
+        check(lib.p2m_pipe_create(mesh._h, int(max_n), int(depth), ctypes.byref(p)),
+              "p2m_pipe_create")
+        self._p = p
+
+    def submit(self, q, dist, prim_id, closest=None, prim_type=None):
+        check(lib.p2m_pipe_submit(self._p, _host_ptr(q), int(q.shape[0]), _host_ptr(dist),
+                                  _host_ptr(closest), _host_ptr(prim_id), _host_ptr(prim_type)),
+              "p2m_pipe_submit")
+
+    def wait(self):
+        check(lib.p2m_pipe_wait(self._p), "p2m_pipe_wait")
+
+    def close(self):
+        if getattr(self, "_p", None):
+            lib.p2m_pipe_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class P2MBatch:
     """Many meshes and their query sets in one persistent launch."""
 
@@ -338,13 +386,14 @@ class P2MBatch:
         t = BatchTuning()
         check(lib.p2m_batch_get_tuning(self._b, ctypes.byref(t)), "p2m_batch_get_tuning")
         return {"sort_bits": t.sort_bits, "tile": t.tile, "block_threads": t.block_threads,
-                "grid_ctas": t.grid_ctas}
+                "grid_ctas": t.grid_ctas, "group_by_vertex": t.group_by_vertex}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
-        t = BatchTuning(cur["sort_bits"], cur["tile"], cur["block_threads"], cur["grid_ctas"])
+        t = BatchTuning(cur["sort_bits"], cur["tile"], cur["block_threads"], cur["grid_ctas"],
+                        cur["group_by_vertex"])
         check(lib.p2m_batch_set_tuning(self._b, ctypes.byref(t)), "p2m_batch_set_tuning")
 
     def close(self):

@@ -1033,6 +1033,106 @@ __global__ void k_batch_query(BatchDesc d, const float4 *__restrict__ sorted, in
   }
 }
 
+// Two-pass batch, as in the single-mesh path: nearest vertex of every sorted
+// query, counted into one histogram over all meshes' vertices (key =
+// voff[mesh] + vertex, nv of a mesh marks its non-finite queries); the
+// queries are regrouped by that key, the persistent list pass drains tiles
+// of the regrouped stream and writes one 32-byte record per query in the
+// concatenated caller order, and k_batch_unpack scatters the records into
+// each mesh's outputs.
+__global__ void k_batch_nn(BatchDesc d, const float4 *__restrict__ sorted, int64_t total,
+                           uint32_t *__restrict__ vhist, uint2 *__restrict__ key_rank) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const float4 s = sorted[i];
+  const int64_t gi = __float_as_int(s.w);
+  const int k = mesh_of(s_off, d.n_meshes, gi);
+  const DevView &m = d.views[k];
+  const int walk = !m.nb_off ? 0 : (m.seed ? 2 : 1);
+  const uint32_t v = finite3(s.x, s.y, s.z) ? (uint32_t)find_nearest(m, walk, s.x, s.y, s.z)
+                                            : (uint32_t)m.nv;
+  key_rank[i] = count_key((uint32_t)d.voff[k] + v, vhist);
+}
+
+__global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS)
+k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__restrict__ gv,
+             int64_t total, int tile, float4 *__restrict__ rec, unsigned int *queue_head,
+             unsigned int *error_word) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  __shared__ unsigned int s_item;
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  const int64_t n_items = (total + tile - 1) / tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(queue_head, 1u);
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= n_items) break;
+    const int64_t base = it * (int64_t)tile;
+    for (int t = threadIdx.x; t < tile; t += blockDim.x) {
+      const int64_t pos = base + t;
+      if (pos >= total) break;
+      const float4 s = grouped[pos];
+      const int64_t gi = __float_as_int(s.w);
+      if (gi < 0 || gi >= total) {
+        atomicOr(error_word, 1u);
+        continue;
+      }
+      const int k = mesh_of(s_off, d.n_meshes, gi);
+      const DevView &m = d.views[k];
+      const int64_t v = (int64_t)gv[pos] - d.voff[k];
+      const bool ok = finite3(s.x, s.y, s.z);
+      if (!ok || v < 0 || v >= m.nv) {
+        if (ok) atomicOr(error_word, 2u);
+        const float nan = __int_as_float(0x7fc00000);
+        rec[2 * gi] = make_float4(nan, nan, nan, nan);
+        rec[2 * gi + 1] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, __uint_as_float(2u));
+        continue;
+      }
+      Best r;
+      const float4 pv = __ldg(&m.kd_points[v]);
+      const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
+      r.d2 = dx * dx + dy * dy + dz * dz;
+      r.cx = pv.x;
+      r.cy = pv.y;
+      r.cz = pv.z;
+      r.tid = (uint32_t)__float_as_int(pv.w);
+      r.w0 = 1.f;
+      r.w1 = 0.f;
+      r.w2 = 0.f;
+      scan_list<false>(m, s.x, s.y, s.z, (int)v, 2, r, nullptr);
+      rec[2 * gi] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
+      rec[2 * gi + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(0u));
+    }
+  }
+}
+
+__global__ void k_batch_unpack(BatchDesc d, const float4 *__restrict__ rec, int64_t total) {
+  __shared__ int64_t s_off[kMaxBatchMeshes + 1];
+  for (int k = threadIdx.x; k <= d.n_meshes; k += blockDim.x) s_off[k] = d.qoff[k];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int k = mesh_of(s_off, d.n_meshes, i);
+  const int64_t l = i - s_off[k];
+  const BatchIO &io = d.ios[k];
+  const float4 a = __ldcs(&rec[2 * i]);
+  const float4 b = __ldcs(&rec[2 * i + 1]);
+  const uint32_t tid = __float_as_uint(b.x);
+  const bool ok = tid != 0xffffffffu;
+  io.dist[l] = a.w;
+  if (io.closest) {
+    io.closest[3 * l] = a.x;
+    io.closest[3 * l + 1] = a.y;
+    io.closest[3 * l + 2] = a.z;
+  }
+  io.prim_id[l] = ok ? (int32_t)(tid & 0x3fffffffu) : -1;
+  if (io.prim_type) io.prim_type[l] = ok ? (uint8_t)(tid >> 30) : (uint8_t)0xff;
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -1173,16 +1273,24 @@ cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
   return cudaGetLastError();
 }
 
-size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits) {
+size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits, int64_t nv_keys) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n_meshes << sort_bits;
-  return al(16 * (size_t)total) + al(8 * (size_t)total) + 2 * al(4 * nb) +
-         al(4 * kMaxScanTiles) + 256;
+  size_t b = al(16 * (size_t)total) + al(8 * (size_t)total) + 2 * al(4 * nb) +
+             al(4 * kMaxScanTiles) + 256;
+  if (nv_keys > 0)  // regrouping: vertex key per query, second float4 stream, records,
+                    // vertex histogram and offsets
+    b += al(4 * (size_t)total) + al(16 * (size_t)total) + al(32 * (size_t)total) +
+         2 * al(4 * (size_t)nv_keys);
+  return b;
 }
 
-int batch_occupancy(int block_threads) {
+int batch_occupancy(int block_threads, int group_by_vertex) {
   int blocks = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_query, block_threads, 0);
+  if (group_by_vertex)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_list, block_threads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_query, block_threads, 0);
   return blocks > 0 ? blocks : 1;
 }
 
@@ -1191,7 +1299,9 @@ cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_
                          unsigned int *error_word, cudaStream_t stream) {
   if (total <= 0) return cudaSuccess;
   if (d.n_meshes > kMaxBatchMeshes || t.tile <= 0) return cudaErrorInvalidValue;
-  if (scratch_bytes < batch_scratch_bytes(total, d.n_meshes, t.sort_bits))
+  const int64_t nv_keys = t.group_by_vertex ? d.nv_keys : 0;
+  if (nv_keys > (int64_t)kScanTile * kMaxScanTiles) return cudaErrorInvalidValue;
+  if (scratch_bytes < batch_scratch_bytes(total, d.n_meshes, t.sort_bits, nv_keys))
     return cudaErrorInvalidValue;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   char *base = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
@@ -1211,6 +1321,28 @@ cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_
   bucket_scan(hist, off, tiles, (int)nb, stream);
   k_batch_scatter<<<blocks_for(total, T), T, 0, stream>>>(d, total, key_rank, off, sorted);
   cudaMemsetAsync(queue_head, 0, sizeof(unsigned int), stream);
+  if (nv_keys > 0) {
+    base = (char *)tiles + al(4 * kMaxScanTiles);
+    uint32_t *gv = (uint32_t *)base;
+    base += al(4 * (size_t)total);
+    float4 *grouped = (float4 *)base;
+    base += al(16 * (size_t)total);
+    float4 *rec = (float4 *)base;
+    base += al(32 * (size_t)total);
+    uint32_t *vhist = (uint32_t *)base;
+    base += al(4 * (size_t)nv_keys);
+    uint32_t *voff = (uint32_t *)base;
+    cudaMemsetAsync(vhist, 0, 4 * (size_t)nv_keys, stream);
+    k_batch_nn<<<blocks_for(total, t.block_threads), t.block_threads, 0, stream>>>(
+        d, sorted, total, vhist, key_rank);
+    bucket_scan(vhist, voff, tiles, (int)nv_keys, stream);
+    k_vertex_scatter<<<blocks_for(total, T), T, 0, stream>>>(sorted, total, key_rank, voff,
+                                                             grouped, gv);
+    k_batch_list<<<grid, t.block_threads, 0, stream>>>(d, grouped, gv, total, t.tile, rec,
+                                                       queue_head, error_word);
+    k_batch_unpack<<<blocks_for(total, T), T, 0, stream>>>(d, rec, total);
+    return cudaGetLastError();
+  }
   k_batch_query<<<grid, t.block_threads, 0, stream>>>(d, sorted, total, t.tile, queue_head,
                                                       error_word);
   return cudaGetLastError();

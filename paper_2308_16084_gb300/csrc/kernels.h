@@ -91,19 +91,22 @@ struct BatchDesc {           // device pointers
   const DevView *views;      // n_meshes
   const BatchIO *ios;        // n_meshes
   const int64_t *qoff;       // n_meshes + 1 prefix sums of the query counts
+  const int64_t *voff;       // n_meshes + 1 prefix sums of (vertex count + 1)
   int n_meshes;
+  int64_t nv_keys;           // voff[n_meshes] (host copy)
 };
 struct BatchTuning {
   int sort_bits = 12;
   int tile = 1024;
   int block_threads = 256;
   int grid_ctas = 0;
+  int group_by_vertex = 1;  // two-pass: nearest vertex, regroup, persistent list pass
 };
-size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits);
+size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits, int64_t nv_keys = 0);
 cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_t scratch_bytes,
                          const BatchTuning &t, int grid, unsigned int *queue_head,
                          unsigned int *error_word, cudaStream_t stream);
 // resident CTAs per SM of the persistent kernel for a block size
-int batch_occupancy(int block_threads);
+int batch_occupancy(int block_threads, int group_by_vertex);
 
 }  // namespace p2m

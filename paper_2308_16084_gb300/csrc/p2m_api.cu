@@ -488,6 +488,131 @@ p2m_status p2m_query_host(p2m_handle *h, const float *q, int64_t n, float *dist,
   return from_cuda(e);
 }
 
+}  // extern "C"
+
+// A pipeline of host-memory queries: `depth` slots, each with its own
+// stream, device scratch and staging buffers, used round robin.  The copies
+// of one slot run on the copy engines while another slot's kernels run, so
+// a stream of batches costs about max(kernels, copies) per batch instead of
+// their sum.
+struct p2m_pipe {
+  struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    bool busy = false;
+  };
+  p2m_handle *h = nullptr;
+  int64_t max_n = 0;
+  std::vector<Slot> slots;
+  int64_t next = 0;
+  ~p2m_pipe() {
+    for (auto &s : slots) {
+      if (s.stream) cudaStreamSynchronize(s.stream);
+      if (s.mem) cudaFree(s.mem);
+      if (s.done) cudaEventDestroy(s.done);
+      if (s.stream) cudaStreamDestroy(s.stream);
+    }
+  }
+  // query scratch for any tuning (sort bits up to 24) + staging of q and of
+  // the outputs
+  size_t query_bytes() const {
+    return (p2m::query_scratch_bytes(max_n, 24, h->L.nv) + 255) & ~(size_t)255;
+  }
+  size_t slot_bytes() const {
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t n = (size_t)max_n;
+    return query_bytes() + al(12 * n) + al(4 * n) + al(12 * n) + al(4 * n) + al(n) + 256;
+  }
+};
+
+extern "C" {
+
+p2m_status p2m_pipe_create(p2m_handle *h, int64_t max_n, int depth, p2m_pipe **out) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (!out || max_n <= 0 || depth < 1 || depth > 8) return P2M_ERR_INVALID_ARG;
+  if (max_n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
+  *out = nullptr;
+  std::unique_ptr<p2m_pipe> p(new (std::nothrow) p2m_pipe());
+  if (!p) return P2M_ERR_OOM;
+  p->h = h;
+  p->max_n = max_n;
+  p->slots.resize(depth);
+  for (auto &sl : p->slots) {
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      sl.bytes = p->slot_bytes();
+      e = cudaMalloc(&sl.mem, sl.bytes);
+      if (e != cudaSuccess) sl.mem = nullptr;
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  *out = p.release();
+  return P2M_OK;
+}
+
+p2m_status p2m_pipe_submit(p2m_pipe *p, const float *q, int64_t n, float *dist, float *closest,
+                           int32_t *prim_id, uint8_t *prim_type) {
+  if (!p) return P2M_ERR_INVALID_ARG;
+  p2m_handle *h = p->h;
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
+  if (n > p->max_n) return P2M_ERR_TOO_LARGE;
+  p2m_pipe::Slot &sl = p->slots[p->next % (int64_t)p->slots.size()];
+  // the slot's previous batch must be done before its buffers are reused
+  cudaError_t e = sl.busy ? cudaEventSynchronize(sl.done) : cudaSuccess;
+  if (e != cudaSuccess) return from_cuda(e);
+  sl.busy = false;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nn = (size_t)p->max_n;
+  char *base = (char *)(((uintptr_t)sl.mem + 255) & ~(uintptr_t)255) + p->query_bytes();
+  float *dq = (float *)base;
+  base += al(12 * nn);
+  float *dd = (float *)base;
+  base += al(4 * nn);
+  float *dc = (float *)base;
+  base += al(12 * nn);
+  int32_t *dp = (int32_t *)base;
+  base += al(4 * nn);
+  uint8_t *dt = (uint8_t *)base;
+  cudaStream_t st = sl.stream;
+  e = cudaMemcpyAsync(dq, q, 12 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = p2m::launch_query(h->view, dq, n, dd, closest ? dc : nullptr, dp,
+                          prim_type ? dt : nullptr, nullptr, nullptr, sl.mem, p->query_bytes(),
+                          h->tune, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dist, dd, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(prim_id, dp, 4 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && closest)
+    e = cudaMemcpyAsync(closest, dc, 12 * (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && prim_type)
+    e = cudaMemcpyAsync(prim_type, dt, (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, st);
+  if (e != cudaSuccess) return from_cuda(e);
+  sl.busy = true;
+  ++p->next;
+  return P2M_OK;
+}
+
+p2m_status p2m_pipe_wait(p2m_pipe *p) {
+  if (!p) return P2M_ERR_INVALID_ARG;
+  for (auto &sl : p->slots) {
+    if (!sl.busy) continue;
+    cudaError_t e = cudaEventSynchronize(sl.done);
+    if (e != cudaSuccess) return from_cuda(e);
+    sl.busy = false;
+  }
+  return P2M_OK;
+}
+
+void p2m_pipe_destroy(p2m_pipe *p) { delete p; }
+
 p2m_status p2m_backward(p2m_handle *h, const float *q, const float *dist, const float *closest,
                         const float *save, const float *grad_dist, int64_t n, float *grad_q,
                         float *grad_verts, void *stream) {
@@ -574,6 +699,8 @@ struct p2m_batch {
   DevBuf<p2m::DevView> views;
   DevBuf<p2m::BatchIO> ios;
   DevBuf<int64_t> qoff;
+  DevBuf<int64_t> voff;        // prefix sums of (vertex count + 1) per mesh
+  int64_t nv_keys = 0;
   DevBuf<unsigned int> words;  // [0] queue head, [1] error word
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -584,10 +711,10 @@ struct p2m_batch {
   }
   int grid() const {
     if (tune.grid_ctas > 0) return tune.grid_ctas;
-    return sms * p2m::batch_occupancy(tune.block_threads);
+    return sms * p2m::batch_occupancy(tune.block_threads, tune.group_by_vertex);
   }
-  p2m_status ensure(int sort_bits) {
-    size_t need = p2m::batch_scratch_bytes(total, n, sort_bits);
+  p2m_status ensure(int sort_bits, int group) {
+    size_t need = p2m::batch_scratch_bytes(total, n, sort_bits, group ? nv_keys : 0);
     if (need <= scratch_bytes) return P2M_OK;
     if (scratch) cudaFree(scratch);
     scratch = nullptr;
@@ -601,7 +728,7 @@ struct p2m_batch {
     return P2M_OK;
   }
   p2m::BatchDesc desc() const {
-    return {views.p, ios.p, qoff.p, n};
+    return {views.p, ios.p, qoff.p, voff.p, n, nv_keys};
   }
 };
 
@@ -615,7 +742,7 @@ p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, i
   if (!b) return P2M_ERR_OOM;
   b->n = n_meshes;
   std::vector<p2m::DevView> v(n_meshes);
-  std::vector<int64_t> off(n_meshes + 1, 0);
+  std::vector<int64_t> off(n_meshes + 1, 0), vo(n_meshes + 1, 0);
   for (int k = 0; k < n_meshes; ++k) {
     p2m_status s = check_ready(meshes[k]);
     if (s) return s;
@@ -626,7 +753,10 @@ p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, i
                      io[k].prim_type});
     v[k] = meshes[k]->view;
     off[k + 1] = off[k] + io[k].n;
+    vo[k + 1] = vo[k] + meshes[k]->L.nv + 1;
   }
+  b->nv_keys = vo[n_meshes];
+  if (b->nv_keys > ((int64_t)1 << 24)) b->tune.group_by_vertex = 0;
   b->total = off[n_meshes];
   if (b->total >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
   int dev = 0;
@@ -635,10 +765,11 @@ p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, i
   cudaError_t e = b->views.upload(v.data(), v.size());
   if (e == cudaSuccess) e = b->ios.upload(b->io.data(), b->io.size());
   if (e == cudaSuccess) e = b->qoff.upload(off.data(), off.size());
+  if (e == cudaSuccess) e = b->voff.upload(vo.data(), vo.size());
   unsigned int zero[2] = {0, 0};
   if (e == cudaSuccess) e = b->words.upload(zero, 2);
   if (e != cudaSuccess) return from_cuda(e);
-  p2m_status s = b->ensure(b->tune.sort_bits);
+  p2m_status s = b->ensure(b->tune.sort_bits, b->tune.group_by_vertex);
   if (s) return s;
   *out = b.release();
   return P2M_OK;
@@ -646,7 +777,8 @@ p2m_status p2m_batch_create(p2m_handle *const *meshes, const p2m_batch_io *io, i
 
 p2m_status p2m_batch_run(p2m_batch *b, void *stream) {
   if (!b) return P2M_ERR_INVALID_ARG;
-  if (b->scratch_bytes < p2m::batch_scratch_bytes(b->total, b->n, b->tune.sort_bits))
+  if (b->scratch_bytes < p2m::batch_scratch_bytes(b->total, b->n, b->tune.sort_bits,
+                                                  b->tune.group_by_vertex ? b->nv_keys : 0))
     return P2M_ERR_INVALID_ARG;
   return from_cuda(p2m::launch_batch(b->desc(), b->total, b->scratch, b->scratch_bytes, b->tune,
                                      b->grid(), b->words.p, b->words.p + 1,
@@ -659,6 +791,7 @@ p2m_status p2m_batch_get_tuning(const p2m_batch *b, p2m_batch_tuning *t) {
   t->tile = b->tune.tile;
   t->block_threads = b->tune.block_threads;
   t->grid_ctas = b->tune.grid_ctas;
+  t->group_by_vertex = b->tune.group_by_vertex;
   return P2M_OK;
 }
 
@@ -668,13 +801,16 @@ p2m_status p2m_batch_set_tuning(p2m_batch *b, const p2m_batch_tuning *t) {
       t->block_threads != 512)
     return P2M_ERR_INVALID_ARG;
   if (t->tile <= 0 || t->tile % t->block_threads) return P2M_ERR_INVALID_ARG;
+  if (t->group_by_vertex != 0 && t->group_by_vertex != 1) return P2M_ERR_INVALID_ARG;
   if (((int64_t)b->n << t->sort_bits) > ((int64_t)1 << 24)) return P2M_ERR_TOO_LARGE;
-  p2m_status s = b->ensure(t->sort_bits);
+  if (t->group_by_vertex && b->nv_keys > ((int64_t)1 << 24)) return P2M_ERR_TOO_LARGE;
+  p2m_status s = b->ensure(t->sort_bits, t->group_by_vertex);
   if (s) return s;
   b->tune.sort_bits = t->sort_bits;
   b->tune.tile = t->tile;
   b->tune.block_threads = t->block_threads;
   b->tune.grid_ctas = t->grid_ctas;
+  b->tune.group_by_vertex = t->group_by_vertex;
   return P2M_OK;
 }
 
@@ -704,12 +840,14 @@ p2m_status p2m_batch_autotune(p2m_batch *b, int reps, void *stream, float *best_
   const int tile_c[] = {256, 1024, 4096};
   const int block_c[] = {128, 256};
   p2m_status status = P2M_OK;
-  for (int bits : bits_c)
-    for (int tile : tile_c)
-      for (int bt : block_c) {
-        if (tile % bt) continue;
-        if (((int64_t)b->n << bits) > ((int64_t)1 << 22)) continue;
-        p2m_batch_tuning t{bits, tile, bt, 0};
+  for (int group = 1; group >= 0; --group)
+    for (int bits : bits_c)
+      for (int tile : tile_c)
+        for (int bt : block_c) {
+          if (tile % bt) continue;
+          if (((int64_t)b->n << bits) > ((int64_t)1 << 22)) continue;
+          if (group && b->nv_keys > ((int64_t)1 << 24)) continue;
+          p2m_batch_tuning t{bits, tile, bt, 0, group};
         if (p2m_batch_set_tuning(b, &t) != P2M_OK) continue;
         if ((status = p2m_batch_run(b, st))) goto done;
         cudaEventRecord(e0, st);
@@ -726,7 +864,7 @@ p2m_status p2m_batch_autotune(p2m_batch *b, int reps, void *stream, float *best_
         }
       }
 done:
-  b->ensure(best.sort_bits);
+  b->ensure(best.sort_bits, best.group_by_vertex);
   b->tune = best;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

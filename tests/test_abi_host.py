@@ -162,3 +162,6 @@ def test_queries_on_host_only_handle_fail_loudly(pg):
     with pytest.raises(pg.P2MError) as e:
         h.query_host(np.zeros((n, 3), np.float32), dist, pid)
     assert e.value.code == 8
+    with pytest.raises(pg.P2MError) as e:
+        h.pipeline(n)
+    assert e.value.code == 8

@@ -167,6 +167,37 @@ def test_host_api_matches_device_api(pg):
     np.testing.assert_array_equal(pt, dev["prim_type"])
 
 
+def test_pipeline_matches_device_api(pg):
+    """Pipelined host batches (slots reused round robin, ragged sizes) give
+    the same bits as the device-buffer query."""
+    m = dg.workload(0, n_queries=30000)
+    mesh = build(pg, m)
+    batches = [m.queries, dg.workload(0, n_queries=12345).queries,
+               dg.workload(0, n_queries=30000).queries[::-1].copy(), m.queries[:1]]
+    pipe = mesh.pipeline(30000, depth=2)
+    outs = []
+    for qb in batches:
+        n = qb.shape[0]
+        o = {"q": torch.from_numpy(qb).pin_memory(),
+             "dist": torch.empty(n).pin_memory(),
+             "prim_id": torch.empty(n, dtype=torch.int32).pin_memory(),
+             "closest": torch.empty(n, 3).pin_memory(),
+             "prim_type": torch.empty(n, dtype=torch.uint8).pin_memory()}
+        pipe.submit(o["q"], o["dist"], o["prim_id"], o["closest"], o["prim_type"])
+        outs.append(o)
+    pipe.wait()
+    for qb, o in zip(batches, outs):
+        dev = run(mesh, qb)
+        for k in ("dist", "prim_id", "closest", "prim_type"):
+            np.testing.assert_array_equal(o[k].numpy(), dev[k])
+    big = torch.zeros(30001, 3).pin_memory()
+    with pytest.raises(pg.P2MError) as e:
+        pipe.submit(big, torch.empty(30001).pin_memory(),
+                    torch.empty(30001, dtype=torch.int32).pin_memory())
+    assert e.value.code == 9
+    pipe.close()
+
+
 # ------------------------------------------------------------------ backward
 
 def test_backward_against_oracle_gradient(pg):
@@ -233,19 +264,28 @@ def _batch_meshes(pg, n_meshes=6):
     return ms, meshes
 
 
-def test_batched_matches_single_and_oracle(pg):
+@pytest.mark.parametrize("group", [1, 0])
+def test_batched_matches_single_and_oracle(pg, group):
     ms, meshes = _batch_meshes(pg)
     qs = [torch.from_numpy(m.queries).cuda() for m in ms]
+    # a few non-finite queries in one mesh
+    qs[1][:3] = torch.tensor([[float("nan"), 0, 0], [0, float("inf"), 0], [0, 0, -float("inf")]])
     b = pg.P2MBatch(meshes, qs, closest=True, prim_type=True)
+    b.tuning = {"group_by_vertex": group}
+    assert b.tuning["group_by_vertex"] == group
     out = b.run()
     b.check()
     torch.cuda.synchronize()
-    for m, mesh, r in zip(ms, meshes, out):
-        single = run(mesh, m.queries)
+    for m, mesh, r, q in zip(ms, meshes, out, qs):
+        qn = q.cpu().numpy()
+        single = run(mesh, qn)
         np.testing.assert_array_equal(r["dist"].cpu().numpy(), single["dist"])
         np.testing.assert_array_equal(r["prim_id"].cpu().numpy(), single["prim_id"])
+        np.testing.assert_array_equal(r["closest"].cpu().numpy(), single["closest"])
+        np.testing.assert_array_equal(r["prim_type"].cpu().numpy(), single["prim_type"])
         o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
         sel = np.arange(0, m.queries.shape[0], 5)
+        sel = sel[np.isfinite(qn[sel]).all(1)]
         ref = o.bruteforce(m.queries[sel])
         got = {k: v.cpu().numpy()[sel] for k, v in r.items()}
         pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts),
