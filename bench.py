@@ -345,9 +345,12 @@ class ClockSampler:
 # --------------------------------------------------------------- our arm
 
 def kernel_hash():
+    """Digest of the device sources (kernels and the box decoding they
+    include): a stored ncu figure is used only while it matches."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2308_16084_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("kernels.cu", "kernels.h", "quant.h"):
+        with open(os.path.join(ROOT, "paper_2308_16084_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
