@@ -258,21 +258,40 @@ struct SortParams {
   int shift;
 };
 
+// Counting-sort passes over kSortItems queries per thread (item k of a
+// block at base + k * blockDim.x, coalesced per item): every thread issues
+// all of its atomics (count) or gathers (scatter) before it waits on the
+// first, which keeps several in flight per thread.
+constexpr int kSortItems = 4;
+
 __global__ void k_bucket_count(const float *__restrict__ q, int64_t n, SortParams sp,
                                uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float x = q[3 * i], y = q[3 * i + 1], z = q[3 * i + 2];
-  const uint32_t b = morton_bucket(x, y, z, sp.lo, sp.inv, sp.shift);
-  // warp-aggregated atomic: lanes of one bucket share a single atomicAdd
-  const unsigned act = __activemask();
-  const unsigned peers = __match_any_sync(act, b);
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kSortItems + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&hist[b], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  key_rank[i] = make_uint2(b, base + __popc(peers & ((1u << lane) - 1u)));
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t b[kSortItems], got[kSortItems];
+  unsigned peers[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    b[k] = i < n ? morton_bucket(q[3 * i], q[3 * i + 1], q[3 * i + 2], sp.lo, sp.inv, sp.shift)
+                 : 0xffffffffu;  // past the end: no bucket has this key
+  }
+  // warp-aggregated atomics: lanes of one bucket share a single atomicAdd
+  // (every lane of the warp stays in the kernel, so the masks are full)
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    peers[k] = __match_any_sync(0xffffffffu, b[k]);
+    got[k] = 0;
+    if (b[k] != 0xffffffffu && lane == __ffs(peers[k]) - 1)
+      got[k] = atomicAdd(&hist[b[k]], (uint32_t)__popc(peers[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    got[k] = __shfl_sync(0xffffffffu, got[k], __ffs(peers[k]) - 1);
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    if (i < n) key_rank[i] = make_uint2(b[k], got[k] + __popc(peers[k] & below));
+  }
 }
 
 // Exclusive scan of hist[0..nb) into off[0..nb) over many CTAs: every CTA
@@ -373,10 +392,25 @@ inline void bucket_scan(const uint32_t *hist, uint32_t *off, uint32_t *tiles, in
 __global__ void k_bucket_scatter(const float *__restrict__ q, int64_t n,
                                  const uint2 *__restrict__ key_rank,
                                  const uint32_t *__restrict__ off, float4 *__restrict__ sorted) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint2 kr = key_rank[i];
-  sorted[off[kr.x] + kr.y] = make_float4(q[3 * i], q[3 * i + 1], q[3 * i + 2], __int_as_float((int)i));
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kSortItems + threadIdx.x;
+  uint2 kr[kSortItems];
+  uint32_t pos[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    kr[k] = i < n ? key_rank[i] : make_uint2(0u, 0u);
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    pos[k] = i < n ? off[kr[k].x] + kr[k].y : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + (int64_t)k * blockDim.x;
+    if (i < n)
+      sorted[pos[k]] = make_float4(q[3 * i], q[3 * i + 1], q[3 * i + 2], __int_as_float((int)i));
+  }
 }
 
 __global__ void k_identity(const float *__restrict__ q, int64_t n, float4 *__restrict__ sorted) {
@@ -1178,9 +1212,10 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     }
     sp.shift = 30 - tune.sort_bits;
     cudaMemsetAsync(hist, 0, 4 * nb, stream);
-    k_bucket_count<<<blocks_for(n, T), T, 0, stream>>>(q, n, sp, hist, key_rank);
+    k_bucket_count<<<blocks_for(n, T * kSortItems), T, 0, stream>>>(q, n, sp, hist, key_rank);
     bucket_scan(hist, off, tiles, (int)nb, stream);
-    k_bucket_scatter<<<blocks_for(n, T), T, 0, stream>>>(q, n, key_rank, off, sorted);
+    k_bucket_scatter<<<blocks_for(n, T * kSortItems), T, 0, stream>>>(q, n, key_rank, off,
+                                                                      sorted);
   } else {
     k_identity<<<blocks_for(n, T), T, 0, stream>>>(q, n, sorted);
   }
