@@ -982,12 +982,14 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   int64_t maxl = 0;
   for (int64_t p = 0; p < nv; ++p) maxl = std::max<int64_t>(maxl, out.row_off[p + 1] - out.row_off[p]);
 
-  // ---- chunks of every row, and the 16-bit boxes
+  // ---- chunks of every row, and the 15-bit box codes (quant.h)
+  float qstep[3], qbase[3];
   for (int d = 0; d < 3; ++d) {
     float flo = (float)(Dlo[d] - 4 * delta), fhi = (float)(Dhi[d] + 4 * delta);
     out.qframe_lo[d] = flo;
-    out.qframe_step[d] = q_step(flo, fhi);
+    out.qframe_inv[d] = (float)((double)(kQMax - 16) / ((double)fhi - (double)flo));
   }
+  q_frame_derive(out.qframe_lo, out.qframe_inv, qstep, qbase);
   out.chunk_off.assign(nv + 1, 0);
   for (int64_t p = 0; p < nv; ++p) {
     uint32_t len = out.row_off[p + 1] - out.row_off[p];
@@ -996,11 +998,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   out.chunks.assign(4 * (size_t)out.chunk_off[nv], 0u);
   out.entries.assign(4 * (size_t)total, 0u);
   std::atomic<int64_t> bad_boxes{0};
-  auto pack = [](const uint32_t *q, uint32_t *w) {
-    w[0] = q[0] | q[1] << 16;
-    w[1] = q[2] | q[3] << 16;
-    w[2] = q[4] | q[5] << 16;
-  };
   parallel_for(nv, threads, 1024, [&](int64_t p, int) {
     uint32_t c = out.chunk_off[p];
     for (uint32_t j = out.row_off[p]; j < out.row_off[p + 1]; j += Layout::kChunk, ++c) {
@@ -1011,35 +1008,49 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
           lo[d] = std::min(lo[d], all[k].box[d]);
           hi[d] = std::max(hi[d], all[k].box[3 + d]);
         }
-      uint32_t q[6];
+      // chunk codes: the entries' hull, two codes wider on each side, so
+      // that an entry test that passes implies a chunk test that passes
+      // (the entry frame is never coarser than this one)
+      uint32_t cl[3], ch[3];
       for (int d = 0; d < 3; ++d) {
-        q[d] = q_enc_lo(lo[d], out.qframe_lo[d], out.qframe_step[d]);
-        q[3 + d] = q_enc_hi(hi[d], out.qframe_lo[d], out.qframe_step[d]);
+        const uint32_t a = q_code(lo[d], out.qframe_lo[d], out.qframe_inv[d]);
+        const uint32_t b = q_code(hi[d], out.qframe_lo[d], out.qframe_inv[d]);
+        cl[d] = a >= 2 ? a - 2 : 0;
+        ch[d] = std::min(kQMax, b + 2);
       }
       uint32_t *cw = &out.chunks[4 * (size_t)c];
-      pack(q, cw);
-      float clo[3], chi[3], cstep[3];
-      q_unpack(cw[0], cw[1], cw[2], out.qframe_lo, out.qframe_step, clo, chi);
+      q_words(cl, ch, cw);
+      // entry frame: origin from the chunk codes, scale inv_g * 2^e with the
+      // largest e that keeps the entries clear of the frame's top code
+      float clo[3], cinv[3];
+      uint32_t w3 = 0;
       for (int d = 0; d < 3; ++d) {
-        if (clo[d] > lo[d] || chi[d] < hi[d]) ++bad_boxes;
-        cstep[d] = q_step(clo[d], chi[d]);
+        clo[d] = q_chunk_lo(cl[d], qstep[d], qbase[d]);
+        const double ext = std::max((double)hi[d] - (double)clo[d], 0.0);
+        uint32_t e = 0;
+        while (e < 60 && ext * (double)out.qframe_inv[d] * std::ldexp(1.0, (int)e + 1) <=
+                             (double)(kQMax - 64))
+          ++e;
+        w3 |= e << (8 * d);
       }
+      cw[3] = w3;
+      for (int d = 0; d < 3; ++d) cinv[d] = q_chunk_inv(out.qframe_inv[d], w3, d);
       for (uint32_t k = j; k < j + cnt; ++k) {
         uint32_t *ew = &out.entries[4 * (size_t)k];
         ew[0] = (uint32_t)all[k].tid;
+        uint32_t el[3], eh[3];
         for (int d = 0; d < 3; ++d) {
-          q[d] = q_enc_lo(all[k].box[d], clo[d], cstep[d]);
-          q[3 + d] = q_enc_hi(all[k].box[3 + d], clo[d], cstep[d]);
+          el[d] = q_code(all[k].box[d], clo[d], cinv[d]);
+          eh[d] = q_code(all[k].box[3 + d], clo[d], cinv[d]);
+          // inside the frame, never clamped: queries far outside fail
+          if (el[d] < 1 || eh[d] >= kQMax) ++bad_boxes;
         }
-        pack(q, ew + 1);
-        float elo[3], ehi[3];
-        q_unpack(ew[1], ew[2], ew[3], clo, cstep, elo, ehi);
-        for (int d = 0; d < 3; ++d)
-          if (elo[d] > all[k].box[d] || ehi[d] < all[k].box[3 + d]) ++bad_boxes;
+        q_words(el, eh, ew + 1);
       }
     }
   });
-  // second level: boxes of every kChunk consecutive chunks of a row
+  // second level: codes of every kChunk consecutive chunks of a row (their
+  // hull, so a chunk that passes lies in a super-chunk that passes)
   out.super_off.assign(nv + 1, 0);
   for (int64_t p = 0; p < nv; ++p) {
     uint32_t nc = out.chunk_off[p + 1] - out.chunk_off[p];
@@ -1050,31 +1061,20 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     uint32_t sidx = out.super_off[p];
     for (uint32_t c = out.chunk_off[p]; c < out.chunk_off[p + 1]; c += Layout::kChunk, ++sidx) {
       uint32_t ce = std::min<uint32_t>(c + Layout::kChunk, out.chunk_off[p + 1]);
-      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      uint32_t sl[3] = {kQMax, kQMax, kQMax}, sh[3] = {0, 0, 0};
       for (uint32_t k = c; k < ce; ++k) {
-        const uint32_t *cw = &out.chunks[4 * (size_t)k];
-        float clo[3], chi[3];
-        q_unpack(cw[0], cw[1], cw[2], out.qframe_lo, out.qframe_step, clo, chi);
+        uint32_t cl[3], ch[3];
+        q_unwords(&out.chunks[4 * (size_t)k], cl, ch);
         for (int d = 0; d < 3; ++d) {
-          lo[d] = std::min(lo[d], clo[d]);
-          hi[d] = std::max(hi[d], chi[d]);
+          sl[d] = std::min(sl[d], cl[d]);
+          sh[d] = std::max(sh[d], ch[d]);
         }
       }
-      uint32_t q[6];
-      for (int d = 0; d < 3; ++d) {
-        q[d] = q_enc_lo(lo[d], out.qframe_lo[d], out.qframe_step[d]);
-        q[3 + d] = q_enc_hi(hi[d], out.qframe_lo[d], out.qframe_step[d]);
-      }
-      uint32_t *sw = &out.supers[4 * (size_t)sidx];
-      pack(q, sw);
-      float slo[3], shi[3];
-      q_unpack(sw[0], sw[1], sw[2], out.qframe_lo, out.qframe_step, slo, shi);
-      for (int d = 0; d < 3; ++d)
-        if (slo[d] > lo[d] || shi[d] < hi[d]) ++bad_boxes;
+      q_words(sl, sh, &out.supers[4 * (size_t)sidx]);
     }
   });
   if (bad_boxes.load()) {
-    err = "internal error: a quantised Region box does not contain its box";
+    err = "internal error: a Region box does not fit the code frame of its chunk";
     return 5;
   }
 

@@ -55,12 +55,12 @@ struct Layout {
   std::vector<uint32_t> row_off;   // nv + 1
   // Entries of each row are in spatial (Morton) order of their Region-box
   // centres and grouped into chunks of up to kChunk consecutive entries (a
-  // one-level R-tree per list, Sec. 4.6).  Boxes are 16-bit (quant.h):
-  //   chunk c: {lo.x | lo.y<<16, lo.z | hi.x<<16, hi.y | hi.z<<16, 0}
-  //            in the frame qframe (D widened by 4 delta)
-  //   entry j: {typed id, lo.x | lo.y<<16, lo.z | hi.x<<16, hi.y | hi.z<<16}
-  //            in the decoded box of its chunk; typed id = type << 30 | id
-  //            (type 1 = edge, 2 = face)
+  // one-level R-tree per list, Sec. 4.6).  Boxes are 15-bit integer codes
+  // (quant.h):
+  //   chunk c: {3 words of codes in the frame qframe (D widened by 4 delta),
+  //             entry-frame exponents e.x | e.y << 8 | e.z << 16}
+  //   entry j: {typed id, 3 words of codes in its chunk's entry frame};
+  //            typed id = type << 30 | id (type 1 = edge, 2 = face)
   // Entry j of row r belongs to chunk chunk_off[r] + (j - row_off[r]) / kChunk.
   static constexpr int kChunk = 8;
   std::vector<uint32_t> entries;   // n_entries * 4
@@ -68,10 +68,10 @@ struct Layout {
   std::vector<uint32_t> chunks;    // n_chunks * 4
   // second level: super-chunk s of row r covers chunks
   // chunk_off[r] + kChunk*(s - super_off[r]) ... (up to kChunk of them); its
-  // box (same 16-bit frame as the chunks) contains their decoded boxes
+  // codes (same frame as the chunks) are the hull of their codes
   std::vector<uint32_t> super_off; // nv + 1
   std::vector<uint32_t> supers;    // n_supers * 4
-  float qframe_lo[3] = {0, 0, 0}, qframe_step[3] = {0, 0, 0};
+  float qframe_lo[3] = {0, 0, 0}, qframe_inv[3] = {0, 0, 0};
   // geometry records
   //   edge e: {a.x, a.y, a.z, 1/|b-a|^2}, {b.x-a.x, b.y-a.y, b.z-a.z, 0}
   //   face f: {a, A}, {b-a, B}, {c-a, C} with the projection weights

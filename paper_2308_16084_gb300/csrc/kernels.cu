@@ -427,18 +427,15 @@ struct Best {
   float w0, w1, w2;
 };
 
-// a4 + a6/a7 for list entry j: Region-box test (box decoded in its chunk's
-// frame clo/cstep), then the gated distance.  Exact ties keep the lower
-// typed id (vertex < edge < face, then lower id), so the result does not
-// depend on the order of the list.
+// a4 + a6/a7 for list entry j: Region-box test (the query's codes qw in its
+// chunk's entry frame against the entry's codes, quant.h), then the gated
+// distance.  Exact ties keep the lower typed id (vertex < edge < face, then
+// lower id), so the result does not depend on the order of the list.
 template <bool COUNT>
 __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy, float qz,
-                                           uint32_t j, const float *clo, const float *cstep,
-                                           Best &r, Work *wk) {
+                                           uint32_t j, const uint32_t *qw, Best &r, Work *wk) {
   const uint4 e = __ldg(&m.entries[j]);
-  float lo[3], hi[3];
-  q_unpack(e.y, e.z, e.w, clo, cstep, lo, hi);
-  if (qx < lo[0] || qy < lo[1] || qz < lo[2] || qx > hi[0] || qy > hi[1] || qz > hi[2]) return;
+  if (!q_pass(qw, e.y, e.z, e.w)) return;
   const uint32_t tid = e.x;
   const uint32_t id = tid & 0x3fffffffu;
   if ((tid >> 30) == 1u) {
@@ -492,45 +489,51 @@ __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy,
   }
 }
 
-// entries of chunk c (entries first .. last-1) once its box admits q
+// entries of chunk c (entries first .. last-1) once its codes admit the
+// query (gw: the query's words in the frame of the chunk boxes)
 template <bool COUNT>
 __device__ __forceinline__ void scan_chunk(const DevView &m, float qx, float qy, float qz,
                                            uint32_t c, uint32_t first, uint32_t last, bool test,
-                                           Best &r, Work *wk) {
+                                           const uint32_t *gw, Best &r, Work *wk) {
   const uint4 cw = __ldg(&m.chunks[c]);
-  float clo[3], chi[3];
-  q_unpack(cw.x, cw.y, cw.z, m.qlo, m.qstep, clo, chi);
-  if (test && (qx < clo[0] || qy < clo[1] || qz < clo[2] || qx > chi[0] || qy > chi[1] ||
-               qz > chi[2]))
-    return;
-  const float cstep[3] = {q_step(clo[0], chi[0]), q_step(clo[1], chi[1]), q_step(clo[2], chi[2])};
+  if (test && !q_pass(gw, cw.x, cw.y, cw.z)) return;
+  // the chunk's entry frame: origin from its lower codes, scale inv * 2^e
+  float clo[3], cinv[3];
+  clo[0] = q_chunk_lo(cw.x & 0xffffu, m.qstep[0], m.qbase[0]);
+  clo[1] = q_chunk_lo(cw.x >> 16, m.qstep[1], m.qbase[1]);
+  clo[2] = q_chunk_lo(cw.y & 0xffffu, m.qstep[2], m.qbase[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cinv[d] = q_chunk_inv(m.qinv[d], cw.w, d);
+  uint32_t ew[3];
+  q_query_words(qx, qy, qz, clo, cinv, ew);
   if (COUNT) wk->entries += (int)(last - first);
-  for (uint32_t j = first; j < last; ++j) test_entry<COUNT>(m, qx, qy, qz, j, clo, cstep, r, wk);
+  for (uint32_t j = first; j < last; ++j) test_entry<COUNT>(m, qx, qy, qz, j, ew, r, wk);
 }
 
 // a3..a8 for a query whose nearest vertex is row v (r already holds v): the
 // list as a two-level R-tree (Sec. 4.6).  mode 2: super-chunk boxes, then
 // chunk boxes, then entry boxes; mode 1: chunk boxes, then entry boxes;
-// mode 0: every entry box.
+// mode 0: every entry box.  The three levels test the same query codes
+// against nested code boxes (an entry that admits q lies in a chunk and a
+// super-chunk that admit q), so every mode finds the same candidates.
 template <bool COUNT>
 __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, float qz, int v,
                                           int mode, Best &r, Work *wk) {
   const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
   const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
+  uint32_t gw[3];
+  q_query_words(qx, qy, qz, m.qlo, m.qinv, gw);
   if (mode == 2 && m.supers) {
     const uint32_t s0 = __ldg(&m.super_off[v]), s1 = __ldg(&m.super_off[v + 1]);
     for (uint32_t s = s0; s < s1; ++s) {
       if (COUNT) ++wk->chunks;
       const uint4 sw = __ldg(&m.supers[s]);
-      float slo[3], shi[3];
-      q_unpack(sw.x, sw.y, sw.z, m.qlo, m.qstep, slo, shi);
-      if (qx < slo[0] || qy < slo[1] || qz < slo[2] || qx > shi[0] || qy > shi[1] || qz > shi[2])
-        continue;
+      if (!q_pass(gw, sw.x, sw.y, sw.z)) continue;
       const uint32_t cb = c0 + 8 * (s - s0), ce = min(cb + 8u, c1);
       if (COUNT) wk->chunks += (int)(ce - cb);
       for (uint32_t c = cb; c < ce; ++c) {
         const uint32_t first = j0 + 8 * (c - c0);
-        scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), true, r, wk);
+        scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), true, gw, r, wk);
       }
     }
     return;
@@ -538,7 +541,7 @@ __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, 
   if (COUNT && mode == 1) wk->chunks += (int)(c1 - c0);
   for (uint32_t c = c0; c < c1; ++c) {
     const uint32_t first = j0 + 8 * (c - c0);
-    scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), mode != 0, r, wk);
+    scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), mode != 0, gw, r, wk);
   }
 }
 

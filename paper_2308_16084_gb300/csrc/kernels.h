@@ -12,7 +12,7 @@ struct DevView {
   const float4 *kd_nodes;   // (L-1) * 3: child boxes of every internal node
   const float4 *kd_points;  // nv: x, y, z, original vertex id bits
   const uint32_t *row_off;  // nv + 1
-  const uint4 *entries;     // per entry: typed id + 16-bit box in its chunk's box
+  const uint4 *entries;     // per entry: typed id + 15-bit box codes in its chunk's frame
   const float4 *edge_rec;   // 2 per edge
   const float4 *face_rec;   // 3 per face
   const int2 *edges;        // canonical edges
@@ -21,10 +21,11 @@ struct DevView {
   const uint32_t *nb;       // neighbour rows
   const float4 *nbp;        // neighbour positions, parallel to nb: x, y, z, row bits
   const uint32_t *chunk_off;  // nv + 1: chunks of each row (CSR)
-  const uint4 *chunks;        // per chunk: 16-bit box in the frame below
+  const uint4 *chunks;        // per chunk: box codes in the frame below + entry-frame exponents
   const uint32_t *super_off;  // nv + 1: super-chunks (8 chunks each) of each row
-  const uint4 *supers;        // per super-chunk: 16-bit box in the same frame
-  float qlo[3], qstep[3];     // frame of the chunk boxes (quant.h)
+  const uint4 *supers;        // per super-chunk: box codes in the same frame
+  float qlo[3], qinv[3];      // frame of the chunk boxes (quant.h)
+  float qstep[3], qbase[3];   // 1 / qinv and qlo - qstep (float ops, quant.h)
   const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre
   int grid_bits;              // G = 2^grid_bits cells per axis over D (0 = no grid)
   int64_t nv;

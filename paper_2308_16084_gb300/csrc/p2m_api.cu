@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -15,6 +16,7 @@
 
 #include "../../include/p2m.h"
 #include "builder.h"
+#include "quant.h"
 #include "kernels.h"
 #include "quant.h"
 
@@ -134,8 +136,9 @@ struct p2m_handle {
     view.supers = (const uint4 *)supers.p;
     for (int d = 0; d < 3; ++d) {
       view.qlo[d] = L.qframe_lo[d];
-      view.qstep[d] = L.qframe_step[d];
+      view.qinv[d] = L.qframe_inv[d];
     }
+    p2m::q_frame_derive(view.qlo, view.qinv, view.qstep, view.qbase);
     view.seed = seed.p;
     view.grid_bits = seed.p ? grid_bits : 0;
     view.nv = L.nv;
@@ -673,15 +676,21 @@ p2m_status p2m_get_list(const p2m_handle *h, int32_t vertex, int32_t *types, int
     if (types) types[j - b] = (int32_t)(w[0] >> 30);
     if (ids) ids[j - b] = (int32_t)(w[0] & 0x3fffffffu);
     if (boxes) {
-      // decode exactly as the query kernel does: chunk box, then entry box
+      // the set of points the query kernel admits: chunk frame from the
+      // chunk's codes, then the entry's codes in it (a hair wider, so that
+      // the float rounding of the code computation stays inside)
       const uint32_t *cw = &L.chunks[4 * (size_t)(L.chunk_off[row] + (j - b) / Layout::kChunk)];
-      float clo[3], chi[3], cstep[3], lo[3], hi[3];
-      p2m::q_unpack(cw[0], cw[1], cw[2], L.qframe_lo, L.qframe_step, clo, chi);
-      for (int d = 0; d < 3; ++d) cstep[d] = p2m::q_step(clo[d], chi[d]);
-      p2m::q_unpack(w[1], w[2], w[3], clo, cstep, lo, hi);
+      float step[3], base[3];
+      p2m::q_frame_derive(L.qframe_lo, L.qframe_inv, step, base);
+      uint32_t clc[3], chc[3], elc[3], ehc[3];
+      p2m::q_unwords(cw, clc, chc);
+      p2m::q_unwords(w + 1, elc, ehc);
       for (int d = 0; d < 3; ++d) {
-        boxes[6 * (j - b) + d] = lo[d];
-        boxes[6 * (j - b) + 3 + d] = hi[d];
+        const double lo = p2m::q_chunk_lo(clc[d], step[d], base[d]);
+        const double inv = p2m::q_chunk_inv(L.qframe_inv[d], cw[3], d);
+        boxes[6 * (j - b) + d] = elc[d] == 0 ? -INFINITY : (float)(lo + (elc[d] - 1.01) / inv);
+        boxes[6 * (j - b) + 3 + d] =
+            ehc[d] == p2m::kQMax ? INFINITY : (float)(lo + (ehc[d] + 0.01) / inv);
       }
     }
   }
@@ -942,7 +951,7 @@ done:
 
 namespace {
 constexpr uint64_t kMagic = 0x314d5032474d5032ull;  // "2PMG2PM1"
-constexpr uint32_t kVersion = 6;
+constexpr uint32_t kVersion = 7;
 
 uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = (const unsigned char *)p;
@@ -988,7 +997,7 @@ p2m_status p2m_save(const p2m_handle *h, const char *path) {
   fl[6] = L.delta;
   std::memcpy(fl + 7, L.kd_root, 24);
   std::memcpy(fl + 13, L.qframe_lo, 12);
-  std::memcpy(fl + 16, L.qframe_step, 12);
+  std::memcpy(fl + 16, L.qframe_inv, 12);
   bool ok = fwrite(&kMagic, 8, 1, f) == 1 && fwrite(&kVersion, 4, 1, f) == 1 &&
             fwrite(scal, 8, 12, f) == 12 && fwrite(fl, 4, 19, f) == 19;
   ck = fnv1a(ck, scal, sizeof(scal));
@@ -1049,7 +1058,7 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
   L.delta = fl[6];
   std::memcpy(L.kd_root, fl + 7, 24);
   std::memcpy(L.qframe_lo, fl + 13, 12);
-  std::memcpy(L.qframe_step, fl + 16, 12);
+  std::memcpy(L.qframe_inv, fl + 16, 12);
   if ((int64_t)L.row_off.size() != L.nv + 1 || (int64_t)L.kd_points.size() != 4 * L.nv ||
       (int64_t)L.entries.size() != 4 * L.n_entries || (int64_t)L.edges.size() != 2 * L.ne ||
       (int64_t)L.nb_off.size() != L.nv + 1 || (int64_t)L.nb.size() != (int64_t)L.nb_off.back() ||

@@ -79,6 +79,11 @@ def test_builder_tables_equal_oracle_tables(pg, idx, kw):
         hb = b[order_a].astype(np.float64)
         tol = 1e-2 * delta
         assert (hb[:, :3] <= ob[:, :3] + tol).all() and (hb[:, 3:] >= ob[:, 3:] - tol).all()
+        # and the integer box codes stay tight: a few codes of the chunk's
+        # frame (at most 2^-12 of the domain) beyond the FP64 box
+        slack = 2.0 ** -12 * (np.asarray(h.domain()[1]) - np.asarray(h.domain()[0]))
+        assert (hb[:, :3] >= ob[:, :3] - slack - tol).all()
+        assert (hb[:, 3:] <= ob[:, 3:] + slack + tol).all()
 
 
 def test_builder_thread_count_does_not_change_tables(pg):
