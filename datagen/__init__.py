@@ -339,6 +339,53 @@ def workload(index: int, n_queries: int | None = None, level: int | None = None,
     raise ValueError("workload 4 is a batch: use batch_workload()")
 
 
+def _soup_streams(n: int):
+    # children 5 and 6 of the root sequence: apart from the five workloads'
+    child = np.random.SeedSequence(ROOT_SEED).spawn(7)[5]
+    return [np.random.default_rng(s) for s in child.spawn(n)]
+
+
+def triangle_soup(kind: str, level: int, rng):
+    """The three versions of a closed surface the paper's soup test uses
+    (Sec. 5, triangle soups): 'watertight' (a noisy icosphere), 'gapped'
+    (every face with its own three vertices, shrunk to 80 % about its
+    centroid, so no two faces touch) and 'penetrating' (own vertices, grown
+    to 160 % and turned by up to 30 degrees about a random axis through the
+    centroid, so neighbouring faces cut through each other)."""
+    v, f = noisy_icosphere(level, 0.05, rng)
+    if kind == "watertight":
+        return v, f
+    tri = v[f]                                   # (F, 3, 3)
+    c = tri.mean(1, keepdims=True)
+    if kind == "gapped":
+        tri = c + 0.8 * (tri - c)
+    elif kind == "penetrating":
+        axis = rng.normal(size=(f.shape[0], 3))
+        axis /= np.linalg.norm(axis, axis=1, keepdims=True)
+        ang = rng.uniform(-math.pi / 6, math.pi / 6, size=f.shape[0])
+        k = axis[:, None, :]
+        p = 1.6 * (tri - c)
+        cos, sin = np.cos(ang)[:, None, None], np.sin(ang)[:, None, None]
+        # Rodrigues' rotation of every corner about the face's axis
+        p = p * cos + np.cross(k, p) * sin + k * (p * k).sum(-1, keepdims=True) * (1 - cos)
+        tri = c + p
+    else:
+        raise ValueError(kind)
+    return tri.reshape(-1, 3), np.arange(3 * f.shape[0]).reshape(-1, 3)
+
+
+def soup_workload(kind: str, level: int = 5, n_queries: int = 1_000_000):
+    """Triangle-soup workload: level 5 gives 20,480 faces (the size of the
+    paper's Bear model); half the queries uniform in the bbox scaled 1.2x,
+    half within 0.01 x bbox diagonal of the surface."""
+    rm, rq = _soup_streams(2)
+    v, f = triangle_soup(kind, level, rm)
+    nu = n_queries // 2
+    q = np.concatenate([uniform_in_box(v, 1.2, nu, rq),
+                        near_surface(v, f, n_queries - nu, 0.01 * bbox_diagonal(v), rq)], 0)
+    return _finish(f"soup-{kind}-L{level}", v, f, q, 1.25, 0.02, meta={"kind": kind})
+
+
 def batch_workload(n_meshes: int = 64, tri_range=(1e3, 5e5), query_range=(1e4, 2e6),
                    query_scale: float = 1.0):
     """64 meshes of uneven size: a coin picks a noisy icosphere (level

@@ -54,7 +54,17 @@ def _host(pg, m, **kw):
 @pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 4}), (2, {"grid": 40}),
                                     (3, {"level": 4})])
 def test_builder_tables_equal_oracle_tables(pg, idx, kw):
-    m = dg.workload(idx, n_queries=10, **kw)
+    _check_tables(pg, dg.workload(idx, n_queries=10, **kw))
+
+
+@pytest.mark.parametrize("kind", ["gapped", "penetrating"])
+def test_builder_tables_equal_oracle_tables_on_soups(pg, kind):
+    """Triangle soups: every face with its own vertices, apart or cutting
+    through each other (all edges are boundary edges)."""
+    _check_tables(pg, dg.soup_workload(kind, level=2, n_queries=10))
+
+
+def _check_tables(pg, m):
     h = _host(pg, m)
     o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
     np.testing.assert_array_equal(h.edges(), o.edges())

@@ -63,6 +63,27 @@ def test_parity_workloads(pg, idx, kw, n, mode):
     np.testing.assert_array_equal((gpu["status"] & 1) == 1, outside)
 
 
+@pytest.mark.parametrize("kind", ["watertight", "gapped", "penetrating"])
+def test_parity_triangle_soups(pg, kind):
+    """The paper's soup test (Sec. 5): the same surface watertight, as a soup
+    of faces apart from each other, and as a soup of faces that cut through
+    each other.  Every R-tree mode and both query orders agree bit for bit."""
+    m = dg.soup_workload(kind, level=3, n_queries=20001)
+    mesh = build(pg, m)
+    o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
+    ref = o.bruteforce(m.queries)
+    gpu = run(mesh, m.queries)
+    s = pu.check(m.verts, o.edges(), m.tris, m.queries, gpu, ref, pu.tolerance(m.verts),
+                 m.name)
+    assert s["prim_exact"] > 0.98
+    for mode in ({"chunked": 0, "group_by_vertex": 0}, {"chunked": 1, "group_by_vertex": 1},
+                 {"chunked": 2, "group_by_vertex": 0, "nn_walk": 0}):
+        mesh.tuning = mode
+        got = run(mesh, m.queries)
+        for k in ("dist", "closest", "prim_id", "prim_type", "status"):
+            np.testing.assert_array_equal(got[k], gpu[k])
+
+
 def test_parity_against_paper_method(pg):
     """The GPU agrees with the oracle's own P2M query (Alg. A.2) too, and the
     product builder's interception lists equal the oracle's."""
