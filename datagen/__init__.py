@@ -386,6 +386,46 @@ def soup_workload(kind: str, level: int = 5, n_queries: int = 1_000_000):
     return _finish(f"soup-{kind}-L{level}", v, f, q, 1.25, 0.02, meta={"kind": kind})
 
 
+def unique_edges(f):
+    """Sorted unique (min, max) vertex pairs of the sides of triangles f."""
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]], 0)
+    return np.unique(np.sort(e, axis=1), axis=0)
+
+
+def points_on_segments(v, s, n, radius, rng):
+    """Uniform point of a length-weighted random segment plus a uniform
+    offset in the ball of the given radius."""
+    a, b = v[s[:, 0]], v[s[:, 1]]
+    w = np.linalg.norm(b - a, axis=1)
+    k = rng.choice(s.shape[0], size=n, p=w / w.sum())
+    t = rng.uniform(size=(n, 1))
+    p = a[k] + t * (b[k] - a[k])
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return p + d * (radius * rng.uniform(size=n) ** (1.0 / 3.0))[:, None]
+
+
+def mixed_workload(mesh_level: int = 6, wire_level: int = 4, n_queries: int = 1_000_000):
+    """Mixed segments and triangles (Sec. 5, mixed primitives): a noisy
+    icosphere (the triangle mesh) beside the wireframe of a displaced one
+    (segments only, no faces), as the paper combines a triangle mesh with
+    another model's wireframe.  Half the queries uniform in the bbox scaled
+    1.2x, a quarter near each part.  Returns the Mesh (tris = the triangles)
+    and the segments as meta['segs'] (indices into verts)."""
+    rm, rq = _soup_streams(2)[::-1]
+    v1, f1 = noisy_icosphere(mesh_level, 0.05, rm)
+    v2, f2 = displaced_icosphere(wire_level, 0.2, rm)
+    v2 = 0.8 * v2 + np.array([2.2, 0.0, 0.0])
+    segs = unique_edges(f2) + v1.shape[0]
+    v = np.concatenate([v1, v2], 0)
+    nu, nm = n_queries // 2, n_queries // 4
+    q = np.concatenate([uniform_in_box(v, 1.2, nu, rq),
+                        near_surface(v1, f1, nm, 0.02, rq),
+                        points_on_segments(v, segs, n_queries - nu - nm, 0.02, rq)], 0)
+    return _finish(f"mixed-L{mesh_level}-wire-L{wire_level}", v, f1, q, 1.25, 0.02,
+                   meta={"segs": np.ascontiguousarray(segs, np.int32)})
+
+
 def batch_workload(n_meshes: int = 64, tri_range=(1e3, 5e5), query_range=(1e4, 2e6),
                    query_scale: float = 1.0):
     """64 meshes of uneven size: a coin picks a noisy icosphere (level

@@ -32,7 +32,7 @@ _lib = None
 VERTEX, EDGE, FACE = 0, 1, 2
 STATUS = {0: "ok", 1: "bad argument", 2: "index out of range", 3: "repeated index",
           4: "duplicate vertex", 5: "unreferenced vertex", 6: "non-finite coordinate",
-          7: "out of memory", 8: "no triangles"}
+          7: "out of memory", 8: "no triangles or segments"}
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +61,10 @@ def _load():
             lib.orc_create.restype = P
             lib.orc_create.argtypes = [P, i64, P, i64, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
+            lib.orc_create_mixed.restype = P
+            lib.orc_create_mixed.argtypes = [P, i64, P, i64, P, i64, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, P]
             lib.orc_destroy.argtypes = [P]
             lib.orc_info.argtypes = [P, P, P]
             lib.orc_edges.argtypes = [P, P]
@@ -96,16 +100,18 @@ class OracleMesh:
     kept as it is, for finite-difference tests)."""
 
     def __init__(self, verts, tris, domain_scale=10.0, domain_margin=0.0,
-                 delta_rel=4e-6, build_tables=True, threads=None):
+                 delta_rel=4e-6, build_tables=True, threads=None, segs=None):
         self._lib = _load()
         self.V = self._widen(verts)
-        self.F = np.ascontiguousarray(np.asarray(tris, np.int32))
+        self.F = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
+        self.S = np.ascontiguousarray(
+            np.zeros((0, 2), np.int32) if segs is None else np.asarray(segs, np.int32).reshape(-1, 2))
         self.threads = default_threads() if threads is None else int(threads)
         st = ctypes.c_int(0)
-        self._h = self._lib.orc_create(_p(self.V), self.V.shape[0], _p(self.F), self.F.shape[0],
-                                       float(domain_scale), float(domain_margin),
-                                       float(delta_rel), int(bool(build_tables)),
-                                       self.threads, ctypes.byref(st))
+        self._h = self._lib.orc_create_mixed(
+            _p(self.V), self.V.shape[0], _p(self.F), self.F.shape[0], _p(self.S),
+            self.S.shape[0], float(domain_scale), float(domain_margin), float(delta_rel),
+            int(bool(build_tables)), self.threads, ctypes.byref(st))
         self.status = st.value
         if not self._h:
             raise ValueError(f"oracle: invalid mesh ({STATUS.get(st.value, st.value)})")

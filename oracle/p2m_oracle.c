@@ -323,12 +323,13 @@ typedef struct {
 } orc_rec;
 
 struct orc_mesh {
-  int64_t nv, nf, ne;
+  int64_t nv, nf, ne, ns;
   double *V;
   int32_t *F;
+  int32_t *S;        /* ns*2 segments (edges of no face), may be NULL */
   int32_t *E;        /* ne*2 canonical edges */
   int32_t *fe;       /* nf*3 edge id of (F[k], F[k+1]) */
-  int64_t *efo;      /* edge -> faces CSR */
+  int64_t *efo;      /* edge -> faces CSR (a segment entry holds -1) */
   int32_t *ef;
   uint8_t *fdeg;     /* 1 = zero-area face (excluded from F, edges kept) */
   int64_t ndeg;
@@ -375,9 +376,11 @@ static int cmp_vpos(const void *x, const void *y, void *ctx) {
   return i < j ? -1 : (i > j);
 }
 
+/* The edges are the unique (min, max) vertex pairs of the faces' sides and
+ * of the segments; a segment that repeats a face side is that edge. */
 static int build_topology(orc_mesh *m) {
-  int64_t nf = m->nf;
-  half_t *h = (half_t *)malloc(sizeof(half_t) * 3 * nf);
+  int64_t nf = m->nf, nh = 3 * m->nf + m->ns;
+  half_t *h = (half_t *)malloc(sizeof(half_t) * (nh > 0 ? nh : 1));
   if (!h) return ORC_NOMEM;
   for (int64_t f = 0; f < nf; ++f)
     for (int k = 0; k < 3; ++k) {
@@ -388,30 +391,38 @@ static int build_topology(orc_mesh *m) {
       e->f = (int32_t)f;
       e->k = k;
     }
-  qsort(h, 3 * nf, sizeof(half_t), cmp_half);
+  for (int64_t s = 0; s < m->ns; ++s) {
+    int32_t u = m->S[2 * s], w = m->S[2 * s + 1];
+    half_t *e = h + 3 * nf + s;
+    e->a = u < w ? u : w;
+    e->b = u < w ? w : u;
+    e->f = -1;
+    e->k = 0;
+  }
+  qsort(h, nh, sizeof(half_t), cmp_half);
   int64_t ne = 0;
-  for (int64_t i = 0; i < 3 * nf; ++i)
+  for (int64_t i = 0; i < nh; ++i)
     if (i == 0 || h[i].a != h[i - 1].a || h[i].b != h[i - 1].b) ++ne;
   m->ne = ne;
-  m->E = (int32_t *)malloc(sizeof(int32_t) * 2 * ne);
-  m->fe = (int32_t *)malloc(sizeof(int32_t) * 3 * nf);
+  m->E = (int32_t *)malloc(sizeof(int32_t) * 2 * (ne > 0 ? ne : 1));
+  m->fe = (int32_t *)malloc(sizeof(int32_t) * 3 * (nf > 0 ? nf : 1));
   m->efo = (int64_t *)calloc(ne + 1, sizeof(int64_t));
-  m->ef = (int32_t *)malloc(sizeof(int32_t) * 3 * nf);
+  m->ef = (int32_t *)malloc(sizeof(int32_t) * (nh > 0 ? nh : 1));
   if (!m->E || !m->fe || !m->efo || !m->ef) { free(h); return ORC_NOMEM; }
   int64_t e = -1;
-  for (int64_t i = 0; i < 3 * nf; ++i) {
+  for (int64_t i = 0; i < nh; ++i) {
     if (i == 0 || h[i].a != h[i - 1].a || h[i].b != h[i - 1].b) {
       ++e;
       m->E[2 * e] = h[i].a;
       m->E[2 * e + 1] = h[i].b;
     }
-    m->fe[3 * h[i].f + h[i].k] = (int32_t)e;
+    if (h[i].f >= 0) m->fe[3 * h[i].f + h[i].k] = (int32_t)e;
     m->ef[i] = h[i].f;
     m->efo[e + 1] = i + 1;
   }
   free(h);
   /* zero-area faces */
-  m->fdeg = (uint8_t *)calloc(nf, 1);
+  m->fdeg = (uint8_t *)calloc(nf > 0 ? nf : 1, 1);
   m->ndeg = 0;
   for (int64_t f = 0; f < nf; ++f) {
     const double *a = m->V + 3 * m->F[3 * f], *b = m->V + 3 * m->F[3 * f + 1],
@@ -426,8 +437,9 @@ static int build_topology(orc_mesh *m) {
   return ORC_OK;
 }
 
-static int validate(const double *V, int64_t nv, const int32_t *F, int64_t nf) {
-  if (nf <= 0) return ORC_EMPTY;
+static int validate(const double *V, int64_t nv, const int32_t *F, int64_t nf,
+                    const int32_t *S, int64_t ns) {
+  if (nf < 0 || ns < 0 || nf + ns <= 0) return ORC_EMPTY;
   for (int64_t i = 0; i < 3 * nv; ++i)
     if (!isfinite(V[i])) return ORC_NONFINITE;
   uint8_t *used = (uint8_t *)calloc(nv > 0 ? nv : 1, 1);
@@ -437,6 +449,12 @@ static int validate(const double *V, int64_t nv, const int32_t *F, int64_t nf) {
     if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) { free(used); return ORC_BAD_INDEX; }
     if (a == b || b == c || a == c) { free(used); return ORC_REPEATED_INDEX; }
     used[a] = used[b] = used[c] = 1;
+  }
+  for (int64_t s = 0; s < ns; ++s) {
+    int32_t a = S[2 * s], b = S[2 * s + 1];
+    if (a < 0 || b < 0 || a >= nv || b >= nv) { free(used); return ORC_BAD_INDEX; }
+    if (a == b) { free(used); return ORC_REPEATED_INDEX; }
+    used[a] = used[b] = 1;
   }
   for (int64_t i = 0; i < nv; ++i)
     if (!used[i]) { free(used); return ORC_UNREFERENCED; }
@@ -854,7 +872,7 @@ static int perp_planes(const orc_mesh *m, int32_t type, int64_t id, double *pl, 
   k = 2;
   for (int64_t j = m->efo[id]; j < m->efo[id + 1] && k < cap; ++j) {
     int64_t f = m->ef[j];
-    if (m->fdeg[f]) continue;
+    if (f < 0 || m->fdeg[f]) continue;  /* a segment side adds no half-space */
     int le = -1;
     for (int s = 0; s < 3; ++s) if (m->fe[3 * f + s] == id) le = s;
     double mm[3];
@@ -1088,15 +1106,27 @@ static int cmp_rec_in_row(const void *x, const void *y) {
 orc_mesh *orc_create(const double *V, int64_t nv, const int32_t *F, int64_t nf,
                      double domain_scale, double domain_margin, double delta_rel,
                      int build_tables, int n_threads, int *status) {
-  int st = (!V || !F || nv <= 0) ? ORC_BAD_ARG : validate(V, nv, F, nf);
+  return orc_create_mixed(V, nv, F, nf, NULL, 0, domain_scale, domain_margin, delta_rel,
+                          build_tables, n_threads, status);
+}
+
+orc_mesh *orc_create_mixed(const double *V, int64_t nv, const int32_t *F, int64_t nf,
+                           const int32_t *S, int64_t ns, double domain_scale,
+                           double domain_margin, double delta_rel, int build_tables,
+                           int n_threads, int *status) {
+  int st = (!V || nv <= 0 || (nf > 0 && !F) || (ns > 0 && !S)) ? ORC_BAD_ARG
+                                                                 : validate(V, nv, F, nf, S, ns);
   if (st) { if (status) *status = st; return NULL; }
   orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
   m->nv = nv;
   m->nf = nf;
+  m->ns = ns;
   m->V = (double *)malloc(sizeof(double) * 3 * nv);
-  m->F = (int32_t *)malloc(sizeof(int32_t) * 3 * nf);
+  m->F = (int32_t *)malloc(sizeof(int32_t) * 3 * (nf > 0 ? nf : 1));
+  m->S = (int32_t *)malloc(sizeof(int32_t) * 2 * (ns > 0 ? ns : 1));
   memcpy(m->V, V, sizeof(double) * 3 * nv);
-  memcpy(m->F, F, sizeof(int32_t) * 3 * nf);
+  if (nf > 0) memcpy(m->F, F, sizeof(int32_t) * 3 * nf);
+  if (ns > 0) memcpy(m->S, S, sizeof(int32_t) * 2 * ns);
   if (n_threads < 1) n_threads = 1;
 
   double t0 = now_ms();
@@ -1219,7 +1249,7 @@ void orc_destroy(orc_mesh *m) {
     for (int64_t i = 0; i < m->nv; ++i) poly_free(&m->cell[i]);
     free(m->cell);
   }
-  free(m->V); free(m->F); free(m->E); free(m->fe); free(m->efo); free(m->ef); free(m->fdeg);
+  free(m->V); free(m->F); free(m->S); free(m->E); free(m->fe); free(m->efo); free(m->ef); free(m->fdeg);
   free(m->kpt); free(m->klo); free(m->khi); free(m->kax); free(m->kbox);
   free(m->cvol); free(m->nbo); free(m->nb);
   free(m->to); free(m->tt); free(m->ti); free(m->tb);

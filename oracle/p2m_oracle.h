@@ -34,13 +34,13 @@ extern "C" {
 enum {
   ORC_OK = 0,
   ORC_BAD_ARG = 1,
-  ORC_BAD_INDEX = 2,        /* triangle index out of range              */
-  ORC_REPEATED_INDEX = 3,   /* a triangle names one vertex twice        */
+  ORC_BAD_INDEX = 2,        /* vertex index out of range                */
+  ORC_REPEATED_INDEX = 3,   /* a triangle or segment names a vertex twice */
   ORC_DUPLICATE_VERTEX = 4, /* two vertices share a position            */
-  ORC_UNREFERENCED = 5,     /* a vertex used by no triangle             */
+  ORC_UNREFERENCED = 5,     /* a vertex used by no triangle or segment  */
   ORC_NONFINITE = 6,        /* NaN / inf coordinate                      */
   ORC_NOMEM = 7,
-  ORC_EMPTY = 8             /* no triangles                              */
+  ORC_EMPTY = 8             /* no triangles and no segments              */
 };
 
 /* primitive types, ordered for tie breaks: vertex < edge < face */
@@ -57,6 +57,15 @@ typedef struct orc_mesh orc_mesh;
 orc_mesh *orc_create(const double *V, int64_t nv, const int32_t *F, int64_t nf,
                      double domain_scale, double domain_margin, double delta_rel,
                      int build_tables, int n_threads, int *status);
+/* Mixed primitives (Sec. 5, mixed segments and triangles): S holds ns
+ * segments (vertex index pairs) that are edges of no face; the segments'
+ * Space-perp is the slab between their endpoint planes (reading of Eq. 5
+ * with no adjacent face).  nf may be 0 (a wireframe).  orc_create is this
+ * with ns = 0. */
+orc_mesh *orc_create_mixed(const double *V, int64_t nv, const int32_t *F, int64_t nf,
+                           const int32_t *S, int64_t ns, double domain_scale,
+                           double domain_margin, double delta_rel, int build_tables,
+                           int n_threads, int *status);
 void orc_destroy(orc_mesh *m);
 
 /* info[0..15]: nv, nf, ne, n_table_entries, n_degenerate_faces,

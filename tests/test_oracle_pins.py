@@ -478,6 +478,101 @@ def test_invalid_meshes_rejected(case, msg):
 
 
 # --------------------------------------------------------------------------
+# mixed segments and triangles (Sec. 5): segments are edges of no face
+# --------------------------------------------------------------------------
+
+def test_segment_closed_forms():
+    """A lone segment from (0,0,0) to (2,0,0): distances by hand."""
+    V = np.array([[0, 0, 0], [2, 0, 0]], np.float32)
+    # margin 2 x the bbox diagonal: every query below lies inside D
+    o = oracle.OracleMesh(V, np.zeros((0, 3), np.int32), 4.0, 2.0, segs=[[0, 1]])
+    assert (np.abs(o.domain_lo) >= 3).all() and (o.domain_hi >= 3).all()
+    assert (o.nf, o.ne) == (0, 1)
+    q = np.array([[1, 3, 0], [3, 1, 0], [-1, 0, 0], [0.5, 0, -2]], np.float32)
+    want_d = [3.0, np.sqrt(2.0), 1.0, 2.0]
+    want_t = [oracle.EDGE, oracle.VERTEX, oracle.VERTEX, oracle.EDGE]
+    want_i = [0, 1, 0, 0]
+    want_c = [[1, 0, 0], [2, 0, 0], [0, 0, 0], [0.5, 0, 0]]
+    for r in (o.bruteforce(q), o.query(q, use_boxes=True)):
+        np.testing.assert_allclose(r["dist"], want_d, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(r["ptype"], want_t)
+        np.testing.assert_array_equal(r["pid"], want_i)
+        np.testing.assert_allclose(r["cp"], want_c, rtol=0, atol=1e-12)
+
+
+def test_mixed_triangle_and_segment_closed_form():
+    """Triangle (0,0,0),(1,0,0),(0,1,0) under the segment (0,0,2)-(1,1,2):
+    edge ids follow the canonical order, so the segment is edge 3."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 2], [1, 1, 2]], np.float32)
+    o = oracle.OracleMesh(V, [[0, 1, 2]], 4.0, 0.5, segs=[[3, 4]])
+    np.testing.assert_array_equal(o.edges(), [[0, 1], [0, 2], [1, 2], [3, 4]])
+    q = np.array([[0.25, 0.25, 1.2], [0.25, 0.25, 0.5], [2, 2, 2]], np.float32)
+    qd = q.astype(np.float64)
+    want_d = [2 - qd[0, 2], qd[1, 2], np.sqrt(2.0)]
+    for r in (o.bruteforce(q), o.query(q, use_boxes=True)):
+        np.testing.assert_allclose(r["dist"], want_d, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(r["ptype"], [oracle.EDGE, oracle.FACE, oracle.VERTEX])
+        np.testing.assert_array_equal(r["pid"], [3, 0, 4])
+        np.testing.assert_allclose(r["cp"], [[qd[0, 0], qd[0, 1], 2], [qd[1, 0], qd[1, 1], 0],
+                                             [1, 1, 2]], rtol=0, atol=1e-12)
+
+
+def test_segment_on_a_face_side_is_that_edge():
+    V, F = dg.octahedron()
+    V = V.astype(np.float32)
+    o1 = oracle.OracleMesh(V, F, build_tables=False)
+    o2 = oracle.OracleMesh(V, F, segs=[list(F[0, :2])], build_tables=False)
+    assert o2.ne == o1.ne
+    q = rng(11).uniform(-2, 2, size=(2000, 3))
+    a, b = o1.bruteforce(q), o2.bruteforce(q)
+    for k in ("dist", "ptype", "pid"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_mixed_tables_and_query():
+    """Mesh + wireframe: the P2M query equals the plain definition, every
+    vertex intercepts its incident segments (Thm. 2), and sampled points
+    find their closest primitive in the list of their nearest vertex."""
+    m = dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=20000)
+    S = m.meta["segs"]
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin, segs=S)
+    bf = o.bruteforce(m.queries)
+    assert (bf["ptype"] == oracle.EDGE).sum() > 1000
+    for ub in (False, True):
+        r = o.query(m.queries, use_boxes=ub)
+        np.testing.assert_array_equal(r["dist"], bf["dist"])
+        np.testing.assert_array_equal(r["pid"], bf["pid"])
+    T = _table_set(o)
+    E = {tuple(e): k for k, e in enumerate(o.edges().tolist())}
+    for a, b in S.tolist():
+        e = E[(min(a, b), max(a, b))]
+        assert (a, oracle.EDGE, e) in T and (b, oracle.EDGE, e) in T
+    q = rng(12).uniform(o.domain_lo, o.domain_hi, size=(20000, 3))
+    r = o.bruteforce(q)
+    nn = brute_nn(m.verts, q)
+    for i in range(q.shape[0]):
+        t, pid = int(r["ptype"][i]), int(r["pid"][i])
+        if t != oracle.VERTEX:
+            b = T[(int(nn[i]), t, pid)]
+            assert (q[i] >= b[:3]).all() and (q[i] <= b[3:]).all()
+
+
+@pytest.mark.parametrize("segs,msg", [([[0, 0]], "repeated index"),
+                                      ([[0, 99]], "index out of range")])
+def test_invalid_segments_rejected(segs, msg):
+    V, F = dg.octahedron()
+    with pytest.raises(ValueError, match=msg):
+        oracle.OracleMesh(V.astype(np.float32), F, segs=segs)
+
+
+def test_vertex_used_only_by_a_segment_is_referenced():
+    V, F = dg.octahedron()
+    V = np.concatenate([V, [[3, 0, 0]]]).astype(np.float32)
+    o = oracle.OracleMesh(V, F, segs=[[0, 6]], build_tables=False)
+    assert o.ne == 13
+
+
+# --------------------------------------------------------------------------
 # statistics the paper reports as ranges (sanity only; parity unpinned:
 # the paper's models are not available)
 # --------------------------------------------------------------------------
