@@ -94,6 +94,19 @@ typedef struct p2m_handle p2m_handle;
  */
 p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out);
 
+/*
+ * Mixed primitives (Sec. 5, mixed segments and triangles): p2m_build with,
+ * besides the mesh's triangles (n_tris may be 0, tris then NULL), n_segs
+ * segments `segs` (2 vertex indices each, host memory) that are edges of no
+ * face, e.g. a wireframe beside a surface.  Segments join the canonical edge
+ * list (a segment that repeats a face side is that edge) and are reported
+ * as P2M_PRIM_EDGE; the Space-perp of a segment is the slab between the
+ * planes through its endpoints.  Every vertex must be used by a triangle or
+ * a segment.  Errors as p2m_build.
+ */
+p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_segs,
+                           const p2m_build_opts *opts, p2m_handle **out);
+
 /* Release the handle and all device memory it owns (NULL is a no-op). */
 void p2m_destroy(p2m_handle *h);
 

@@ -70,20 +70,28 @@ class P2M:
     preprocessing (Alg. A.1) through ``p2m_build``.  ``verts`` (V,3) float32
     and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors."""
 
-    def __init__(self, verts=None, tris=None, *, domain_scale=10.0, domain_margin=0.0,
-                 delta_rel=4e-6, host_threads=0, device_assist=True, leaf_size=8, _handle=None):
+    def __init__(self, verts=None, tris=None, *, segs=None, domain_scale=10.0,
+                 domain_margin=0.0, delta_rel=4e-6, host_threads=0, device_assist=True,
+                 leaf_size=8, _handle=None):
         self._h = None
         if _handle is not None:
             self._h = _handle
         else:
             V = np.ascontiguousarray(np.asarray(verts, dtype=np.float32).reshape(-1, 3))
-            F = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+            F = np.ascontiguousarray(np.asarray(
+                np.zeros((0, 3)) if tris is None else tris, dtype=np.int32).reshape(-1, 3))
             desc = MeshDesc(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
             opts = BuildOpts(domain_scale, domain_margin, delta_rel, host_threads,
                              int(bool(device_assist)), leaf_size)
             h = ctypes.c_void_p()
-            check(lib.p2m_build(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
-                  "p2m_build")
+            if segs is None:
+                check(lib.p2m_build(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
+                      "p2m_build")
+            else:
+                S = np.ascontiguousarray(np.asarray(segs, dtype=np.int32).reshape(-1, 2))
+                check(lib.p2m_build_mixed(ctypes.byref(desc), S.ctypes.data, S.shape[0],
+                                          ctypes.byref(opts), ctypes.byref(h)),
+                      "p2m_build_mixed")
             self._h = h
         st = self.stats()
         self.n_verts, self.n_tris, self.n_edges = st["n_verts"], st["n_tris"], st["n_edges"]

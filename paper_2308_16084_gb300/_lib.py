@@ -38,6 +38,7 @@ _INT = ctypes.c_int
 _SIGS = {
     "p2m_default_opts": (None, [_P]),
     "p2m_build": (_INT, [_P, _P, _P]),
+    "p2m_build_mixed": (_INT, [_P, _P, _I64, _P, _P]),
     "p2m_destroy": (None, [_P]),
     "p2m_query": (_INT, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P]),
     "p2m_query_host": (_INT, [_P, _P, _I64, _P, _P, _P, _P, _P]),

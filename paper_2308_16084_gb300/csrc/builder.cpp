@@ -257,9 +257,10 @@ struct Mesh {
   std::vector<uint8_t> degenerate;
 };
 
-int validate(const float *V, int64_t nv, const int32_t *F, int64_t nf, std::string &err) {
-  if (nf <= 0 || nv < 3) {
-    err = "mesh has no triangles";
+int validate(const float *V, int64_t nv, const int32_t *F, int64_t nf, const int32_t *S,
+             int64_t ns, std::string &err) {
+  if (nf < 0 || ns < 0 || nf + ns <= 0 || nv < 2) {
+    err = "mesh has no triangles and no segments";
     return 2;
   }
   for (int64_t i = 0; i < 3 * nv; ++i)
@@ -280,9 +281,21 @@ int validate(const float *V, int64_t nv, const int32_t *F, int64_t nf, std::stri
     }
     used[a] = used[b] = used[c] = 1;
   }
+  for (int64_t s = 0; s < ns; ++s) {
+    int32_t a = S[2 * s], b = S[2 * s + 1];
+    if (a < 0 || b < 0 || a >= nv || b >= nv) {
+      err = "segment index out of range";
+      return 2;
+    }
+    if (a == b) {
+      err = "segment repeats a vertex";
+      return 2;
+    }
+    used[a] = used[b] = 1;
+  }
   for (int64_t i = 0; i < nv; ++i)
     if (!used[i]) {
-      err = "vertex referenced by no triangle";
+      err = "vertex referenced by no triangle or segment";
       return 2;
     }
   std::vector<int32_t> ord(nv);
@@ -301,32 +314,39 @@ int validate(const float *V, int64_t nv, const int32_t *F, int64_t nf, std::stri
   return 0;
 }
 
-void build_topology(Mesh &M) {
+// Edges: the unique (min, max) vertex pairs of the face sides and of the
+// segments (Sec. 5, mixed primitives); a segment that repeats a face side
+// is that edge.  Segment sides enter the edge -> faces lists as face -1.
+void build_topology(Mesh &M, const int32_t *S, int64_t ns) {
   struct HalfEdge {
     int64_t key;  // min << 32 | max
     int32_t face;
     int32_t k;
   };
-  std::vector<HalfEdge> h(3 * M.nf);
+  std::vector<HalfEdge> h(3 * M.nf + ns);
   for (int64_t f = 0; f < M.nf; ++f)
     for (int k = 0; k < 3; ++k) {
       int64_t u = M.F[3 * f + k], w = M.F[3 * f + (k + 1) % 3];
       h[3 * f + k] = {std::min(u, w) << 32 | std::max(u, w), (int32_t)f, k};
     }
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t u = S[2 * s], w = S[2 * s + 1];
+    h[3 * M.nf + s] = {std::min(u, w) << 32 | std::max(u, w), -1, 0};
+  }
   std::sort(h.begin(), h.end(), [](const HalfEdge &a, const HalfEdge &b) {
     return a.key < b.key || (a.key == b.key && a.face < b.face);
   });
   M.fedge.assign(3 * M.nf, -1);
   M.E.clear();
   M.ef_off.assign(1, 0);
-  M.ef.resize(3 * M.nf);
+  M.ef.resize(h.size());
   for (size_t i = 0; i < h.size(); ++i) {
     if (i == 0 || h[i].key != h[i - 1].key) {
       M.E.push_back((int32_t)(h[i].key >> 32));
       M.E.push_back((int32_t)(h[i].key & 0xffffffff));
       M.ef_off.push_back(M.ef_off.back());
     }
-    M.fedge[3 * h[i].face + h[i].k] = (int32_t)(M.E.size() / 2 - 1);
+    if (h[i].face >= 0) M.fedge[3 * h[i].face + h[i].k] = (int32_t)(M.E.size() / 2 - 1);
     M.ef[i] = h[i].face;
     M.ef_off.back()++;
   }
@@ -531,11 +551,12 @@ struct PrimGeom {  // what the filter needs about a primitive
 }  // namespace
 
 int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
-                 const BuildParams &prm, NearestService *nearest,
+                 const int32_t *Sin, int64_t ns, const BuildParams &prm,
+                 NearestService *nearest,
                  bool (*on_tree)(void *, const Layout &), void *ctx, Layout &out,
                  std::string &err) {
   const double t_start = now_ms();
-  int st = validate(Vin, nv, Fin, nf, err);
+  int st = validate(Vin, nv, Fin, nf, Sin, ns, err);
   if (st) return st;
   const int threads = prm.threads > 0 ? prm.threads
                                       : (int)std::max(1u, std::thread::hardware_concurrency());
@@ -544,8 +565,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   M.nf = nf;
   M.V.resize(nv);
   for (int64_t i = 0; i < nv; ++i) M.V[i] = {Vin[3 * i], Vin[3 * i + 1], Vin[3 * i + 2]};
-  M.F.assign(Fin, Fin + 3 * nf);
-  build_topology(M);
+  if (nf > 0) M.F.assign(Fin, Fin + 3 * nf);
+  build_topology(M, Sin, ns);
 
   // domain D
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -792,7 +813,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       perp[np_++] = {u, dot(u, b) + delta, -11};
       for (int64_t j = M.ef_off[e]; j < M.ef_off[e + 1] && np_ < 16; ++j) {
         int64_t f = M.ef[j];
-        if (M.degenerate[f]) continue;
+        if (f < 0 || M.degenerate[f]) continue;  // a segment side adds no half-space
         int k = M.fedge[3 * f] == e ? 0 : (M.fedge[3 * f + 1] == e ? 1 : 2);
         V3 m = face_inward(f, k);  // the far side of f: m.(x - a) <= 0
         perp[np_++] = {m, dot(m, a) + delta, (int32_t)(-12 - j)};

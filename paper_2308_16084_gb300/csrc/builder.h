@@ -87,8 +87,9 @@ struct Layout {
 };
 
 // Status codes mirror p2m_status.
-int build_layout(const float *V, int64_t nv, const int32_t *F, int64_t nf,
-                 const BuildParams &prm, NearestService *nearest,
+// S: ns segments (vertex pairs) that are edges of no face, may be NULL.
+int build_layout(const float *V, int64_t nv, const int32_t *F, int64_t nf, const int32_t *S,
+                 int64_t ns, const BuildParams &prm, NearestService *nearest,
                  // called once the KD tree exists, before the cells need it
                  bool (*on_tree)(void *ctx, const Layout &), void *ctx, Layout &out,
                  std::string &err);

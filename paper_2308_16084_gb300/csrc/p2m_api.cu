@@ -278,10 +278,18 @@ const char *p2m_status_string(p2m_status s) {
 }
 
 p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out) {
-  if (!mesh || !out || !mesh->verts || !mesh->tris || mesh->n_verts < 0 || mesh->n_tris < 0)
+  if (!mesh || !mesh->tris) return P2M_ERR_INVALID_ARG;
+  return p2m_build_mixed(mesh, nullptr, 0, opts, out);
+}
+
+p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_segs,
+                           const p2m_build_opts *opts, p2m_handle **out) {
+  if (!mesh || !out || !mesh->verts || mesh->n_verts < 0 || mesh->n_tris < 0 || n_segs < 0 ||
+      (mesh->n_tris > 0 && !mesh->tris) || (n_segs > 0 && !segs))
     return P2M_ERR_INVALID_ARG;
   *out = nullptr;
-  if (mesh->n_verts >= ((int64_t)1 << 30) || mesh->n_tris >= ((int64_t)1 << 29))
+  if (mesh->n_verts >= ((int64_t)1 << 30) || mesh->n_tris >= ((int64_t)1 << 29) ||
+      n_segs >= ((int64_t)1 << 29))
     return P2M_ERR_TOO_LARGE;
   p2m_build_opts o;
   p2m_default_opts(&o);
@@ -305,7 +313,8 @@ p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handl
   std::string err;
   int st;
   try {
-    st = p2m::build_layout(mesh->verts, mesh->n_verts, mesh->tris, mesh->n_tris, prm,
+    st = p2m::build_layout(mesh->verts, mesh->n_verts, mesh->tris, mesh->n_tris, segs, n_segs,
+                           prm,
                            assist ? &dn : nullptr, assist ? on_tree_cb : nullptr, h.get(), h->L,
                            err);
   } catch (const std::bad_alloc &) {

@@ -47,8 +47,8 @@ def test_status_strings(pg):
 
 
 def _host(pg, m, **kw):
-    return pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
-                  device_assist=False, **kw)
+    return pg.P2M(m.verts, m.tris, segs=m.meta.get("segs"), domain_scale=m.domain_scale,
+                  domain_margin=m.domain_margin, device_assist=False, **kw)
 
 
 @pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 4}), (2, {"grid": 40}),
@@ -64,9 +64,32 @@ def test_builder_tables_equal_oracle_tables_on_soups(pg, kind):
     _check_tables(pg, dg.soup_workload(kind, level=2, n_queries=10))
 
 
+def test_builder_tables_equal_oracle_tables_on_mixed_input(pg):
+    """A triangle mesh beside a wireframe (segments of no face), and the
+    wireframe alone."""
+    m = dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10)
+    _check_tables(pg, m)
+    S = m.meta["segs"]
+    used = np.unique(S)
+    remap = np.full(m.verts.shape[0], -1, np.int64)
+    remap[used] = np.arange(used.size)
+    wire = dg.Mesh("wire", m.verts[used], np.zeros((0, 3), np.int32), m.queries,
+                   m.domain_scale, m.domain_margin, meta={"segs": remap[S].astype(np.int32)})
+    _check_tables(pg, wire)
+
+
+def test_invalid_segments_return_status(pg):
+    V, F = dg.octahedron()
+    for segs in ([[0, 0]], [[0, 99]]):
+        with pytest.raises(pg.P2MError) as e:
+            pg.P2M(V.astype(np.float32), F, segs=segs, device_assist=False)
+        assert e.value.code == 2
+
+
 def _check_tables(pg, m):
     h = _host(pg, m)
-    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin,
+                          segs=m.meta.get("segs"))
     np.testing.assert_array_equal(h.edges(), o.edges())
     st = h.stats()
     assert st["n_entries"] == o.n_entries

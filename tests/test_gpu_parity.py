@@ -84,6 +84,30 @@ def test_parity_triangle_soups(pg, kind):
             np.testing.assert_array_equal(got[k], gpu[k])
 
 
+@pytest.mark.parametrize("wire_only", [False, True])
+def test_parity_mixed_primitives(pg, wire_only):
+    """Mixed segments and triangles (Sec. 5): a triangle mesh beside a
+    wireframe, and the wireframe alone (no faces at all)."""
+    m = dg.mixed_workload(mesh_level=3, wire_level=2, n_queries=30001)
+    S = m.meta["segs"]
+    V, F = m.verts, m.tris
+    if wire_only:
+        used = np.unique(S)
+        remap = np.full(V.shape[0], -1, np.int64)
+        remap[used] = np.arange(used.size)
+        V, F, S = V[used], np.zeros((0, 3), np.int32), remap[S].astype(np.int32)
+    mesh = pg.P2M(V, F, segs=S, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
+    o = oracle.OracleMesh(V, F, segs=S, build_tables=False)
+    np.testing.assert_array_equal(mesh.edges(), o.edges())
+    ref = o.bruteforce(m.queries)
+    gpu = run(mesh, m.queries)
+    s = pu.check(V, o.edges(), F, m.queries, gpu, ref, pu.tolerance(V), m.name)
+    assert s["prim_exact"] > 0.98
+    assert (gpu["prim_type"] == pg.EDGE).sum() > 3000
+    if wire_only:
+        assert not (gpu["prim_type"] == pg.FACE).any()
+
+
 def test_parity_against_paper_method(pg):
     """The GPU agrees with the oracle's own P2M query (Alg. A.2) too, and the
     product builder's interception lists equal the oracle's."""
