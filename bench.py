@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=None, help="fewer queries (profiling only)")
     ap.add_argument("--workload", type=int, default=1, choices=[1, 3, 4],
                     help="1: forward queries (default); 3: forward+backward; 4: 64-mesh batch")
+    ap.add_argument("--sweep", action="store_true",
+                    help="extra workloads: mesh resolution, query box, soups, mixed primitives")
     ap.add_argument("--layout", default=None,
                     help="load the built layout from this file if it exists, else build and "
                          "save it there")
@@ -577,10 +579,82 @@ def run_ours(args):
     return 0
 
 
+def run_sweep(args):
+    """Extra workloads (not the headline): mesh resolution, query box,
+    triangle soups and mixed primitives.  One JSON line with one entry per
+    case: build seconds, device-resident queries/s (CUDA events, 5 steps
+    after 2 warm-ups, fixed default tuning) and work per query."""
+    import torch
+    import paper_2308_16084_gb300 as pg
+    n = args.queries or 4_000_000
+    cases = []
+
+    def measure(name, mesh, q, extra):
+        out = {"dist": torch.empty(q.shape[0], device="cuda"),
+               "prim_id": torch.empty(q.shape[0], dtype=torch.int32, device="cuda"),
+               "closest": torch.empty(q.shape[0], 3, device="cuda"),
+               "prim_type": torch.empty(q.shape[0], dtype=torch.uint8, device="cuda")}
+        mesh.reserve(q.shape[0])
+        stream = torch.cuda.current_stream()
+        ms = timed(lambda: mesh.query(q, out=out), 2, stream)
+        ms = timed(lambda: mesh.query(q, out=out), 5, stream) / 5
+        cnt = mesh.counters(q)
+        st = mesh.stats()
+        cases.append({"case": name, "n_tris": mesh.n_tris, "n_queries": int(q.shape[0]),
+                      "queries_per_s": q.shape[0] / (ms / 1e3), "ms": ms,
+                      "entries_per_vertex": st["n_entries"] / max(1, mesh.n_verts),
+                      "work_per_query": {k: round(v / q.shape[0], 2) for k, v in cnt.items()},
+                      **extra})
+        print(json.dumps(cases[-1]), file=sys.stderr, flush=True)
+
+    def build(m, segs=None, scale=None):
+        t0 = time.perf_counter()
+        mesh = pg.P2M(m.verts, m.tris, segs=segs,
+                      domain_scale=m.domain_scale if scale is None else scale,
+                      domain_margin=m.domain_margin)
+        return mesh, time.perf_counter() - t0
+
+    # mesh resolution (workload 1's recipe at coarser levels)
+    for lvl in (5, 6, 7):
+        m = dg.workload(1, n_queries=n, level=lvl)
+        mesh, bs = build(m)
+        measure(f"resolution L{lvl}", mesh, torch.from_numpy(m.queries).cuda(),
+                {"build_s": round(bs, 1), "queries": "uniform in bbox x1.5"})
+    # query box on one mesh whose domain covers the widest box
+    m = dg.workload(1, n_queries=16, level=7)
+    mesh, bs = build(m, scale=3.2)
+    rq = np.random.default_rng(np.random.SeedSequence(dg.ROOT_SEED).spawn(8)[7])
+    diag = dg.bbox_diagonal(m.verts)
+    tris_f = m.tris.astype(np.int64)
+    boxes = [("near 0.01 diag", dg.near_surface(m.verts.astype(np.float64), tris_f, n, 0.01 * diag, rq))]
+    for sc in (1.2, 1.5, 3.0):
+        boxes.append((f"uniform bbox x{sc}", dg.uniform_in_box(m.verts.astype(np.float64), sc, n, rq)))
+    for label, qq in boxes:
+        measure(f"query box: {label}", mesh, torch.from_numpy(qq.astype(np.float32)).cuda(),
+                {"build_s": round(bs, 1), "domain": "bbox x3.2 + 0.01 diag"})
+    # triangle soups (the paper's soup test) and mixed primitives
+    for kind in ("watertight", "gapped", "penetrating"):
+        m = dg.soup_workload(kind, level=4, n_queries=min(n, 1_000_000))
+        mesh, bs = build(m)
+        measure(f"soup {kind} (5,120 faces)", mesh, torch.from_numpy(m.queries).cuda(),
+                {"build_s": round(bs, 1)})
+    m = dg.mixed_workload(mesh_level=6, wire_level=4, n_queries=min(n, 2_000_000))
+    mesh, bs = build(m, segs=m.meta["segs"])
+    measure("mixed: mesh L6 + wireframe L4", mesh, torch.from_numpy(m.queries).cuda(),
+            {"build_s": round(bs, 1), "n_segments": int(m.meta["segs"].shape[0])})
+    line = {"metric": "point-to-mesh queries/sec by workload (sweep)", "unit": UNIT,
+            "n_gpus": 1, "data": "synthetic", "dtype": "f32", "higher_is_better": True,
+            "sweep": cases}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.workload == 3:
         return run_fwd_bwd(args)
     if args.workload == 4:
