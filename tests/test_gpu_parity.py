@@ -96,7 +96,10 @@ def test_parity_mixed_primitives(pg, wire_only):
         remap = np.full(V.shape[0], -1, np.int64)
         remap[used] = np.arange(used.size)
         V, F, S = V[used], np.zeros((0, 3), np.int32), remap[S].astype(np.int32)
-    mesh = pg.P2M(V, F, segs=S, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
+    # the wireframe alone is smaller than the query box: widen its domain so
+    # that every query lies inside D
+    scale = 4.0 if wire_only else m.domain_scale
+    mesh = pg.P2M(V, F, segs=S, domain_scale=scale, domain_margin=m.domain_margin)
     o = oracle.OracleMesh(V, F, segs=S, build_tables=False)
     np.testing.assert_array_equal(mesh.edges(), o.edges())
     ref = o.bruteforce(m.queries)
@@ -104,6 +107,7 @@ def test_parity_mixed_primitives(pg, wire_only):
     s = pu.check(V, o.edges(), F, m.queries, gpu, ref, pu.tolerance(V), m.name)
     assert s["prim_exact"] > 0.98
     assert (gpu["prim_type"] == pg.EDGE).sum() > 3000
+    assert not (gpu["status"] & pg.Q_OUTSIDE_DOMAIN).any()
     if wire_only:
         assert not (gpu["prim_type"] == pg.FACE).any()
 
