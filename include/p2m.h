@@ -209,7 +209,12 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *   group_by_vertex  1 = two passes: nearest vertex of every query, a
  *                  counting sort of the queries by that vertex, then the
  *                  list scans, so the lanes of a warp share interception
- *                  lists (default); 0 = one fused kernel. */
+ *                  lists (default); 0 = one fused kernel.
+ *   sort_key       0 = the first sort orders the queries by Morton bucket
+ *                  (2^sort_bits buckets, default); 1 = by the vertex the
+ *                  seed grid gives their cell, so the lanes of a warp start
+ *                  their Voronoi walks at the same vertex (needs
+ *                  group_by_vertex = 1 and nn_walk = 2; sort_bits unused). */
 typedef struct {
   int sort_bits;
   int block_threads;
@@ -217,6 +222,7 @@ typedef struct {
   int nn_walk;
   int chunked;
   int group_by_vertex;
+  int sort_key;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);

@@ -34,7 +34,8 @@ class MeshDesc(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int),
-                ("chunked", ctypes.c_int), ("group_by_vertex", ctypes.c_int)]
+                ("chunked", ctypes.c_int), ("group_by_vertex", ctypes.c_int),
+                ("sort_key", ctypes.c_int)]
 
 
 class BatchIO(ctypes.Structure):
@@ -159,14 +160,15 @@ class P2M:
         check(lib.p2m_get_tuning(self._h, ctypes.byref(t)), "p2m_get_tuning")
         return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
                 "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk,
-                "chunked": t.chunked, "group_by_vertex": t.group_by_vertex}
+                "chunked": t.chunked, "group_by_vertex": t.group_by_vertex,
+                "sort_key": t.sort_key}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
         t = Tuning(cur["sort_bits"], cur["block_threads"], cur["warp_cooperative"],
-                   cur["nn_walk"], cur["chunked"], cur["group_by_vertex"])
+                   cur["nn_walk"], cur["chunked"], cur["group_by_vertex"], cur["sort_key"])
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):

@@ -264,7 +264,31 @@ struct SortParams {
 // first, which keeps several in flight per thread.
 constexpr int kSortItems = 4;
 
-__global__ void k_bucket_count(const float *__restrict__ q, int64_t n, SortParams sp,
+// sort keys: the Morton bucket of the query, or the seed-grid vertex of its
+// cell (nv for a query outside D or not finite): sorted by the latter, the
+// lanes of a warp start their Voronoi walks at the same vertex
+struct MortonKey {
+  SortParams sp;
+  __device__ __forceinline__ uint32_t operator()(float x, float y, float z) const {
+    return morton_bucket(x, y, z, sp.lo, sp.inv, sp.shift);
+  }
+};
+
+struct SeedKey {
+  DevView m;
+  __device__ __forceinline__ uint32_t operator()(float x, float y, float z) const {
+    const bool in = x >= m.dom_lo[0] && y >= m.dom_lo[1] && z >= m.dom_lo[2] &&
+                    x <= m.dom_hi[0] && y <= m.dom_hi[1] && z <= m.dom_hi[2];  // false for NaN
+    if (!in) return (uint32_t)m.nv;
+    const int gb = m.grid_bits;
+    const size_t cell = ((size_t)grid_cell(m, z, 2) << (2 * gb)) |
+                        ((size_t)grid_cell(m, y, 1) << gb) | (size_t)grid_cell(m, x, 0);
+    return __ldg(&m.seed[cell]);
+  }
+};
+
+template <class Key>
+__global__ void k_bucket_count(const float *__restrict__ q, int64_t n, Key key,
                                uint32_t *__restrict__ hist, uint2 *__restrict__ key_rank) {
   const int64_t base = (int64_t)blockIdx.x * blockDim.x * kSortItems + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -274,7 +298,7 @@ __global__ void k_bucket_count(const float *__restrict__ q, int64_t n, SortParam
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t i = base + (int64_t)k * blockDim.x;
-    b[k] = i < n ? morton_bucket(q[3 * i], q[3 * i + 1], q[3 * i + 2], sp.lo, sp.inv, sp.shift)
+    b[k] = i < n ? key(q[3 * i], q[3 * i + 1], q[3 * i + 2])
                  : 0xffffffffu;  // past the end: no bucket has this key
   }
   // warp-aggregated atomics: lanes of one bucket share a single atomicAdd
@@ -1200,8 +1224,35 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   base += al(8 * (size_t)n);
   const int T = 256;
   if (ev) cudaEventRecord(ev[0], stream);
-  if (tune.sort_bits > 0) {
-    const size_t nb = (size_t)1 << tune.sort_bits;
+  const bool grouped = tune.group_by_vertex && !counters && !tune.warp_mode &&
+                       m.nv + 1 <= (int64_t)kScanTile * kMaxScanTiles;
+  const size_t nbm = tune.sort_bits > 0 ? ((size_t)1 << tune.sort_bits) : 0;
+  // regrouping buffers, after the sort's own scratch
+  char *b2 = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) + al(16 * (size_t)n) +
+             al(8 * (size_t)n) + 2 * al(4 * nbm) + al(4 * kMaxScanTiles);
+  uint32_t *gv = (uint32_t *)b2;
+  b2 += al(4 * (size_t)n);
+  float4 *grouped_q = (float4 *)b2;
+  b2 += al(16 * (size_t)n);
+  float4 *rec = (float4 *)b2;
+  b2 += al(32 * (size_t)n);
+  uint32_t *vhist = (uint32_t *)b2;
+  b2 += al(4 * (size_t)(m.nv + 1));
+  uint32_t *voff = (uint32_t *)b2;
+  uint32_t *tiles2 = (uint32_t *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) +
+                     (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
+  if (grouped && scratch_bytes < query_scratch_bytes(n, tune.sort_bits, m.nv))
+    return cudaErrorInvalidValue;
+  if (grouped && tune.sort_key == 1 && m.seed) {
+    // counting sort by seed-grid vertex, in the regrouping's vertex buffers
+    cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
+    k_bucket_count<SeedKey><<<blocks_for(n, T * kSortItems), T, 0, stream>>>(
+        q, n, SeedKey{m}, vhist, key_rank);
+    bucket_scan(vhist, voff, tiles2, (int)(m.nv + 1), stream);
+    k_bucket_scatter<<<blocks_for(n, T * kSortItems), T, 0, stream>>>(q, n, key_rank, voff,
+                                                                      sorted);
+  } else if (tune.sort_bits > 0) {
+    const size_t nb = nbm;
     uint32_t *hist = (uint32_t *)base;
     base += al(4 * nb);
     uint32_t *off = (uint32_t *)base;
@@ -1215,7 +1266,8 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     }
     sp.shift = 30 - tune.sort_bits;
     cudaMemsetAsync(hist, 0, 4 * nb, stream);
-    k_bucket_count<<<blocks_for(n, T * kSortItems), T, 0, stream>>>(q, n, sp, hist, key_rank);
+    k_bucket_count<MortonKey><<<blocks_for(n, T * kSortItems), T, 0, stream>>>(
+        q, n, MortonKey{sp}, hist, key_rank);
     bucket_scan(hist, off, tiles, (int)nb, stream);
     k_bucket_scatter<<<blocks_for(n, T * kSortItems), T, 0, stream>>>(q, n, key_rank, off,
                                                                       sorted);
@@ -1224,31 +1276,16 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   }
   const int bt = tune.block_threads;
   if (ev) cudaEventRecord(ev[1], stream);
-  if (tune.group_by_vertex && !counters && !tune.warp_mode && m.nv + 1 <= (int64_t)kScanTile * kMaxScanTiles) {
-    // regroup by nearest vertex: buffers after the sort's own scratch
-    if (scratch_bytes < query_scratch_bytes(n, tune.sort_bits, m.nv)) return cudaErrorInvalidValue;
-    const size_t nbm = tune.sort_bits > 0 ? ((size_t)1 << tune.sort_bits) : 0;
-    char *b2 = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) + al(16 * (size_t)n) +
-               al(8 * (size_t)n) + 2 * al(4 * nbm) + al(4 * kMaxScanTiles);
-    uint32_t *gv = (uint32_t *)b2;
-    b2 += al(4 * (size_t)n);
-    float4 *grouped = (float4 *)b2;
-    b2 += al(16 * (size_t)n);
-    float4 *rec = (float4 *)b2;
-    b2 += al(32 * (size_t)n);
-    uint32_t *vhist = (uint32_t *)b2;
-    b2 += al(4 * (size_t)(m.nv + 1));
-    uint32_t *voff = (uint32_t *)b2;
-    uint32_t *tiles2 = (uint32_t *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) +
-                       (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
+  if (grouped) {
     const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
     cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
     k_nn_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, sorted, n, walk, vhist, key_rank);
     if (ev) cudaEventRecord(ev[2], stream);
     bucket_scan(vhist, voff, tiles2, (int)(m.nv + 1), stream);
-    k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped, gv);
+    k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped_q,
+                                                         gv);
     if (ev) cudaEventRecord(ev[3], stream);
-    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped, gv, n, tune.chunked, rec);
+    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
     if (ev) cudaEventRecord(ev[4], stream);
     k_unpack<<<blocks_for(n, T), T, 0, stream>>>(rec, n, dist, closest, prim_id, prim_type, save,
                                                  status);

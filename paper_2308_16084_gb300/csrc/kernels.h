@@ -45,6 +45,8 @@ struct QueryTuning {
                       // 2: super-chunk boxes, then chunk boxes
   int group_by_vertex = 1;  // 1: nearest-vertex pass, regroup queries by
                             // vertex, then the list pass (two kernels)
+  int sort_key = 0;  // 0: Morton buckets (2^sort_bits); 1: the seed-grid vertex of
+                     // the query's cell (with group_by_vertex and a seed grid)
 };
 
 // Scratch needed by launch_query for n points, in bytes (nv: vertices of

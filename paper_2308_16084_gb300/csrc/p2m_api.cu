@@ -340,6 +340,7 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   t->nn_walk = h->tune.nn_walk;
   t->chunked = h->tune.chunked;
   t->group_by_vertex = h->tune.group_by_vertex;
+  t->sort_key = h->tune.sort_key;
   return P2M_OK;
 }
 
@@ -352,7 +353,9 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
   if (t->nn_walk < 0 || t->nn_walk > 2) return P2M_ERR_INVALID_ARG;
   if (t->chunked < 0 || t->chunked > 2) return P2M_ERR_INVALID_ARG;
   if (t->group_by_vertex != 0 && t->group_by_vertex != 1) return P2M_ERR_INVALID_ARG;
+  if (t->sort_key != 0 && t->sort_key != 1) return P2M_ERR_INVALID_ARG;
   h->tune.group_by_vertex = t->group_by_vertex;
+  h->tune.sort_key = t->sort_key;
   h->tune.nn_walk = t->nn_walk;
   h->tune.chunked = t->chunked;
   h->tune.sort_bits = t->sort_bits;
@@ -926,9 +929,12 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   for (int gv = 0; gv < 2; ++gv)
   for (int ch = 2; ch < 3; ++ch)
   for (int wm = 0; wm < 1; ++wm)
+  for (int key = 0; key < 2; ++key)
   for (int bits : bits_c)
     for (int bt : block_c) {
-      p2m_tuning t{bits, bt, wm, 2, ch, gv};
+      // sorting by seed vertex ignores sort_bits and needs the regrouping
+      if (key == 1 && (gv == 0 || bits != bits_c[0] || !h->seed.p)) continue;
+      p2m_tuning t{bits, bt, wm, 2, ch, gv, key};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);

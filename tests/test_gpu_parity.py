@@ -149,6 +149,23 @@ def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked, 
         np.testing.assert_array_equal(got[k], base[k])
 
 
+@pytest.mark.parametrize("idx,kw", [(0, {}), (2, {"grid": 96}), (1, {"level": 5})])
+@pytest.mark.parametrize("threads", [64, 256])
+@pytest.mark.parametrize("chunked", [0, 2])
+def test_seed_vertex_sort_gives_identical_results(pg, idx, kw, threads, chunked):
+    """Sorting the queries by their seed-grid vertex instead of their Morton
+    bucket changes the order of work, not the results."""
+    m = dg.workload(idx, n_queries=50001, **kw)
+    mesh = build(pg, m)
+    mesh.tuning = {"chunked": chunked, "block_threads": threads}
+    base = run(mesh, m.queries)
+    mesh.tuning = {"sort_key": 1}
+    assert mesh.tuning["sort_key"] == 1
+    got = run(mesh, m.queries)
+    for k in ("dist", "closest", "prim_id", "prim_type", "status"):
+        np.testing.assert_array_equal(got[k], base[k])
+
+
 def test_edge_cases(pg):
     m = dg.workload(0, n_queries=10)
     mesh = build(pg, m)
