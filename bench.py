@@ -403,6 +403,42 @@ def kernels_per_step(tuning):
     return sort + 1
 
 
+def max_over_ranks(values, dist):
+    """Element-wise maximum of per-rank floats over all ranks: the slowest
+    replica sets each time.  dist is torch.distributed (NCCL or gloo) or
+    None for one process."""
+    if dist is None:
+        return list(values)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def share_layout(rank, world, build, load, path, dist):
+    """Rank 0 builds the layout and saves it to `path`; the other replicas
+    load it after a barrier (the query path has no exchange step, so this
+    file is the only thing the replicas share)."""
+    mesh = None
+    if rank == 0:
+        mesh = build()
+        if world > 1:
+            mesh.save(path)
+    if world > 1:
+        dist.barrier()
+        if rank != 0:
+            mesh = load(path)
+        dist.barrier()
+    return mesh
+
+
+def replica_throughput(units_per_rank, steps, world, seconds):
+    """Whole-job rate of N replicas: all ranks' units over the slowest
+    rank's time."""
+    return units_per_rank * steps * world / seconds
+
+
 def run_ours(args):
     import torch
     import paper_2308_16084_gb300 as pg
@@ -421,17 +457,14 @@ def run_ours(args):
     layout = os.path.join("/tmp", f"p2m_bench_{os.getpid() if world == 1 else 'shared'}.p2m")
     if args.layout and os.path.exists(args.layout):
         mesh = pg.P2M.load(args.layout)
-    elif rank == 0:
-        mesh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin)
-        if world > 1:
-            mesh.save(layout)
-        if args.layout:
-            mesh.save(args.layout)
-    if world > 1 and not (args.layout and os.path.exists(args.layout)):
-        dist.barrier()
-        if rank != 0:
-            mesh = pg.P2M.load(layout)
-        dist.barrier()
+    else:
+        def build_and_keep():
+            mh = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale,
+                        domain_margin=m.domain_margin)
+            if args.layout:
+                mh.save(args.layout)
+            return mh
+        mesh = share_layout(rank, world, build_and_keep, pg.P2M.load, layout, dist)
     build_s = time.perf_counter() - t0
     st = mesh.stats()
 
@@ -471,11 +504,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     tsum = mesh.timing_summary()
     mesh.set_timing(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks([ms], dist)[0]
+    value = replica_throughput(n, args.steps, world, ms / 1e3)
 
     # end to end through the host APIs: pinned host buffers, every step copies
     # its queries in and its distances and ids out inside the timed region.
@@ -506,14 +536,11 @@ def run_ours(args):
     pipe.wait()
     e2e_s = time.perf_counter() - t0
     pipe.close()
-    if dist:
-        t = torch.tensor([e2e_s, serial_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s, serial_s = float(t[0].item()), float(t[1].item())
-    e2e = {"value": n * args.steps * world / e2e_s, "unit": UNIT,
+    e2e_s, serial_s = max_over_ranks([e2e_s, serial_s], dist)
+    e2e = {"value": replica_throughput(n, args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 8 * n,
            "api": "p2m_pipe_submit, 2 slots (pinned host buffers)",
-           "serial_value": n * args.steps * world / serial_s,
+           "serial_value": replica_throughput(n, args.steps, world, serial_s),
            "serial_api": "p2m_query_host (synchronous per step)"}
 
     # roofline of the dominant kernel, timed live over the timed region
