@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--queries", type=int, default=None, help="fewer queries (profiling only)")
     ap.add_argument("--workload", type=int, default=1, choices=[1, 3, 4],
                     help="1: forward queries (default); 3: forward+backward; 4: 64-mesh batch")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed p2m_tuning fields as JSON (profiling runs with --no-autotune)")
     ap.add_argument("--sweep", action="store_true",
                     help="extra workloads: mesh resolution, query box, soups, mixed primitives")
     ap.add_argument("--layout", default=None,
@@ -475,6 +477,8 @@ def run_ours(args):
            "prim_type": torch.empty(n, dtype=torch.uint8, device="cuda")}
     mesh.reserve(n)
     tuned_ms = None
+    if args.tuning:
+        mesh.tuning = json.loads(args.tuning)
     if not args.no_autotune:
         tuned_ms = mesh.autotune(q, reps=2)
     stream = torch.cuda.current_stream()
