@@ -15,6 +15,8 @@
 #include "quant.h"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -650,6 +652,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     C.safe2 = k == KSEED ? 0.25 * d2s[KSEED - 1] : std::numeric_limits<double>::infinity();
   });
 
+  // optional trace of the cell stage on stderr (P2M_BUILD_TRACE=1)
+  const bool trace = std::getenv("P2M_BUILD_TRACE") != nullptr;
+  if (trace) std::fprintf(stderr, "p2m build: seeding %.0f ms\n", now_ms() - t_cells);
+  std::atomic<int64_t> host_searches{0};
   // ---- certification rounds: a corner x is settled when no vertex is
   // strictly nearer to x than the cell's own vertex; a cell whose corners
   // are all settled equals Cell(v) ∩ D (it is convex and contains the cell).
@@ -677,6 +683,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     if (nq == 0) break;
     ++rounds;
     cert_queries += nq;
+    const double t_round = now_ms();
+    host_searches = 0;
     std::vector<int64_t> viol_pos(nq, -1);
     bool used_device = false;
     if (nearest) {
@@ -707,9 +715,13 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
           // (a float32 near-tie), settle the corner with the host search
           const int64_t prop = qans[coff[p] + i];
           w = (prop >= 0 && prop != p && len2(T.P[prop] - x) < r2) ? prop : -1;
-          if (w < 0 && prop != p) w = nearest_within(T, x, r2);
+          if (w < 0 && prop != p) {
+            w = nearest_within(T, x, r2);
+            if (trace) ++host_searches;
+          }
         } else {
           w = nearest_within(T, x, r2);
+          if (trace) ++host_searches;
         }
         if (w >= 0 && w != p &&
             std::find(C.applied.begin(), C.applied.end(), (int32_t)w) == C.applied.end() &&
@@ -728,6 +740,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
         C.applied.push_back((int32_t)w);
       }
     });
+    if (trace)
+      std::fprintf(stderr, "p2m build: round %lld: %lld corners, %lld host searches, %.0f ms\n",
+                   (long long)rounds, (long long)nq, (long long)host_searches.load(),
+                   now_ms() - t_round);
     if (rounds > 64) break;
   }
   corner.clear();
