@@ -701,6 +701,42 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       });
       used_device = nearest->query(qbuf.data(), nq, qans.data());
     }
+    // corners whose float32 proposal does not settle them: decided by the
+    // exact double-precision search, on the device when it offers one
+    std::vector<int64_t> exact(nq, -3);  // -3: not needed
+    if (used_device) {
+      std::vector<uint8_t> need(nq, 0);
+      parallel_for(nv, threads, 256, [&](int64_t p, int) {
+        for (size_t i = 0; i < corner[p].size(); ++i) {
+          const int64_t g = coff[p] + (int64_t)i;
+          const V3 x = corner[p][i];
+          const double r2 = len2(x - T.P[p]) - epsc;
+          const int64_t prop = qans[g];
+          const bool settled = prop == p || (prop >= 0 && len2(T.P[prop] - x) < r2);
+          need[g] = settled ? 0 : 1;
+        }
+      });
+      std::vector<int64_t> idx;
+      for (int64_t g = 0; g < nq; ++g)
+        if (need[g]) idx.push_back(g);
+      if (!idx.empty()) {
+        std::vector<double> xs(3 * idx.size()), rs(idx.size());
+        std::vector<int64_t> ans(idx.size());
+        std::vector<int64_t> owner(nq);
+        for (int64_t p = 0; p < nv; ++p)
+          for (int64_t g = coff[p]; g < coff[p + 1]; ++g) owner[g] = p;
+        for (size_t k = 0; k < idx.size(); ++k) {
+          const int64_t g = idx[k], p = owner[g];
+          const V3 x = corner[p][g - coff[p]];
+          xs[3 * k] = x.x;
+          xs[3 * k + 1] = x.y;
+          xs[3 * k + 2] = x.z;
+          rs[k] = len2(x - T.P[p]) - epsc;
+        }
+        if (nearest->within(xs.data(), rs.data(), (int64_t)idx.size(), ans.data()))
+          for (size_t k = 0; k < idx.size(); ++k) exact[idx[k]] = ans[k];
+      }
+    }
     parallel_for(nv, threads, 64, [&](int64_t p, int t) {
       CellWork &C = cells[p];
       if (corner[p].empty()) return;
@@ -712,12 +748,17 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
         if (used_device) {
           // the float32 search proposes, double precision decides; when the
           // proposal is another vertex that is not strictly nearer in double
-          // (a float32 near-tie), settle the corner with the host search
+          // (a float32 near-tie), the exact search settles the corner
           const int64_t prop = qans[coff[p] + i];
           w = (prop >= 0 && prop != p && len2(T.P[prop] - x) < r2) ? prop : -1;
           if (w < 0 && prop != p) {
-            w = nearest_within(T, x, r2);
-            if (trace) ++host_searches;
+            const int64_t e = exact[coff[p] + i];
+            if (e >= -1) {
+              w = e;
+            } else {
+              w = nearest_within(T, x, r2);
+              if (trace) ++host_searches;
+            }
           }
         } else {
           w = nearest_within(T, x, r2);
@@ -741,9 +782,12 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       }
     });
     if (trace)
-      std::fprintf(stderr, "p2m build: round %lld: %lld corners, %lld host searches, %.0f ms\n",
-                   (long long)rounds, (long long)nq, (long long)host_searches.load(),
-                   now_ms() - t_round);
+      std::fprintf(stderr, "p2m build: round %lld: %lld corners, %lld exact searches on the "
+                   "device, %lld on the host, %.0f ms\n",
+                   (long long)rounds, (long long)nq,
+                   (long long)std::count_if(exact.begin(), exact.end(),
+                                            [](int64_t e) { return e >= -1; }),
+                   (long long)host_searches.load(), now_ms() - t_round);
     if (rounds > 64) break;
   }
   corner.clear();

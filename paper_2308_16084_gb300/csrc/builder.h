@@ -28,6 +28,13 @@ struct BuildParams {
 struct NearestService {
   virtual ~NearestService() = default;
   virtual bool query(const float *xyz, int64_t n, int32_t *out_pos) = 0;
+  // exact (double precision) certification search: for each x (3 doubles)
+  // the nearest KD-tree position strictly closer than sqrt(r2), -1 if none,
+  // -2 where the service gave up (the host searches); false = unavailable
+  virtual bool within(const double *xyz, const double *r2, int64_t n, int64_t *out_pos) {
+    (void)xyz, (void)r2, (void)n, (void)out_pos;
+    return false;
+  }
 };
 
 // Device-ready arrays (all little-endian, float32 unless stated).

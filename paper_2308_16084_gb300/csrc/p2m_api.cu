@@ -232,6 +232,27 @@ struct DeviceNearest : p2m::NearestService {
     if (!ok) cudaGetLastError();
     return ok;
   }
+  bool within(const double *xyz, const double *r2, int64_t n, int64_t *out) override {
+    const int64_t chunk = 1 << 22;
+    const int64_t m = std::min(n, chunk);
+    double *dx = nullptr, *dr = nullptr;
+    int64_t *dout = nullptr;
+    bool ok = cudaMalloc((void **)&dx, 24 * m) == cudaSuccess &&
+              cudaMalloc((void **)&dr, 8 * m) == cudaSuccess &&
+              cudaMalloc((void **)&dout, 8 * m) == cudaSuccess;
+    for (int64_t s = 0; s < n && ok; s += chunk) {
+      const int64_t k = std::min(chunk, n - s);
+      ok = cudaMemcpy(dx, xyz + 3 * s, 24 * k, cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(dr, r2 + s, 8 * k, cudaMemcpyHostToDevice) == cudaSuccess &&
+           p2m::launch_nearest_within_f64(h->view, dx, dr, k, dout, 0) == cudaSuccess &&
+           cudaMemcpy(out + s, dout, 8 * k, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (dx) cudaFree(dx);
+    if (dr) cudaFree(dr);
+    if (dout) cudaFree(dout);
+    if (!ok) cudaGetLastError();
+    return ok;
+  }
 };
 
 // the builder fills the handle's own layout; once its KD tree exists the

@@ -63,6 +63,25 @@ def test_parity_workloads(pg, idx, kw, n, mode):
     np.testing.assert_array_equal((gpu["status"] & 1) == 1, outside)
 
 
+@pytest.mark.parametrize("idx,kw", [(1, {"level": 4}), (2, {"grid": 40})])
+def test_device_assisted_build_equals_host_build(pg, idx, kw):
+    """The certification of the Voronoi cells on the device (float32
+    proposals, double-precision decisions) gives the host builder's tables
+    bit for bit: same lists, same box codes."""
+    m = dg.workload(idx, n_queries=10, **kw)
+    a = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
+               device_assist=True)
+    b = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
+               device_assist=False)
+    assert a.stats()["n_entries"] == b.stats()["n_entries"]
+    for v in range(0, m.verts.shape[0], 3):
+        ta, ia, ba = a.interception_list(v)
+        tb, ib, bb = b.interception_list(v)
+        np.testing.assert_array_equal(ta, tb)
+        np.testing.assert_array_equal(ia, ib)
+        np.testing.assert_array_equal(ba, bb)
+
+
 @pytest.mark.parametrize("kind", ["watertight", "gapped", "penetrating"])
 def test_parity_triangle_soups(pg, kind):
     """The paper's soup test (Sec. 5): the same surface watertight, as a soup
