@@ -25,7 +25,8 @@ def _nvcc():
 
 def _sources():
     return {
-        "kernels.cu": "cu", "p2m_api.cu": "cu", "noalloc.cu": "cu", "builder.cpp": "cpp",
+        "kernels.cu": "cu", "certify.cu": "cu", "p2m_api.cu": "cu", "noalloc.cu": "cu",
+        "builder.cpp": "cpp",
     }
 
 

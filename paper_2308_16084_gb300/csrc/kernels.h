@@ -70,13 +70,6 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
 cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_t *out_pos,
                            cudaStream_t stream, bool original_ids = false, int nn_walk = 0);
 
-// Builder certification in double precision: for each point x[i] (3
-// doubles), the nearest KD-tree position strictly closer than sqrt(r2[i]),
-// -1 if none, -2 if the traversal stack would overflow (search on the host).
-// Same answers as the host search.
-cudaError_t launch_nearest_within_f64(const DevView &m, const double *x, const double *r2,
-                                      int64_t n, int64_t *out, cudaStream_t stream = 0);
-
 // Fill the seed grid: nearest vertex (row) of every cell centre of the
 // G^3 grid over D (G = 2^view.grid_bits), by KD-tree backtracking.
 cudaError_t launch_seed_grid(const DevView &m, uint32_t *seed, cudaStream_t stream);

@@ -16,6 +16,7 @@
 
 #include "../../include/p2m.h"
 #include "builder.h"
+#include "certify.h"
 #include "quant.h"
 #include "kernels.h"
 #include "quant.h"
