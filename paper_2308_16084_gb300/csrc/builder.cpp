@@ -913,8 +913,22 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     while (head < tail) {
       const int64_t p = X.queue[head++];
       ++X.inspections;
-      // ConvexPoly(v, prim) = Cell(v) ∩ Space-perp(prim)
+      // ConvexPoly(v, prim) = Cell(v) ∩ Space-perp(prim).  A half-space that
+      // leaves every point of the cell beyond it empties the result whatever
+      // the order of the cuts (later corners are convex combinations of the
+      // cell's), so that case is settled before any cut is made.
       const Poly *cur = &cell[p];
+      bool emptied = false;
+      for (int j = 0; j < np_ && !emptied; ++j) {
+        bool all_beyond = true;
+        for (const V3 &x : cur->pt)
+          if (!(dot(perp[j].n, x) - perp[j].c > eps)) {
+            all_beyond = false;
+            break;
+          }
+        emptied = all_beyond && !cur->pt.empty();
+      }
+      if (emptied) continue;
       Poly *bufs[2] = {&X.A, &X.B};
       int wsel = 0;
       for (int j = 0; j < np_ && !cur->empty(); ++j) {
