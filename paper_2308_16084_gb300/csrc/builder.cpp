@@ -733,8 +733,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
           xs[3 * k + 2] = x.z;
           rs[k] = len2(x - T.P[p]) - epsc;
         }
+        const double t_dev = now_ms();
         if (nearest->within(xs.data(), rs.data(), (int64_t)idx.size(), ans.data()))
           for (size_t k = 0; k < idx.size(); ++k) exact[idx[k]] = ans[k];
+        if (trace) std::fprintf(stderr, "p2m build:   exact device search %.0f ms\n", now_ms() - t_dev);
       }
     }
     parallel_for(nv, threads, 64, [&](int64_t p, int t) {
@@ -848,6 +850,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     std::vector<int32_t> queue;
     Poly A, B;
     CutScratch S;
+    std::vector<double> gv;
     int64_t inspections = 0;
   };
   std::vector<TLS> tls(threads);
@@ -950,11 +953,14 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
         blo[2] = std::min(blo[2], x.z); bhi[2] = std::max(bhi[2], x.z);
         have = true;
       };
+      // g at every loop point once (each point ends two loop edges)
+      X.gv.resize(cur->pt.size());
+      for (size_t q = 0; q < cur->pt.size(); ++q) X.gv[q] = gval(cur->pt[q], pv);
       for (int f = 0; f < cur->nf(); ++f) {
         const int b0 = cur->beg[f], k = cur->beg[f + 1] - b0;
         for (int q = 0; q < k; ++q) {
           V3 x0 = cur->pt[b0 + q], x1 = cur->pt[b0 + (q + 1) % k];
-          double g0 = gval(x0, pv), g1 = gval(x1, pv);
+          double g0 = X.gv[b0 + q], g1 = X.gv[b0 + (q + 1) % k];
           if (g0 > 0) {
             keep = true;
             grow(x0);
