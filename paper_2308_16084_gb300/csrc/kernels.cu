@@ -276,14 +276,19 @@ struct MortonKey {
 
 struct SeedKey {
   DevView m;
+  __device__ __forceinline__ int cell(float v, int a) const {
+    const int G = 1 << m.sort_grid_bits;
+    const float u = (v - m.dom_lo[a]) / (m.dom_hi[a] - m.dom_lo[a]);
+    return min(G - 1, max(0, (int)(u * (float)G)));
+  }
   __device__ __forceinline__ uint32_t operator()(float x, float y, float z) const {
     const bool in = x >= m.dom_lo[0] && y >= m.dom_lo[1] && z >= m.dom_lo[2] &&
                     x <= m.dom_hi[0] && y <= m.dom_hi[1] && z <= m.dom_hi[2];  // false for NaN
     if (!in) return (uint32_t)m.nv;
-    const int gb = m.grid_bits;
-    const size_t cell = ((size_t)grid_cell(m, z, 2) << (2 * gb)) |
-                        ((size_t)grid_cell(m, y, 1) << gb) | (size_t)grid_cell(m, x, 0);
-    return __ldg(&m.seed[cell]);
+    const int gb = m.sort_grid_bits;
+    const size_t c = ((size_t)cell(z, 2) << (2 * gb)) | ((size_t)cell(y, 1) << gb) |
+                     (size_t)cell(x, 0);
+    return __ldg(&m.sort_seed[c]);
   }
 };
 
@@ -1243,7 +1248,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
                      (al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nbm)) / 4;
   if (grouped && scratch_bytes < query_scratch_bytes(n, tune.sort_bits, m.nv))
     return cudaErrorInvalidValue;
-  if (grouped && tune.sort_key == 1 && m.seed) {
+  if (grouped && tune.sort_key == 1 && m.sort_seed) {
     // counting sort by seed-grid vertex, in the regrouping's vertex buffers
     cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);
     k_bucket_count<SeedKey><<<blocks_for(n, T * kSortItems), T, 0, stream>>>(

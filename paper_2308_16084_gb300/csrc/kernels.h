@@ -28,6 +28,8 @@ struct DevView {
   float qstep[3], qbase[3];   // 1 / qinv and qlo - qstep (float ops, quant.h)
   const uint32_t *seed;       // G^3 rows: nearest vertex of every seed-grid cell centre
   int grid_bits;              // G = 2^grid_bits cells per axis over D (0 = no grid)
+  const uint32_t *sort_seed;  // the same at 2^sort_grid_bits <= 256 cells per axis (small
+  int sort_grid_bits;         // enough for L2): the key of the seed-vertex sort
   int64_t nv;
   int64_t L;                // KD-tree leaves (2^depth)
   int depth;

@@ -82,8 +82,8 @@ struct p2m_handle {
   Layout L;                 // host copy of the layout
   DevBuf<float> kd_nodes, kd_points, edge_rec, face_rec;
   DevBuf<uint32_t> entries;
-  DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed;
-  int grid_bits = 0;
+  DevBuf<uint32_t> row_off, nb_off, nb, chunk_off, seed, sort_seed;
+  int grid_bits = 0, sort_grid_bits = 0;
   DevBuf<uint32_t> chunks, super_off, supers;
   DevBuf<float> nbp;
   DevBuf<int32_t> edges, tris;
@@ -142,6 +142,8 @@ struct p2m_handle {
     p2m::q_frame_derive(view.qlo, view.qinv, view.qstep, view.qbase);
     view.seed = seed.p;
     view.grid_bits = seed.p ? grid_bits : 0;
+    view.sort_seed = sort_seed.p ? sort_seed.p : seed.p;
+    view.sort_grid_bits = sort_seed.p ? sort_grid_bits : view.grid_bits;
     view.nv = L.nv;
     view.depth = L.kd_depth;
     view.L = (int64_t)1 << L.kd_depth;
@@ -178,7 +180,7 @@ struct p2m_handle {
     if (e == cudaSuccess) e = make_seed_grid();
     device_bytes = 4 * (kd_nodes.n + kd_points.n + entries.n + edge_rec.n + face_rec.n +
                         row_off.n + edges.n + tris.n + nb_off.n + nb.n + chunk_off.n + chunks.n +
-                        seed.n + nbp.n + super_off.n + supers.n);
+                        seed.n + sort_seed.n + nbp.n + super_off.n + supers.n);
     return e;
   }
 
@@ -200,6 +202,23 @@ struct p2m_handle {
     grid_bits = k;
     make_view();
     e = p2m::launch_seed_grid(view, seed.p, 0);
+    // the sort key's grid: the same at 256^3 (64 MiB, small enough for L2)
+    // when the walk's grid is finer
+    sort_seed.reset();
+    if (e == cudaSuccess && k > 8) {
+      const size_t c2 = (size_t)1 << 24;
+      e = cudaMalloc((void **)&sort_seed.p, c2 * sizeof(uint32_t));
+      if (e != cudaSuccess) {
+        sort_seed.p = nullptr;
+        return e;
+      }
+      sort_seed.n = c2;
+      sort_grid_bits = 8;
+      p2m::DevView v2 = view;
+      v2.grid_bits = 8;
+      e = p2m::launch_seed_grid(v2, sort_seed.p, 0);
+    }
+    make_view();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
   }
