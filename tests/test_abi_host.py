@@ -203,3 +203,21 @@ def test_queries_on_host_only_handle_fail_loudly(pg):
     with pytest.raises(pg.P2MError) as e:
         h.pipeline(n)
     assert e.value.code == 8
+
+
+def test_tuning_fields_are_validated(pg):
+    """Every p2m_tuning field is range-checked; a rejected setting leaves the
+    previous one in place."""
+    m = dg.workload(0, n_queries=10, level=1)
+    h = _host(pg, m)
+    base = h.tuning
+    assert set(base) == {"sort_bits", "block_threads", "warp_cooperative", "nn_walk",
+                         "chunked", "group_by_vertex", "sort_key"}
+    h.tuning = {"sort_key": 1, "block_threads": 128, "sort_bits": 12}
+    assert h.tuning["sort_key"] == 1 and h.tuning["block_threads"] == 128
+    for bad in ({"sort_key": 2}, {"group_by_vertex": 3}, {"chunked": 3}, {"nn_walk": -1},
+                {"block_threads": 96}, {"sort_bits": 25}, {"warp_cooperative": 2}):
+        with pytest.raises(pg.P2MError) as e:
+            h.tuning = bad
+        assert e.value.code == 1
+        assert h.tuning["sort_key"] == 1 and h.tuning["block_threads"] == 128
