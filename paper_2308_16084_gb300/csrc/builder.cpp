@@ -433,7 +433,10 @@ inline double box_d2(const double *b, V3 q) {
   return dx * dx + dy * dy + dz * dz;
 }
 
-// nearest tree position strictly closer than sqrt(r2), or -1
+// The nearest tree position strictly closer than sqrt(r2), or -1; among
+// positions at the same (double) distance the lowest.  The answer is thus
+// fixed by the point set alone, whatever order a search visits it in (the
+// device search prunes in float32 and must agree with this one).
 int64_t nearest_within(const Tree &T, V3 q, double r2) {
   struct Item {
     int64_t node;
@@ -444,14 +447,17 @@ int64_t nearest_within(const Tree &T, V3 q, double r2) {
   int64_t best = -1;
   double bd = r2;
   st[sp++] = {0, box_d2(&T.box[0], q)};
+  // a subtree may hold a better point while its box is nearer than the best
+  // distance, or exactly as near once a best exists (a lower position)
+  auto open = [&](double d2) { return d2 < bd || (best >= 0 && d2 == bd); };
   while (sp) {
     Item it = st[--sp];
-    if (!(it.d2 < bd)) continue;
+    if (!open(it.d2)) continue;
     if (it.node >= T.L - 1) {
       int64_t j = it.node - (T.L - 1);
       for (int64_t p = T.first(j), e = T.first(j + 1); p < e; ++p) {
         double d = len2(T.P[p] - q);
-        if (d < bd) {
+        if (d < bd || (best >= 0 && d == bd && p < best)) {
           bd = d;
           best = p;
         }
@@ -464,8 +470,8 @@ int64_t nearest_within(const Tree &T, V3 q, double r2) {
       std::swap(c0, c1);
       std::swap(d0, d1);
     }
-    if (d1 < bd) st[sp++] = {c1, d1};
-    if (d0 < bd) st[sp++] = {c0, d0};
+    if (open(d1)) st[sp++] = {c1, d1};
+    if (open(d0)) st[sp++] = {c0, d0};
   }
   return best;
 }
