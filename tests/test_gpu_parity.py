@@ -216,6 +216,28 @@ def test_edge_cases(pg):
     assert (gpu["status"][:2] & pg.Q_NONFINITE).all() and np.isfinite(gpu["dist"][2])
 
 
+def test_size_limits_rejected_before_any_work(pg):
+    """Counts at the 2^31 limit (and negative ones) come back as status codes
+    from the argument checks, before any allocation or launch; the small
+    buffers passed are never touched."""
+    import ctypes
+    m = dg.workload(0, n_queries=10)
+    mesh = build(pg, m)
+    buf = torch.zeros(16, device="cuda")
+    ptr = ctypes.c_void_p(buf.data_ptr())
+    big = 1 << 31
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    lib = pg.lib
+    assert lib.p2m_query(mesh._h, ptr, big, ptr, None, ptr, None, None, None, st) == 9
+    assert lib.p2m_query(mesh._h, ptr, -1, ptr, None, ptr, None, None, None, st) == 1
+    assert lib.p2m_nearest_vertex(mesh._h, ptr, big, ptr, st) == 9
+    assert lib.p2m_reserve(mesh._h, big) == 9
+    out = (ctypes.c_int64 * 6)()
+    assert lib.p2m_query_counters(mesh._h, ptr, big, out, st) == 9
+    torch.cuda.synchronize()
+    assert (buf == 0).all()
+
+
 def test_determinism_and_save_load(pg):
     m = dg.workload(2, n_queries=40000, grid=64)
     mesh = build(pg, m)
