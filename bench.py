@@ -277,10 +277,11 @@ def run_reference(args):
     v = per * args.steps / dt
     sample = (f"{per} queries per step, evenly strided over the {m.queries.shape[0]} queries; "
               "FP64 brute force over all vertices, open edges and open faces")
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
+            "hardware": "host cores only: rank 0 runs the oracle, the GPUs stay idle",
             "config": config_of(m, args, {"parallelism": f"{threads} host threads"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
