@@ -211,10 +211,12 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  list scans, so the lanes of a warp share interception
  *                  lists (default); 0 = one fused kernel.
  *   sort_key       0 = the first sort orders the queries by Morton bucket
- *                  (2^sort_bits buckets, default); 1 = by the vertex the
- *                  seed grid gives their cell, so the lanes of a warp start
- *                  their Voronoi walks at the same vertex (needs
- *                  group_by_vertex = 1 and nn_walk = 2; sort_bits unused). */
+ *                  (2^sort_bits buckets, default); 1 = by the vertex a seed
+ *                  grid gives their cell (a 256^3 copy of the walk's grid
+ *                  when that is finer), so the lanes of a warp start their
+ *                  Voronoi walks near the same vertex (needs
+ *                  group_by_vertex = 1; otherwise the Morton sort runs;
+ *                  sort_bits unused).  Results do not depend on it. */
 typedef struct {
   int sort_bits;
   int block_threads;
