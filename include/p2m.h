@@ -74,8 +74,9 @@ typedef struct {
   float delta_rel;     /* conservative widening of cells, Space-perp half-spaces, filter
                           and Region boxes, as a fraction of diag(D) (default 4e-6)        */
   int host_threads;    /* preprocessing threads, 0 = all cores (default 0)                 */
-  int device_assist;   /* 1 = certify Voronoi cells with the GPU nearest-vertex kernel,
-                          0 = CPU only (default 1; 0 works without a GPU for the tables)   */
+  int device_assist;   /* 1 = certify Voronoi cells on the GPU (float32 nearest-vertex
+                          proposals, exact searches decided in double precision; same
+                          tables as 0), 0 = CPU only (default 1; 0 works without a GPU) */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
 } p2m_build_opts;
 
