@@ -78,6 +78,30 @@ def test_builder_tables_equal_oracle_tables_on_mixed_input(pg):
     _check_tables(pg, wire)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_builder_tables_equal_oracle_tables_on_random_inputs(pg, seed):
+    """Seeded random inputs beyond the workloads: a soup of random triangles
+    in a box (some cutting through each other), plus random segments on
+    half of the seeds."""
+    rng = np.random.default_rng(1000 + seed)
+    nt = int(rng.integers(8, 40))
+    c = rng.uniform(-1, 1, size=(nt, 1, 3))
+    tri = c + rng.uniform(-0.35, 0.35, size=(nt, 3, 3))
+    V = tri.reshape(-1, 3)
+    F = np.arange(3 * nt, dtype=np.int32).reshape(-1, 3)
+    segs = None
+    if seed % 2:
+        ns = int(rng.integers(3, 12))
+        a = rng.uniform(-1, 1, size=(ns, 3))
+        b = a + rng.uniform(-0.4, 0.4, size=(ns, 3))
+        base = V.shape[0]
+        V = np.concatenate([V, a, b], 0)
+        segs = np.stack([base + np.arange(ns), base + ns + np.arange(ns)], 1).astype(np.int32)
+    m = dg.Mesh(f"random-{seed}", V.astype(np.float32), F, np.zeros((1, 3), np.float32),
+                1.25, 0.05, meta={} if segs is None else {"segs": segs})
+    _check_tables(pg, m)
+
+
 def test_invalid_segments_return_status(pg):
     V, F = dg.octahedron()
     for segs in ([[0, 0]], [[0, 99]]):
