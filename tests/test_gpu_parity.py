@@ -134,6 +134,33 @@ def test_parity_mixed_primitives(pg, wire_only):
         assert not (gpu["prim_type"] == pg.FACE).any()
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_parity_random_soups(pg, seed):
+    """Seeded random triangle soups in a box (faces cutting through each
+    other), with random segments on half of the seeds, against the oracle's
+    plain definition."""
+    rng = np.random.default_rng(2000 + seed)
+    nt = int(rng.integers(20, 200))
+    c = rng.uniform(-1, 1, size=(nt, 1, 3))
+    V = (c + rng.uniform(-0.3, 0.3, size=(nt, 3, 3))).reshape(-1, 3)
+    F = np.arange(3 * nt, dtype=np.int32).reshape(-1, 3)
+    S = None
+    if seed % 2:
+        ns = int(rng.integers(5, 40))
+        a = rng.uniform(-1, 1, size=(ns, 3))
+        base = V.shape[0]
+        V = np.concatenate([V, a, a + rng.uniform(-0.4, 0.4, size=(ns, 3))], 0)
+        S = np.stack([base + np.arange(ns), base + ns + np.arange(ns)], 1).astype(np.int32)
+    V = V.astype(np.float32)
+    q = dg.uniform_in_box(V.astype(np.float64), 1.2, 20001, rng).astype(np.float32)
+    mesh = pg.P2M(V, F, segs=S, domain_scale=1.25, domain_margin=0.05)
+    o = oracle.OracleMesh(V, F, segs=S, build_tables=False)
+    ref = o.bruteforce(q)
+    gpu = run(mesh, q)
+    s = pu.check(V, o.edges(), F, q, gpu, ref, pu.tolerance(V), f"random soup {seed}")
+    assert s["prim_exact"] > 0.98
+
+
 def test_parity_against_paper_method(pg):
     """The GPU agrees with the oracle's own P2M query (Alg. A.2) too, and the
     product builder's interception lists equal the oracle's."""
