@@ -426,6 +426,22 @@ def mixed_workload(mesh_level: int = 6, wire_level: int = 4, n_queries: int = 1_
                    meta={"segs": np.ascontiguousarray(segs, np.int32)})
 
 
+def high_valence_fan(n_rim: int = 120, seed: int = 7):
+    """A flat fan: an apex above the centre of n_rim nearly co-circular rim
+    vertices (radius and height jittered by 2e-5), one triangle per rim
+    side.  Every rim vertex is a Voronoi neighbour of the apex, so the
+    apex's cell has about n_rim + 2 faces: a stress case for bounded work
+    buffers (the builder's flooding hands such primitives to unbounded code).
+    Queries: none (tables-only workload); domain 1.5x the bbox."""
+    rng = np.random.default_rng(seed)
+    th = 2 * math.pi * np.arange(n_rim) / n_rim
+    r = 1 + rng.uniform(-2e-5, 2e-5, n_rim)
+    rim = np.stack([r * np.cos(th), r * np.sin(th), rng.uniform(-2e-5, 2e-5, n_rim)], 1)
+    v = np.concatenate([[[0.0, 0.0, 0.1]], rim], 0).astype(np.float32)
+    f = np.array([[0, 1 + i, 1 + (i + 1) % n_rim] for i in range(n_rim)], np.int32)
+    return Mesh(f"fan-{n_rim}", v, f, np.zeros((1, 3), np.float32), 1.5, 0.05, meta={})
+
+
 def batch_workload(n_meshes: int = 64, tri_range=(1e3, 5e5), query_range=(1e4, 2e6),
                    query_scale: float = 1.0):
     """64 meshes of uneven size: a coin picks a noisy icosphere (level

@@ -75,8 +75,11 @@ typedef struct {
                           and Region boxes, as a fraction of diag(D) (default 4e-6)        */
   int host_threads;    /* preprocessing threads, 0 = all cores (default 0)                 */
   int device_assist;   /* 1 = certify Voronoi cells on the GPU (float32 nearest-vertex
-                          proposals, exact searches decided in double precision; same
-                          tables as 0), 0 = CPU only (default 1; 0 works without a GPU) */
+                          proposals, exact searches decided in double precision),
+                          2 = that and the flooding (Alg. 1) on the GPU too (the same
+                          double-precision steps, no fused multiply-adds), 0 = CPU only.
+                          Every setting gives the same tables bit for bit (default 1;
+                          0 works without a GPU)                                       */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
 } p2m_build_opts;
 
@@ -346,6 +349,14 @@ p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges);
  * cells ms, inspection ms, certification rounds, certification queries,
  * degenerate faces. */
 p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]);
+
+/* How the flooding of a handle's build was split: out[0] = primitives
+ * flooded on the device (device_assist = 2), out[1] = flooded on the host by
+ * the bounded core shared with the device, out[2] = flooded on the host by
+ * the unbounded code (primitives whose polytopes exceed the core's fixed
+ * buffers, or whose cap loop needs the angular ordering).  All zero for a
+ * handle made by p2m_load. */
+p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]);
 
 /* The domain D (lo xyz, hi xyz) and delta of a handle. */
 p2m_status p2m_domain(const p2m_handle *h, float out[7]);

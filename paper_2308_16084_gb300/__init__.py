@@ -69,7 +69,10 @@ class P2M:
     ``P2M(verts, tris, domain_scale=10, domain_margin=0, delta_rel=4e-6,
     host_threads=0, device_assist=True, leaf_size=8)`` runs the paper's
     preprocessing (Alg. A.1) through ``p2m_build``.  ``verts`` (V,3) float32
-    and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors."""
+    and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors.
+    ``device_assist``: False/0 host only, True/1 Voronoi-cell certification
+    on the GPU, 2 the flooding (Alg. 1) on the GPU as well; every setting
+    gives the same tables."""
 
     def __init__(self, verts=None, tris=None, *, segs=None, domain_scale=10.0,
                  domain_margin=0.0, delta_rel=4e-6, host_threads=0, device_assist=True,
@@ -82,8 +85,11 @@ class P2M:
             F = np.ascontiguousarray(np.asarray(
                 np.zeros((0, 3)) if tris is None else tris, dtype=np.int32).reshape(-1, 3))
             desc = MeshDesc(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
-            opts = BuildOpts(domain_scale, domain_margin, delta_rel, host_threads,
-                             int(bool(device_assist)), leaf_size)
+            assist = int(device_assist)
+            if assist not in (0, 1, 2):
+                raise ValueError("device_assist must be 0, 1 or 2")
+            opts = BuildOpts(domain_scale, domain_margin, delta_rel, host_threads, assist,
+                             leaf_size)
             h = ctypes.c_void_p()
             if segs is None:
                 check(lib.p2m_build(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
@@ -125,6 +131,13 @@ class P2M:
                 "kd_leaves", "kd_depth", "neighbour_pairs", "inspections", "build_ms",
                 "cells_ms", "inspect_ms", "cert_rounds", "cert_queries", "n_degenerate"]
         return dict(zip(keys, list(out)))
+
+    def flood_stats(self):
+        """How the build's flooding was split: primitives flooded on the
+        device, by the host's bounded core, by its unbounded code."""
+        out = (ctypes.c_int64 * 3)()
+        check(lib.p2m_flood_stats(self._h, out), "p2m_flood_stats")
+        return {"device": out[0], "host_bounded": out[1], "host_unbounded": out[2]}
 
     def domain(self):
         out = (ctypes.c_float * 7)()

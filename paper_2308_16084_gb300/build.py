@@ -26,7 +26,7 @@ def _nvcc():
 def _sources():
     return {
         "kernels.cu": "cu", "certify.cu": "cu", "p2m_api.cu": "cu", "noalloc.cu": "cu",
-        "builder.cpp": "cpp",
+        "flood.cu": "cu-nofma", "builder.cpp": "cpp",
     }
 
 
@@ -50,9 +50,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src, kind in _sources().items():
         obj = os.path.join(OUT, src + ".o")
         path = os.path.join(CSRC, src)
-        if kind == "cu":
+        if kind.startswith("cu"):
+            # the device flooding must round every double operation on its
+            # own, as the host builder (-ffp-contract=off) does
+            nofma = ["-fmad=false"] if kind == "cu-nofma" else []
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-Xptxas", "-v" if verbose else "-O3", *extra, *inc, "-c", path, "-o", obj]
+                   "-Xptxas", "-v" if verbose else "-O3", *nofma, *extra, *inc, "-c", path,
+                   "-o", obj]
         else:
             cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off",
                    *inc, "-I", "/usr/local/cuda/include", "-c", path, "-o", obj]

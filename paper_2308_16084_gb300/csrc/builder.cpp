@@ -12,6 +12,7 @@
 // puts just outside the exact cell of its nearest vertex therefore still
 // finds its primitive in the list of the vertex the kernel picks.
 #include "builder.h"
+#include "flood_core.h"
 #include "quant.h"
 
 #include <algorithm>
@@ -22,28 +23,20 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <thread>
 
 namespace p2m {
 namespace {
 
 // ---------------------------------------------------------------- vectors
-struct V3 {
-  double x, y, z;
-};
-inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
-inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-inline V3 cross(V3 a, V3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-inline double len2(V3 a) { return dot(a, a); }
-inline bool lex_less(V3 a, V3 b) {
-  if (a.x != b.x) return a.x < b.x;
-  if (a.y != b.y) return a.y < b.y;
-  return a.z < b.z;
-}
+// double-precision 3-vectors and their operations: the ones the flooding
+// core shares with the device (flood_core.h)
+using V3 = fc::D3;
+using fc::cross;
+using fc::dot;
+using fc::len2;
+using fc::lex_less;
 
 // half-space n.x <= c, with the id of whatever generated it
 struct Plane {
@@ -121,14 +114,7 @@ void make_box(Poly &p, const double lo[3], const double hi[3]) {
   face({0, 0, -1}, -Z0, -6, {X0, Y0, Z0}, {X0, Y1, Z0}, {X1, Y1, Z0}, {X1, Y0, Z0});
 }
 
-inline V3 crossing(V3 a, V3 b, double sa, double sb) {
-  if (lex_less(b, a)) {
-    std::swap(a, b);
-    std::swap(sa, sb);
-  }
-  double t = sa / (sa - sb);
-  return a + t * (b - a);
-}
+using fc::crossing;
 
 // Cut `in` by h into `out`.  Returns false (and leaves out untouched) when
 // nothing lies beyond h.  An emptied polytope comes back with no faces.
@@ -546,10 +532,7 @@ void distinct_corners(const Poly &p, std::vector<V3> &out) {
 }
 
 // ------------------------------------------------------------- flooding
-struct Rec {
-  int32_t row, tid;  // table row (tree position) and typed id
-  float box[6];
-};
+using Rec = FloodRec;  // table row (tree position), typed id, Region box
 
 struct PrimGeom {  // what the filter needs about a primitive
   int type;        // 1 edge (line through a, unit u), 2 face (plane through a, unit u)
@@ -854,25 +837,35 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     std::vector<Rec> recs;
     std::vector<int64_t> seen;
     std::vector<int32_t> queue;
-    Poly A, B;
+    Poly A, B, C;
     CutScratch S;
     std::vector<double> gv;
-    int64_t inspections = 0;
+    std::unique_ptr<fc::Work> W{new fc::Work};
+    int64_t inspections = 0, bounded = 0, unbounded = 0;
   };
   std::vector<TLS> tls(threads);
   for (auto &x : tls) {
     x.seen.assign(nv, -1);
     x.queue.resize(nv + 3);
   }
-  const int64_t nprim = M.ne + M.nf;
-  parallel_for(nprim, threads, 32, [&](int64_t i, int t) {
-    TLS &X = tls[t];
+  // what the flooding of primitive i needs: its Space-perp half-spaces, the
+  // filter's geometry, its seeds (vertex ids) and typed id; false for a
+  // degenerate face, which is not flooded
+  struct PrimData {
     Plane perp[16];
-    int np_ = 0;
+    int np = 0;
     PrimGeom g;
-    int32_t seeds[3];
-    int ns;
-    int32_t tid;
+    int32_t seeds[3] = {-1, -1, -1};
+    int ns = 0;
+    int32_t tid = 0;
+  };
+  auto setup = [&](int64_t i, PrimData &P) -> bool {
+    Plane *perp = P.perp;
+    int &np_ = P.np;
+    PrimGeom &g = P.g;
+    int32_t *seeds = P.seeds;
+    int &ns = P.ns;
+    int32_t &tid = P.tid;
     if (i < M.ne) {
       int64_t e = i;
       V3 a = M.V[M.E[2 * e]], b = M.V[M.E[2 * e + 1]];
@@ -894,7 +887,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       tid = (int32_t)(1u << 30 | (uint32_t)e);
     } else {
       int64_t f = i - M.ne;
-      if (M.degenerate[f]) return;
+      if (M.degenerate[f]) return false;
       for (int k = 0; k < 3; ++k) {
         V3 m = face_inward(f, k);  // inside: m.(x - p_k) >= 0
         V3 pk = M.V[M.F[3 * f + k]];
@@ -907,6 +900,96 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       ns = 3;
       tid = (int32_t)(2u << 30 | (uint32_t)f);
     }
+    return true;
+  };
+  // ---- the flooding problem in flat arrays (fc::Flat), read alike by the
+  // host core, the device kernel and (cells only) the unbounded fallback:
+  // the widened cells, then every non-degenerate primitive
+  std::vector<int64_t> pt_off(nv + 1, 0), beg_off(nv + 1, 0);
+  for (int64_t p = 0; p < nv; ++p) {
+    pt_off[p + 1] = pt_off[p] + (int64_t)cell[p].pt.size();
+    beg_off[p + 1] = beg_off[p] + (int64_t)cell[p].beg.size();
+  }
+  std::vector<V3> cpt((size_t)pt_off[nv]);
+  std::vector<int32_t> cbeg((size_t)beg_off[nv]);
+  parallel_for(nv, threads, 1024, [&](int64_t p, int) {
+    Poly &c = cell[p];
+    std::copy(c.pt.begin(), c.pt.end(), cpt.begin() + pt_off[p]);
+    std::copy(c.beg.begin(), c.beg.end(), cbeg.begin() + beg_off[p]);
+    c = Poly();
+  });
+  cell.clear();
+  cell.shrink_to_fit();
+  const int64_t nprim = M.ne + M.nf;
+  std::vector<int32_t> prim_np(nprim, -1);  // -1: not flooded (degenerate face)
+  parallel_for(nprim, threads, 4096, [&](int64_t i, int) {
+    PrimData P;
+    if (setup(i, P)) prim_np[i] = P.np;
+  });
+  std::vector<int64_t> idx;  // problem index -> primitive
+  std::vector<int64_t> perp_off(1, 0);
+  for (int64_t i = 0; i < nprim; ++i)
+    if (prim_np[i] >= 0) {
+      idx.push_back(i);
+      perp_off.push_back(perp_off.back() + prim_np[i]);
+    }
+  std::vector<int32_t>().swap(prim_np);
+  const int64_t nk = (int64_t)idx.size();
+  std::vector<double> perp(4 * (size_t)perp_off[nk]), g(6 * (size_t)nk);
+  std::vector<int32_t> gtype(nk), srow(3 * (size_t)nk), svid(3 * (size_t)nk), tids(nk);
+  parallel_for(nk, threads, 4096, [&](int64_t k, int) {
+    PrimData P;
+    setup(idx[k], P);
+    for (int j = 0; j < P.np; ++j) {
+      double *h = &perp[4 * (size_t)(perp_off[k] + j)];
+      h[0] = P.perp[j].n.x;
+      h[1] = P.perp[j].n.y;
+      h[2] = P.perp[j].n.z;
+      h[3] = P.perp[j].c;
+    }
+    gtype[k] = P.g.type;
+    const double gg[6] = {P.g.a.x, P.g.a.y, P.g.a.z, P.g.u.x, P.g.u.y, P.g.u.z};
+    std::copy(gg, gg + 6, g.begin() + 6 * k);
+    for (int j = 0; j < 3; ++j) {
+      svid[3 * k + j] = j < P.ns ? P.seeds[j] : -1;
+      srow[3 * k + j] = j < P.ns ? out.pos_of_vertex[P.seeds[j]] : -1;
+    }
+    tids[k] = P.tid;
+  });
+  fc::Flat fl;
+  fl.pt_off = pt_off.data();
+  fl.pt = cpt.data();
+  fl.beg_off = beg_off.data();
+  fl.beg = cbeg.data();
+  fl.pos = T.P.data();
+  fl.vids = T.order.data();
+  fl.nbo = out.nb_off.data();
+  fl.nbs = out.nb.data();
+  fl.perp_off = perp_off.data();
+  fl.perp = perp.data();
+  fl.gtype = gtype.data();
+  fl.g = g.data();
+  fl.seed_row = srow.data();
+  fl.seed_vid = svid.data();
+  fl.tid = tids.data();
+  // row p's cell as a Poly, for the unbounded fallback (the planes of its
+  // faces are not needed by the flooding, only their loops)
+  auto cell_poly = [&](int64_t p, Poly &c) {
+    c.pt.assign(cpt.begin() + pt_off[p], cpt.begin() + pt_off[p + 1]);
+    c.beg.assign(cbeg.begin() + beg_off[p], cbeg.begin() + beg_off[p + 1]);
+    c.pl.assign(c.beg.size() - 1, Plane{{0, 0, 0}, 0, -1});
+  };
+
+  // the unbounded host flooding of a primitive the shared core
+  // (flood_core.h) gives up: the same steps on growable buffers, with the cap
+  // loop ordered by angle where it cannot be chained; stamp marks its visits
+  auto flood_unbounded = [&](int64_t stamp, const PrimData &P, TLS &X) {
+    const Plane *perp = P.perp;
+    const int np_ = P.np;
+    const PrimGeom &g = P.g;
+    const int32_t *seeds = P.seeds;
+    const int ns = P.ns;
+    const int32_t tid = P.tid;
     auto gval = [&](V3 x, V3 pv) {
       V3 w = x - g.a;
       double s = dot(w, g.u);
@@ -916,7 +999,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     int64_t head = 0, tail = 0;
     for (int s = 0; s < ns; ++s) {
       int64_t p = out.pos_of_vertex[seeds[s]];
-      X.seen[p] = i;
+      X.seen[p] = stamp;
       X.queue[tail++] = (int32_t)p;
     }
     while (head < tail) {
@@ -926,7 +1009,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       // leaves every point of the cell beyond it empties the result whatever
       // the order of the cuts (later corners are convex combinations of the
       // cell's), so that case is settled before any cut is made.
-      const Poly *cur = &cell[p];
+      cell_poly(p, X.C);
+      const Poly *cur = &X.C;
       bool emptied = false;
       for (int j = 0; j < np_ && !emptied; ++j) {
         bool all_beyond = true;
@@ -1020,20 +1104,113 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       }
       X.recs.push_back(r);
       for (int32_t w : nbr[p])
-        if (X.seen[w] != i) {
-          X.seen[w] = i;
+        if (X.seen[w] != stamp) {
+          X.seen[w] = stamp;
           X.queue[tail++] = w;
         }
     }
+  };
+  auto prim_of_tid = [&](int32_t tid) -> int64_t {
+    const int64_t id = tid & ((1 << 30) - 1);
+    return ((uint32_t)tid >> 30) == 1 ? id : M.ne + id;
+  };
+
+  // on the device service, when asked; the host floods what it gives up
+  std::vector<uint8_t> host_todo;  // empty: the host floods everything
+  int64_t n_device = 0;
+  if (prm.device_flood && nearest && nk > 0) {
+    FloodProblem pb;
+    pb.nv = nv;
+    pb.n = nk;
+    pb.cell_pt_off = pt_off.data();
+    pb.cell_pt = &cpt.data()->x;
+    pb.cell_beg_off = beg_off.data();
+    pb.cell_beg = cbeg.data();
+    pb.pv = &T.P.data()->x;
+    pb.vid = T.order.data();
+    pb.nb_off = out.nb_off.data();
+    pb.nb = out.nb.data();
+    pb.perp_off = perp_off.data();
+    pb.perp = perp.data();
+    pb.gtype = gtype.data();
+    pb.g = g.data();
+    pb.seed_row = srow.data();
+    pb.seed_vid = svid.data();
+    pb.tid = tids.data();
+    pb.eps = eps;
+    pb.delta = delta;
+    pb.eta = eta;
+    std::vector<FloodRec> drec;
+    std::vector<uint8_t> gave;
+    int64_t dinsp = 0;
+    if (nearest->flood(pb, drec, gave, dinsp) && (int64_t)gave.size() == nk) {
+      host_todo.swap(gave);
+      std::vector<uint8_t> prim_gave(nprim, 0);
+      for (int64_t k = 0; k < nk; ++k) {
+        if (host_todo[k]) prim_gave[idx[k]] = 1;
+        else ++n_device;
+      }
+      for (const FloodRec &r : drec) {
+        const int64_t pi = prim_of_tid(r.tid);
+        if (r.row >= 0 && r.row < nv && pi >= 0 && pi < nprim && !prim_gave[pi])
+          tls[0].recs.push_back(r);
+      }
+      tls[0].inspections += dinsp;
+    }
+  }
+
+  // the host side of the shared core
+  struct HostEnv : fc::Flat {
+    int64_t *seen;
+    int64_t stamp;
+    std::vector<Rec> *recs;
+    void mark_seed(int32_t p) { seen[p] = stamp; }
+    bool mark(int32_t w, const int32_t *, int64_t) {
+      if (seen[w] == stamp) return false;
+      seen[w] = stamp;
+      return true;
+    }
+    void emit(int32_t row, int32_t tid, const float box[6]) {
+      Rec r;
+      r.row = row;
+      r.tid = tid;
+      for (int d = 0; d < 6; ++d) r.box[d] = box[d];
+      recs->push_back(r);
+    }
+  };
+  parallel_for(nk, threads, 32, [&](int64_t k, int t) {
+    if (!host_todo.empty() && !host_todo[k]) return;
+    TLS &X = tls[t];
+    HostEnv env;
+    static_cast<fc::Flat &>(env) = fl;
+    env.seen = X.seen.data();
+    env.stamp = 2 * k;
+    env.recs = &X.recs;
+    const size_t r0 = X.recs.size();
+    int64_t insp = 0;
+    fc::Prim fp;
+    if (fl.load(k, fp) && fc::flood_prim(fp, eps, delta, eta, env, *X.W, X.queue.data(),
+                                         (int64_t)X.queue.size(), insp) == 0) {
+      X.inspections += insp;
+      ++X.bounded;
+      return;
+    }
+    X.recs.resize(r0);
+    ++X.unbounded;
+    PrimData P;
+    setup(idx[k], P);
+    flood_unbounded(2 * k + 1, P, X);
   });
-  cell.clear();
-  cell.shrink_to_fit();
 
   // ---- pack the CSR table in row (tree) order
   int64_t total = 0, insp = 0;
+  out.flood_device = n_device;
+  out.flood_bounded = out.flood_unbounded = 0;
   for (auto &x : tls) {
     total += (int64_t)x.recs.size();
     insp += x.inspections;
+    out.flood_bounded += x.bounded;
+    out.flood_unbounded += x.unbounded;
   }
   if (total >= ((int64_t)1 << 32)) {
     err = "interception table exceeds 2^32 entries";

@@ -20,6 +20,45 @@ struct BuildParams {
   double delta_rel = 4e-6;
   int threads = 0;
   int leaf_size = 8;
+  bool device_flood = false;  // flood on the nearest service when it offers that
+};
+
+// The flooding inspection (Alg. 1) of a set of primitives, for a device
+// service.  Host arrays; rows are KD-tree positions.
+struct FloodProblem {
+  int64_t nv = 0;  // rows
+  int64_t n = 0;   // primitives
+  // widened cells: the points of row p's cell are
+  // cell_pt[cell_pt_off[p] .. cell_pt_off[p+1]) (3 doubles each); its nf
+  // face loops start at the offsets cell_beg[cell_beg_off[p] ..
+  // cell_beg_off[p+1]) relative to its first point (nf + 1 of them, the
+  // last one the point count)
+  const int64_t *cell_pt_off = nullptr;
+  const double *cell_pt = nullptr;
+  const int64_t *cell_beg_off = nullptr;
+  const int32_t *cell_beg = nullptr;
+  const double *pv = nullptr;      // nv * 3 vertex positions
+  const int32_t *vid = nullptr;    // nv vertex ids
+  const uint32_t *nb_off = nullptr;  // nv + 1, Voronoi neighbours (rows)
+  const uint32_t *nb = nullptr;
+  // primitive i: Space-perp half-spaces perp[perp_off[i] .. perp_off[i+1])
+  // (n.x <= c as 4 doubles n, c; at most 16), the filter's geometry g[6i..]
+  // (a, unit u; gtype 1 = line, 2 = plane), its seeds (2 for an edge, 3 for
+  // a face: rows and vertex ids) and its typed id
+  const int64_t *perp_off = nullptr;
+  const double *perp = nullptr;
+  const int32_t *gtype = nullptr;
+  const double *g = nullptr;
+  const int32_t *seed_row = nullptr;  // n * 3
+  const int32_t *seed_vid = nullptr;  // n * 3
+  const int32_t *tid = nullptr;
+  double eps = 0, delta = 0, eta = 0;
+};
+
+// one interception-table entry: table row, typed id, Region box lo, hi
+struct FloodRec {
+  int32_t row, tid;
+  float box[6];
 };
 
 // Batched nearest-vertex service used to certify Voronoi cells.  query()
@@ -33,6 +72,15 @@ struct NearestService {
   // -2 where the service gave up (the host searches); false = unavailable
   virtual bool within(const double *xyz, const double *r2, int64_t n, int64_t *out_pos) {
     (void)xyz, (void)r2, (void)n, (void)out_pos;
+    return false;
+  }
+  // the flooding of every primitive of pb: the records of the primitives
+  // it finished (in any order), gave_up[i] = 1 for those it did not (their
+  // records are left out: the host floods them), and the vertices inspected
+  // for the finished ones; false = unavailable (the host floods everything)
+  virtual bool flood(const FloodProblem &pb, std::vector<FloodRec> &out,
+                     std::vector<uint8_t> &gave_up, int64_t &inspections) {
+    (void)pb, (void)out, (void)gave_up, (void)inspections;
     return false;
   }
 };
@@ -90,6 +138,9 @@ struct Layout {
   // statistics
   int64_t n_entries = 0, max_list = 0, neighbour_pairs = 0, inspections = 0;
   int64_t cert_rounds = 0, cert_queries = 0, n_degenerate = 0;
+  // primitives flooded on the device, by the host's bounded core and by its
+  // unbounded code (the ones the core gave up)
+  int64_t flood_device = 0, flood_bounded = 0, flood_unbounded = 0;
   double ms_total = 0, ms_cells = 0, ms_inspect = 0;
 };
 

@@ -17,6 +17,7 @@
 #include "../../include/p2m.h"
 #include "builder.h"
 #include "certify.h"
+#include "flood.h"
 #include "quant.h"
 #include "kernels.h"
 #include "quant.h"
@@ -273,6 +274,10 @@ struct DeviceNearest : p2m::NearestService {
     if (!ok) cudaGetLastError();
     return ok;
   }
+  bool flood(const p2m::FloodProblem &pb, std::vector<p2m::FloodRec> &out,
+             std::vector<uint8_t> &gave_up, int64_t &inspections) override {
+    return p2m::flood_on_device(pb, out, gave_up, inspections);
+  }
 };
 
 // the builder fills the handle's own layout; once its KD tree exists the
@@ -336,7 +341,7 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
   p2m_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.domain_scale > 0.f) || !(o.domain_margin >= 0.f) || !(o.delta_rel >= 0.f) ||
-      o.leaf_size < 2 || o.leaf_size > 32)
+      o.leaf_size < 2 || o.leaf_size > 32 || o.device_assist < 0 || o.device_assist > 2)
     return P2M_ERR_INVALID_ARG;
   std::unique_ptr<p2m_handle> h(new (std::nothrow) p2m_handle());
   if (!h) return P2M_ERR_OOM;
@@ -349,6 +354,7 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
   prm.delta_rel = o.delta_rel;
   prm.threads = o.host_threads;
   prm.leaf_size = o.leaf_size;
+  prm.device_flood = o.device_assist == 2;
   DeviceNearest dn(h.get());
   const bool assist = o.device_assist && h->device >= 0;
   std::string err;
@@ -707,6 +713,14 @@ p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]) {
   out[13] = L.cert_rounds;
   out[14] = L.cert_queries;
   out[15] = L.n_degenerate;
+  return P2M_OK;
+}
+
+p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]) {
+  if (!h || !out) return P2M_ERR_INVALID_ARG;
+  out[0] = h->L.flood_device;
+  out[1] = h->L.flood_bounded;
+  out[2] = h->L.flood_unbounded;
   return P2M_OK;
 }
 

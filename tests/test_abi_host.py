@@ -102,6 +102,35 @@ def test_builder_tables_equal_oracle_tables_on_random_inputs(pg, seed):
     _check_tables(pg, m)
 
 
+def test_builder_tables_equal_oracle_tables_on_a_high_valence_fan(pg):
+    """A vertex whose Voronoi cell has ~122 faces: the primitives that reach
+    it overflow the bounded flooding core's buffers and are flooded by the
+    unbounded host code; the rest stay on the core.  The table is the
+    oracle's either way."""
+    m = dg.high_valence_fan(120)
+    _check_tables(pg, m)
+    fs = _host(pg, m).flood_stats()
+    assert fs["device"] == 0
+    assert fs["host_bounded"] > 0 and fs["host_unbounded"] > 0
+    assert fs["host_bounded"] + fs["host_unbounded"] == 3 * 120
+
+
+def test_flood_stats_on_a_regular_mesh(pg):
+    """Every edge and face of a regular mesh is flooded by the bounded core
+    (nothing overflows it), and a host-only build floods nothing on the
+    device."""
+    m = dg.workload(0, n_queries=10)
+    st = _host(pg, m).flood_stats()
+    assert st == {"device": 0, "host_bounded": 1920 + 1280, "host_unbounded": 0}
+
+
+def test_device_assist_values(pg):
+    V, F = dg.octahedron()
+    for bad in (-1, 3):
+        with pytest.raises(ValueError):
+            pg.P2M(V.astype(np.float32), F, device_assist=bad)
+
+
 def test_invalid_segments_return_status(pg):
     V, F = dg.octahedron()
     for segs in ([[0, 0]], [[0, 99]]):
