@@ -1178,6 +1178,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       recs->push_back(r);
     }
   };
+  // P2M_FLOOD_UNBOUNDED=1 floods every primitive with the unbounded code
+  // (a check that both host paths build the same layout)
+  const char *fu = std::getenv("P2M_FLOOD_UNBOUNDED");
+  const bool only_unbounded = fu && std::atoi(fu) != 0;
   parallel_for(nk, threads, 32, [&](int64_t k, int t) {
     if (!host_todo.empty() && !host_todo[k]) return;
     TLS &X = tls[t];
@@ -1189,8 +1193,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     const size_t r0 = X.recs.size();
     int64_t insp = 0;
     fc::Prim fp;
-    if (fl.load(k, fp) && fc::flood_prim(fp, eps, delta, eta, env, *X.W, X.queue.data(),
-                                         (int64_t)X.queue.size(), insp) == 0) {
+    if (!only_unbounded && fl.load(k, fp) &&
+        fc::flood_prim(fp, eps, delta, eta, env, *X.W, X.queue.data(), (int64_t)X.queue.size(),
+                       insp) == 0) {
       X.inspections += insp;
       ++X.bounded;
       return;

@@ -4,8 +4,9 @@
 // vertices (perfect binary tree, child boxes in the parent), the CSR
 // interception table in KD-tree row order with one Region box per entry,
 // and per-primitive geometry records.  Runs on the host with std::thread;
-// the Voronoi-cell certification can hand its nearest-vertex queries to a
-// device kernel through the NearestOracle interface.
+// the Voronoi-cell certification can hand its nearest-vertex queries, and
+// the flooding its primitives, to device kernels through the NearestService
+// interface.
 #pragma once
 
 #include <cstdint>

@@ -274,3 +274,24 @@ def test_tuning_fields_are_validated(pg):
             h.tuning = bad
         assert e.value.code == 1
         assert h.tuning["sort_key"] == 1 and h.tuning["block_threads"] == 128
+
+
+@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan"])
+def test_both_host_flooding_paths_build_the_same_layout(pg, name, monkeypatch, tmp_path):
+    """The bounded flooding core (shared with the device) and the unbounded
+    host code it hands overflowing primitives to compute the same records:
+    forcing every primitive through the unbounded code
+    (P2M_FLOOD_UNBOUNDED=1) saves the same layout file byte for byte."""
+    m = {"sphere": lambda: dg.workload(3, n_queries=10, level=3),
+         "soup": lambda: dg.soup_workload("penetrating", level=2, n_queries=10),
+         "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10),
+         "fan": lambda: dg.high_valence_fan(120)}[name]()
+    a = _host(pg, m)
+    monkeypatch.setenv("P2M_FLOOD_UNBOUNDED", "1")
+    b = _host(pg, m)
+    fa, fb = a.flood_stats(), b.flood_stats()
+    assert fb["host_bounded"] == 0
+    assert fa["host_bounded"] + fa["host_unbounded"] == fb["host_unbounded"]
+    a.save(str(tmp_path / "a.p2m"))
+    b.save(str(tmp_path / "b.p2m"))
+    assert (tmp_path / "a.p2m").read_bytes() == (tmp_path / "b.p2m").read_bytes()
