@@ -1,13 +1,15 @@
 // flood.cu -- the builder's flooding inspection (Alg. 1) on the device.
 //
-// One thread per primitive runs the core shared with the host builder
-// (flood_core.h): breadth-first over Voronoi neighbours, the cut of each
-// visited cell by the primitive's Space-perp half-spaces, the filter of
-// Thm. 5/6 and the Region box of Sec. 4.6.  Its work polytopes live in
-// local memory; records are appended to one array through an atomic counter
-// and the host sorts them into rows as it does its own.  This translation
-// unit is compiled with -fmad=false: every double operation rounds on its
-// own, as on the host.
+// A persistent kernel: one block of kFloodWarps warps per SM, each warp
+// taking primitives from an atomic counter and flooding them with its 32
+// lanes (flood_warp.h: breadth-first over Voronoi neighbours, the cut of
+// each visited cell by the primitive's Space-perp half-spaces, the filter of
+// Thm. 5/6 and the Region box of Sec. 4.6, the per-point work spread over
+// the lanes).  A warp's work polytopes and queue live in shared memory;
+// records are appended to one array through an atomic counter and the host
+// sorts them into rows as it does its own.  This translation unit is
+// compiled with -fmad=false: every double operation rounds on its own, as
+// on the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,25 +18,19 @@
 
 #include "flood.h"
 #include "flood_core.h"
+#include "flood_warp.h"
 
 namespace p2m {
 namespace {
 
-constexpr int kQueue = 1024;  // vertices one primitive may visit on the device
+constexpr int kFloodWarps = 8;  // warps per block, one block per SM
 
-// the device side of the shared core: membership by a scan of the queue
-// (every vertex seen so far is in it), records through an atomic counter
+// the device side of the flat problem: records through an atomic counter
 struct DevEnv : fc::Flat {
   FloodRec *rec;
   unsigned long long *count;
   unsigned long long cap;
 
-  __device__ void mark_seed(int32_t) {}
-  __device__ bool mark(int32_t w, const int32_t *queue, int64_t tail) const {
-    for (int64_t k = 0; k < tail; ++k)
-      if (queue[k] == w) return false;
-    return true;
-  }
   __device__ void emit(int32_t row, int32_t tid, const float box[6]) {
     const unsigned long long slot = atomicAdd(count, 1ull);
     if (slot < cap) {
@@ -47,19 +43,25 @@ struct DevEnv : fc::Flat {
   }
 };
 
-__global__ void __launch_bounds__(128) k_flood(DevEnv env, int64_t n, double eps, double delta,
-                                               double eta, uint8_t *gave_up,
-                                               unsigned long long *insp_total) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  fc::Prim P;
-  fc::Work W;
-  int32_t queue[kQueue];
-  int64_t insp = 0;
-  const int r = env.load(i, P) ? fc::flood_prim(P, eps, delta, eta, env, W, queue, kQueue, insp)
-                               : 1;
-  gave_up[i] = (uint8_t)(r != 0);
-  if (r == 0) atomicAdd(insp_total, (unsigned long long)insp);
+__global__ void __launch_bounds__(kFloodWarps * 32, 1)
+    k_flood_warp(DevEnv env, int64_t n, double eps, double delta, double eta, uint8_t *gave_up,
+                 unsigned long long *insp_total, unsigned long long *next) {
+  extern __shared__ __align__(16) unsigned char flood_smem[];
+  fw::WarpWork &S = reinterpret_cast<fw::WarpWork *>(flood_smem)[threadIdx.x >> 5];
+  DevEnv e = env;
+  for (;;) {
+    P2M_LANE0 { S.item = (int64_t)atomicAdd(next, 1ull); }
+    P2M_SYNC;
+    const int64_t k = S.item;
+    P2M_SYNC;
+    if (k >= n) return;
+    int64_t insp = 0;
+    const int r = fw::flood_warp(S, e, k, eps, delta, eta, insp);
+    P2M_LANE0 {
+      gave_up[k] = (uint8_t)(r != 0);
+      if (r == 0) atomicAdd(insp_total, (unsigned long long)insp);
+    }
+  }
 }
 
 // device buffers of one call, freed together
@@ -96,11 +98,12 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
   const int64_t nv = pb.nv, n = pb.n;
   const int64_t npt = pb.cell_pt_off[nv], nbeg = pb.cell_beg_off[nv];
   const int64_t nnb = pb.nb_off[nv], nperp = pb.perp_off[n];
-  // the kernel's work polytopes take ~39 KB of stack a thread; the driver
-  // grows the per-thread stack for the launch and keeps it, so the previous
-  // limit is put back afterwards to release that reservation
-  size_t stack0 = 0;
-  cudaError_t e = cudaDeviceGetLimit(&stack0, cudaLimitStackSize);
+  const size_t smem = kFloodWarps * sizeof(fw::WarpWork);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_flood_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   {
     Bufs B;
     DevEnv env;
@@ -120,21 +123,23 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     env.seed_vid = B.put(pb.seed_vid, 3 * (size_t)n, e);
     env.tid = B.put(pb.tid, (size_t)n, e);
     uint8_t *dgave = B.get<uint8_t>((size_t)n, e);
-    unsigned long long *cnt = B.get<unsigned long long>(2, e);  // records, inspections
-    // room for 16 records a primitive; a second run with the exact count
-    // when that is not enough (the run is deterministic in its record set)
-    unsigned long long cap = (unsigned long long)std::max<int64_t>(1 << 20, 16 * n);
+    // records, inspections, work counter
+    unsigned long long *cnt = B.get<unsigned long long>(3, e);
+    // room for 64 records a primitive (workload meshes take 15 to 45); a
+    // second run with the exact count when that is not enough (the record
+    // set of a run is deterministic)
+    unsigned long long cap = (unsigned long long)std::max<int64_t>(1 << 20, 64 * n);
     unsigned long long h_cnt[2] = {0, 0};
     for (int attempt = 0; attempt < 2 && e == cudaSuccess; ++attempt) {
       FloodRec *drec = B.get<FloodRec>((size_t)cap, e);
       if (e != cudaSuccess) break;
-      e = cudaMemset(cnt, 0, 2 * sizeof(unsigned long long));
+      e = cudaMemset(cnt, 0, 3 * sizeof(unsigned long long));
       if (e != cudaSuccess) break;
       env.rec = drec;
       env.count = cnt;
       env.cap = cap;
-      const unsigned blocks = (unsigned)((n + 127) / 128);
-      k_flood<<<blocks, 128>>>(env, n, pb.eps, pb.delta, pb.eta, dgave, cnt + 1);
+      k_flood_warp<<<sms, kFloodWarps * 32, smem>>>(env, n, pb.eps, pb.delta, pb.eta, dgave,
+                                                     cnt + 1, cnt + 2);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
       if (e == cudaSuccess) e = cudaMemcpy(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost);
@@ -153,10 +158,6 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     }
     if (e == cudaSuccess && gave_up.size() != (size_t)n) e = cudaErrorUnknown;
     inspections = (int64_t)h_cnt[1];
-  }
-  if (stack0 > 0) {
-    const cudaError_t e2 = cudaDeviceSetLimit(cudaLimitStackSize, stack0);
-    if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

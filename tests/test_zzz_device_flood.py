@@ -1,9 +1,10 @@
 """The builder's flooding inspection (Alg. 1) on the device
-(device_assist=2): one thread per primitive runs the core the host builder
-uses, in double precision without fused multiply-adds, and hands back the
-primitives its fixed buffers cannot hold.  The layout it builds is the host
-flooding's byte for byte: both builds are saved and the files compared (they
-hold every table, box code, neighbour list and the inspection count)."""
+(device_assist=2): each warp floods one primitive at a time with the steps
+of the core the host builder uses, in double precision without fused
+multiply-adds, and hands back the primitives its shared-memory buffers
+cannot hold.  The layout it builds is the host flooding's byte for byte:
+both builds are saved and the files compared (they hold every table, box
+code, neighbour list and the inspection count)."""
 import os
 import tempfile
 
