@@ -76,8 +76,9 @@ typedef struct {
   int host_threads;    /* preprocessing threads, 0 = all cores (default 0)                 */
   int device_assist;   /* 1 = certify Voronoi cells on the GPU (float32 nearest-vertex
                           proposals, exact searches decided in double precision),
-                          2 = that and the flooding (Alg. 1) on the GPU too (the same
-                          double-precision steps, no fused multiply-adds), 0 = CPU only.
+                          2 = that and the flooding (Alg. 1) on the GPU too (one warp per
+                          primitive, the same double-precision steps, no fused
+                          multiply-adds), 0 = CPU only.
                           Every setting gives the same tables bit for bit (default 1;
                           0 works without a GPU)                                       */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */

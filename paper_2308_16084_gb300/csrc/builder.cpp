@@ -1115,6 +1115,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     return ((uint32_t)tid >> 30) == 1 ? id : M.ne + id;
   };
 
+  const double t_flat = now_ms();
+  if (trace) std::fprintf(stderr, "p2m build: flooding problem %.0f ms\n", t_flat - t_flood);
   // on the device service, when asked; the host floods what it gives up
   std::vector<uint8_t> host_todo;  // empty: the host floods everything
   int64_t n_device = 0;
@@ -1178,6 +1180,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       recs->push_back(r);
     }
   };
+  const double t_host_flood = now_ms();
+  if (trace && !host_todo.empty())
+    std::fprintf(stderr, "p2m build: device flooding %.0f ms (%lld primitives, %lld handed back)\n",
+                 t_host_flood - t_flat, (long long)n_device, (long long)(nk - n_device));
   // P2M_FLOOD_UNBOUNDED=1 floods every primitive with the unbounded code
   // (a check that both host paths build the same layout)
   const char *fu = std::getenv("P2M_FLOOD_UNBOUNDED");
@@ -1207,6 +1213,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     flood_unbounded(2 * k + 1, P, X);
   });
 
+  if (trace)
+    std::fprintf(stderr, "p2m build: host flooding %.0f ms\n", now_ms() - t_host_flood);
   // ---- pack the CSR table in row (tree) order
   int64_t total = 0, insp = 0;
   out.flood_device = n_device;

@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstdint>
 #include <vector>
 
@@ -98,6 +101,13 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
   const int64_t nv = pb.nv, n = pb.n;
   const int64_t npt = pb.cell_pt_off[nv], nbeg = pb.cell_beg_off[nv];
   const int64_t nnb = pb.nb_off[nv], nperp = pb.perp_off[n];
+  // optional timing of the steps on stderr (P2M_BUILD_TRACE=1)
+  const bool trace = std::getenv("P2M_BUILD_TRACE") != nullptr;
+  auto ms = [] {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+  };
+  double t0 = ms(), t1 = t0, t2 = t0;
   const size_t smem = kFloodWarps * sizeof(fw::WarpWork);
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -138,10 +148,12 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
       env.rec = drec;
       env.count = cnt;
       env.cap = cap;
+      t1 = ms();
       k_flood_warp<<<sms, kFloodWarps * 32, smem>>>(env, n, pb.eps, pb.delta, pb.eta, dgave,
                                                      cnt + 1, cnt + 2);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      t2 = ms();
       if (e == cudaSuccess) e = cudaMemcpy(h_cnt, cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) break;
       if (h_cnt[0] <= cap) {
@@ -158,6 +170,11 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     }
     if (e == cudaSuccess && gave_up.size() != (size_t)n) e = cudaErrorUnknown;
     inspections = (int64_t)h_cnt[1];
+    if (trace)
+      std::fprintf(stderr,
+                   "p2m build:   device flooding: upload %.0f ms, kernel %.0f ms, download %.0f ms "
+                   "(%llu records)\n",
+                   t1 - t0, t2 - t1, ms() - t2, h_cnt[0]);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
