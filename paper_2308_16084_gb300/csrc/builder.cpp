@@ -1120,6 +1120,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   // on the device service, when asked; the host floods what it gives up
   std::vector<uint8_t> host_todo;  // empty: the host floods everything
   int64_t n_device = 0;
+  std::vector<Rec> drec;  // the device's records (row -1: dropped)
   if (prm.device_flood && nearest && nk > 0) {
     FloodProblem pb;
     pb.nv = nv;
@@ -1142,7 +1143,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     pb.eps = eps;
     pb.delta = delta;
     pb.eta = eta;
-    std::vector<FloodRec> drec;
     std::vector<uint8_t> gave;
     int64_t dinsp = 0;
     if (nearest->flood(pb, drec, gave, dinsp) && (int64_t)gave.size() == nk) {
@@ -1152,12 +1152,18 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
         if (host_todo[k]) prim_gave[idx[k]] = 1;
         else ++n_device;
       }
-      for (const FloodRec &r : drec) {
-        const int64_t pi = prim_of_tid(r.tid);
-        if (r.row >= 0 && r.row < nv && pi >= 0 && pi < nprim && !prim_gave[pi])
-          tls[0].recs.push_back(r);
-      }
+      // the records of the primitives handed back are the host's to make
+      const int64_t nd = (int64_t)drec.size();
+      parallel_for((nd + 4095) / 4096, threads, 16, [&](int64_t c, int) {
+        for (int64_t j = 4096 * c; j < std::min(nd, 4096 * (c + 1)); ++j) {
+          Rec &r = drec[j];
+          const int64_t pi = prim_of_tid(r.tid);
+          if (!(r.row >= 0 && r.row < nv && pi >= 0 && pi < nprim && !prim_gave[pi])) r.row = -1;
+        }
+      });
       tls[0].inspections += dinsp;
+    } else {
+      drec.clear();
     }
   }
 
@@ -1213,35 +1219,54 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     flood_unbounded(2 * k + 1, P, X);
   });
 
-  if (trace)
-    std::fprintf(stderr, "p2m build: host flooding %.0f ms\n", now_ms() - t_host_flood);
+  const double t_pack = now_ms();
+  if (trace) std::fprintf(stderr, "p2m build: host flooding %.0f ms\n", t_pack - t_host_flood);
   // ---- pack the CSR table in row (tree) order
   int64_t total = 0, insp = 0;
   out.flood_device = n_device;
   out.flood_bounded = out.flood_unbounded = 0;
   for (auto &x : tls) {
-    total += (int64_t)x.recs.size();
     insp += x.inspections;
     out.flood_bounded += x.bounded;
     out.flood_unbounded += x.unbounded;
   }
-  if (total >= ((int64_t)1 << 32)) {
-    err = "interception table exceeds 2^32 entries";
-    return 9;
-  }
+  // bucket the records by row: counts and then positions taken with atomic
+  // increments, in parallel over blocks of every record list (the order
+  // inside a row is fixed by the sort below, a total order)
+  std::vector<std::vector<Rec> *> srcs;
+  for (auto &x : tls) srcs.push_back(&x.recs);
+  srcs.push_back(&drec);
+  std::vector<std::pair<int, int64_t>> blocks;  // (list, first record)
+  for (size_t q = 0; q < srcs.size(); ++q)
+    for (int64_t j = 0; j < (int64_t)srcs[q]->size(); j += 1 << 16) blocks.push_back({(int)q, j});
+  auto for_records = [&](auto &&fn) {
+    parallel_for((int64_t)blocks.size(), threads, 1, [&](int64_t bi, int) {
+      const std::vector<Rec> &v = *srcs[blocks[bi].first];
+      const int64_t j0 = blocks[bi].second, j1 = std::min<int64_t>(j0 + (1 << 16), v.size());
+      for (int64_t j = j0; j < j1; ++j)
+        if (v[j].row >= 0) fn(v[j]);
+    });
+  };
   out.row_off.assign(nv + 1, 0);
-  for (auto &x : tls)
-    for (const Rec &r : x.recs) out.row_off[r.row + 1]++;
-  for (int64_t p = 0; p < nv; ++p) out.row_off[p + 1] += out.row_off[p];
-  std::vector<Rec> all(total);
+  for_records([&](const Rec &r) { __atomic_fetch_add(&out.row_off[r.row + 1], 1u, __ATOMIC_RELAXED); });
+  total = 0;
+  for (int64_t p = 0; p < nv; ++p) {
+    total += out.row_off[p + 1];
+    if (total >= ((int64_t)1 << 32)) {
+      err = "interception table exceeds 2^32 entries";
+      return 9;
+    }
+    out.row_off[p + 1] += out.row_off[p];
+  }
+  std::unique_ptr<Rec[]> all(new Rec[total > 0 ? total : 1]);  // filled below, no zeroing
   {
     std::vector<uint32_t> fill(out.row_off.begin(), out.row_off.end() - 1);
-    for (auto &x : tls) {
-      for (const Rec &r : x.recs) all[fill[r.row]++] = r;
-      std::vector<Rec>().swap(x.recs);
-    }
+    for_records([&](const Rec &r) {
+      all[__atomic_fetch_add(&fill[r.row], 1u, __ATOMIC_RELAXED)] = r;
+    });
   }
   tls.clear();
+  std::vector<Rec>().swap(drec);
   // spatial order inside every row (Morton code of the box centre within the
   // union of the row's boxes), then chunks of kChunk consecutive entries
   auto spread = [](uint32_t v) {
@@ -1252,11 +1277,15 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     v = (v | (v << 2)) & 0x09249249;
     return v;
   };
-  parallel_for(nv, threads, 1024, [&](int64_t p, int) {
-    auto b = all.begin() + out.row_off[p], e = all.begin() + out.row_off[p + 1];
+  // per thread: (Morton key << 32 | typed id, position) of a row, and the
+  // row in that order (typed ids are distinct in a row: a total order)
+  std::vector<std::vector<std::pair<uint64_t, uint32_t>>> sort_keys(threads);
+  std::vector<std::vector<Rec>> sort_tmp(threads);
+  parallel_for(nv, threads, 1024, [&](int64_t p, int t) {
+    Rec *b = all.get() + out.row_off[p], *e = all.get() + out.row_off[p + 1];
     if (e - b < 2) return;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (auto it = b; it != e; ++it)
+    for (Rec *it = b; it != e; ++it)
       for (int d = 0; d < 3; ++d) {
         float c = 0.5f * (it->box[d] + it->box[3 + d]);
         lo[d] = std::min(lo[d], c);
@@ -1271,11 +1300,17 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       }
       return spread(k[0]) | (spread(k[1]) << 1) | (spread(k[2]) << 2);
     };
-    std::sort(b, e, [&](const Rec &x, const Rec &y) {
-      uint32_t kx = key(x), ky = key(y);
-      return kx < ky || (kx == ky && (uint32_t)x.tid < (uint32_t)y.tid);
-    });
+    auto &ks = sort_keys[t];
+    ks.resize(e - b);
+    for (int64_t j = 0; j < e - b; ++j)
+      ks[j] = {(uint64_t)key(b[j]) << 32 | (uint32_t)b[j].tid, (uint32_t)j};
+    std::sort(ks.begin(), ks.end());
+    auto &tmp = sort_tmp[t];
+    tmp.assign(b, e);
+    for (size_t j = 0; j < ks.size(); ++j) b[j] = tmp[ks[j].second];
   });
+  sort_keys.clear();
+  sort_tmp.clear();
   int64_t maxl = 0;
   for (int64_t p = 0; p < nv; ++p) maxl = std::max<int64_t>(maxl, out.row_off[p + 1] - out.row_off[p]);
 
@@ -1420,6 +1455,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   out.cert_queries = cert_queries;
   out.n_degenerate = ndeg;
   const double t_end = now_ms();
+  if (trace) std::fprintf(stderr, "p2m build: packing %.0f ms\n", t_end - t_pack);
   out.ms_total = t_end - t_start;
   out.ms_cells = t_flood - t_cells;
   out.ms_inspect = t_end - t_flood;
