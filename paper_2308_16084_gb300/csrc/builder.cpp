@@ -13,6 +13,7 @@
 // finds its primitive in the list of the vertex the kernel picks.
 #include "builder.h"
 #include "flood_core.h"
+#include "flood_warp.h"
 #include "quant.h"
 
 #include <algorithm>
@@ -1190,10 +1191,18 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   if (trace && !host_todo.empty())
     std::fprintf(stderr, "p2m build: device flooding %.0f ms (%lld primitives, %lld handed back)\n",
                  t_host_flood - t_flat, (long long)n_device, (long long)(nk - n_device));
-  // P2M_FLOOD_UNBOUNDED=1 floods every primitive with the unbounded code
-  // (a check that both host paths build the same layout)
-  const char *fu = std::getenv("P2M_FLOOD_UNBOUNDED");
-  const bool only_unbounded = fu && std::atoi(fu) != 0;
+  // P2M_FLOOD_UNBOUNDED=1 floods every primitive with the unbounded code;
+  // P2M_FLOOD_LANES=1 floods with the device kernel's warp algorithm
+  // (flood_warp.h, its 32 lanes run one after another) before the bounded
+  // core: checks that these paths build the same layout
+  auto env_flag = [](const char *name) {
+    const char *v = std::getenv(name);
+    return v && std::atoi(v) != 0;
+  };
+  const bool only_unbounded = env_flag("P2M_FLOOD_UNBOUNDED");
+  const bool lanes = env_flag("P2M_FLOOD_LANES");
+  std::vector<std::unique_ptr<fw::WarpWork>> lane_work(lanes ? threads : 0);
+  for (auto &w : lane_work) w.reset(new fw::WarpWork);
   parallel_for(nk, threads, 32, [&](int64_t k, int t) {
     if (!host_todo.empty() && !host_todo[k]) return;
     TLS &X = tls[t];
@@ -1204,6 +1213,14 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     env.recs = &X.recs;
     const size_t r0 = X.recs.size();
     int64_t insp = 0;
+    if (lanes && !only_unbounded) {
+      if (fw::flood_warp(*lane_work[t], env, k, eps, delta, eta, insp) == 0) {
+        X.inspections += insp;
+        ++X.bounded;
+        return;
+      }
+      X.recs.resize(r0);
+    }
     fc::Prim fp;
     if (!only_unbounded && fl.load(k, fp) &&
         fc::flood_prim(fp, eps, delta, eta, env, *X.W, X.queue.data(), (int64_t)X.queue.size(),

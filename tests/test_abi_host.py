@@ -295,3 +295,24 @@ def test_both_host_flooding_paths_build_the_same_layout(pg, name, monkeypatch, t
     a.save(str(tmp_path / "a.p2m"))
     b.save(str(tmp_path / "b.p2m"))
     assert (tmp_path / "a.p2m").read_bytes() == (tmp_path / "b.p2m").read_bytes()
+
+
+@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan"])
+def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, monkeypatch,
+                                                                      tmp_path):
+    """The device kernel's warp algorithm (flood_warp.h: one point or face
+    per lane, loops placed by prefix sums, cap chained by lane 0), run on the
+    host with its 32 lanes one after another (P2M_FLOOD_LANES=1), builds the
+    default layout byte for byte, handing what overflows its shared-memory
+    buffers to the bounded core and the unbounded code."""
+    m = {"sphere": lambda: dg.workload(3, n_queries=10, level=3),
+         "soup": lambda: dg.soup_workload("penetrating", level=3, n_queries=10),
+         "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10),
+         "fan": lambda: dg.high_valence_fan(120)}[name]()
+    a = _host(pg, m)
+    monkeypatch.setenv("P2M_FLOOD_LANES", "1")
+    b = _host(pg, m)
+    assert sum(a.flood_stats().values()) == sum(b.flood_stats().values())
+    a.save(str(tmp_path / "a.p2m"))
+    b.save(str(tmp_path / "b.p2m"))
+    assert (tmp_path / "a.p2m").read_bytes() == (tmp_path / "b.p2m").read_bytes()
