@@ -1,5 +1,6 @@
-// flood_core.h -- the flooding inspection of one primitive (Alg. 1), written
-// once for the host builder and the device flooding kernel.
+// flood_core.h -- the flooding inspection of one primitive (Alg. 1) as the
+// host builder runs it, and the types, flat problem view and cut primitive
+// that the device kernel's warp version (flood_warp.h) shares with it.
 //
 // For a primitive p (an edge or a face) the flood starts at p's vertices and
 // visits Voronoi neighbours breadth first.  At each visited vertex v it forms
@@ -12,8 +13,9 @@
 // vertices spread the flood.
 //
 // Every step is plain IEEE double arithmetic (+, -, *, /, sqrt) in a fixed
-// order, and both compilers are told not to fuse multiply-adds, so the host
-// and the device emit the same records bit for bit.  The work buffers have
+// order, and both compilers are told not to fuse multiply-adds, so the warp
+// version computes every value as this one does and the records agree bit
+// for bit.  The work buffers have
 // fixed capacities; a primitive that would overflow one, or whose cap loop
 // cannot be chained point to point, is given up (return 1) and its caller
 // floods it with unbounded host code.
