@@ -316,3 +316,25 @@ def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, 
     a.save(str(tmp_path / "a.p2m"))
     b.save(str(tmp_path / "b.p2m"))
     assert (tmp_path / "a.p2m").read_bytes() == (tmp_path / "b.p2m").read_bytes()
+
+
+def test_device_flooding_requested_without_a_gpu(pg):
+    """device_assist=2 on a machine without a GPU builds on the host (the
+    same layout), and a loaded handle reports no flooding split."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = dg.workload(0, n_queries=10)
+    a = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
+               device_assist=2)
+    b = _host(pg, m)
+    assert a.flood_stats() == b.flood_stats()
+    assert a.flood_stats()["device"] == 0
+    with tempfile.TemporaryDirectory() as d:
+        pa, pb = os.path.join(d, "a.p2m"), os.path.join(d, "b.p2m")
+        a.save(pa)
+        b.save(pb)
+        assert open(pa, "rb").read() == open(pb, "rb").read()
+        c = pg.P2M.load(pa)
+        assert c.flood_stats() == {"device": 0, "host_bounded": 0, "host_unbounded": 0}
+        assert c.stats()["n_entries"] == a.stats()["n_entries"]
