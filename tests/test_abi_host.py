@@ -338,3 +338,21 @@ def test_device_flooding_requested_without_a_gpu(pg):
         c = pg.P2M.load(pa)
         assert c.flood_stats() == {"device": 0, "host_bounded": 0, "host_unbounded": 0}
         assert c.stats()["n_entries"] == a.stats()["n_entries"]
+
+
+def test_builder_spherical_surface_every_vertex_intercepts_every_face(pg):
+    """Sec. 6: on a spherical surface each vertex intercepts every triangle
+    (tests/golden/spherical_surface_intercepts.txt); the product builder's
+    lists hold every face."""
+    path = os.path.join(ROOT, "tests", "golden", "spherical_surface_intercepts.txt")
+    gens = {"icosphere(0)": lambda: dg.icosphere(0), "icosphere(1)": lambda: dg.icosphere(1),
+            "octahedron()": dg.octahedron}
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for name, gen, nv, nf, per in rows:
+        V, F = gens[gen]()
+        h = pg.P2M(V.astype(np.float32), F.astype(np.int32), device_assist=False)
+        assert (h.n_verts, h.n_tris) == (int(nv), int(nf))
+        for v in range(h.n_verts):
+            t, i, _ = h.interception_list(v)
+            assert set(i[t == 2].tolist()) == set(range(int(per))), (name, v)

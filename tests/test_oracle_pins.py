@@ -7,6 +7,7 @@ own formulas: the references are closed forms, a different algorithm
 brute-force enumeration.
 """
 import itertools
+import os
 import math
 
 import numpy as np
@@ -683,3 +684,35 @@ def test_region_box_contains_relaxed_region_corners():
         assert (sel >= bx[:3] + 0.5 * o.delta).all() and (sel <= bx[3:] - 0.5 * o.delta).all()
         n_seen += 1
     assert n_seen > 100
+
+
+def _spherical_fixture():
+    rows = []
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "spherical_surface_intercepts.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            name, gen, nv, nf, per = line.split()
+            rows.append((name, gen, int(nv), int(nf), int(per)))
+    return rows
+
+
+def _spherical_mesh(gen):
+    V, F = {"icosphere(0)": lambda: dg.icosphere(0), "icosphere(1)": lambda: dg.icosphere(1),
+            "octahedron()": dg.octahedron}[gen]()
+    return V.astype(np.float32), F.astype(np.int32)
+
+
+@pytest.mark.parametrize("row", _spherical_fixture(), ids=lambda r: r[0])
+def test_spherical_surface_every_vertex_intercepts_every_face(row):
+    """Sec. 6: on a spherical surface each vertex intercepts every triangle
+    (tests/golden/spherical_surface_intercepts.txt).  Every Voronoi cell
+    reaches the sphere's centre, which projects inside every face."""
+    name, gen, nv, nf, per = row
+    V, F = _spherical_mesh(gen)
+    o = oracle.OracleMesh(V, F, 10.0, 0.0)
+    assert (o.nv, o.nf) == (nv, nf)
+    off, tt, ii, _ = o.table()
+    for v in range(o.nv):
+        faces = set(ii[off[v]:off[v + 1]][tt[off[v]:off[v + 1]] == 2].tolist())
+        assert faces == set(range(per)), (name, v)
