@@ -297,7 +297,30 @@ def test_both_host_flooding_paths_build_the_same_layout(pg, name, monkeypatch, t
     assert (tmp_path / "a.p2m").read_bytes() == (tmp_path / "b.p2m").read_bytes()
 
 
-@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan"])
+def _tiny(name):
+    """Edge cases of the flooding: one triangle, one segment, two triangles
+    far apart, a zero-area face beside a good one (not flooded)."""
+    V, F, S = {
+        "one-triangle": ([[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 2]], None),
+        "one-segment": ([[0, 0, 0], [1, 0.2, 0.1]], [], [[0, 1]]),
+        "two-triangles-apart": ([[0, 0, 0], [1, 0, 0], [0, 1, 0], [3, 3, 3], [4, 3, 3],
+                                 [3, 4, 3.5]], [[0, 1, 2], [3, 4, 5]], None),
+        "zero-area-face": ([[0, 0, 0], [1, 0, 0], [2, 0, 0], [0, 1, 0]],
+                           [[0, 1, 2], [0, 1, 3]], None),
+    }[name]
+    return dg.Mesh(name, np.array(V, np.float32), np.array(F, np.int32).reshape(-1, 3),
+                   np.zeros((1, 3), np.float32), 1.5, 0.1,
+                   meta={} if S is None else {"segs": np.array(S, np.int32)})
+
+
+@pytest.mark.parametrize("name", ["one-triangle", "one-segment", "two-triangles-apart",
+                                  "zero-area-face"])
+def test_builder_tables_equal_oracle_tables_on_tiny_inputs(pg, name):
+    _check_tables(pg, _tiny(name))
+
+
+@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan", "one-triangle",
+                                  "one-segment", "zero-area-face"])
 def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, monkeypatch,
                                                                       tmp_path):
     """The device kernel's warp algorithm (flood_warp.h: one point or face
@@ -308,7 +331,7 @@ def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, 
     m = {"sphere": lambda: dg.workload(3, n_queries=10, level=3),
          "soup": lambda: dg.soup_workload("penetrating", level=3, n_queries=10),
          "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10),
-         "fan": lambda: dg.high_valence_fan(120)}[name]()
+         "fan": lambda: dg.high_valence_fan(120)}.get(name, lambda: _tiny(name))()
     a = _host(pg, m)
     monkeypatch.setenv("P2M_FLOOD_LANES", "1")
     b = _host(pg, m)
