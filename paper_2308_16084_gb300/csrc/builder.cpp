@@ -561,20 +561,21 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   build_topology(M, Sin, ns);
 
   // domain D
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  double vlo[3] = {1e300, 1e300, 1e300}, vhi[3] = {-1e300, -1e300, -1e300};
   for (const V3 &v : M.V) {
     double c[3] = {v.x, v.y, v.z};
     for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], c[d]);
-      hi[d] = std::max(hi[d], c[d]);
+      vlo[d] = std::min(vlo[d], c[d]);
+      vhi[d] = std::max(vhi[d], c[d]);
     }
   }
-  double bbd = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
-                         (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  double bbd = std::sqrt((vhi[0] - vlo[0]) * (vhi[0] - vlo[0]) +
+                         (vhi[1] - vlo[1]) * (vhi[1] - vlo[1]) +
+                         (vhi[2] - vlo[2]) * (vhi[2] - vlo[2]));
   double Dlo[3], Dhi[3];
   for (int d = 0; d < 3; ++d) {
-    double c = 0.5 * (lo[d] + hi[d]);
-    double h = 0.5 * (hi[d] - lo[d]) * prm.domain_scale + prm.domain_margin * bbd;
+    double c = 0.5 * (vlo[d] + vhi[d]);
+    double h = 0.5 * (vhi[d] - vlo[d]) * prm.domain_scale + prm.domain_margin * bbd;
     if (h <= 0) h = 1e-3 * bbd;
     Dlo[d] = c - h;
     Dhi[d] = c + h;
@@ -865,7 +866,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     int &np_ = P.np;
     PrimGeom &g = P.g;
     int32_t *seeds = P.seeds;
-    int &ns = P.ns;
+    int &nseed = P.ns;
     int32_t &tid = P.tid;
     if (i < M.ne) {
       int64_t e = i;
@@ -884,7 +885,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       g = {1, a, u};
       seeds[0] = M.E[2 * e];
       seeds[1] = M.E[2 * e + 1];
-      ns = 2;
+      nseed = 2;
       tid = (int32_t)(1u << 30 | (uint32_t)e);
     } else {
       int64_t f = i - M.ne;
@@ -898,7 +899,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       V3 n = cross(b - a, c - a);
       g = {2, a, (1.0 / std::sqrt(len2(n))) * n};
       for (int k = 0; k < 3; ++k) seeds[k] = M.F[3 * f + k];
-      ns = 3;
+      nseed = 3;
       tid = (int32_t)(2u << 30 | (uint32_t)f);
     }
     return true;
@@ -936,13 +937,13 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     }
   std::vector<int32_t>().swap(prim_np);
   const int64_t nk = (int64_t)idx.size();
-  std::vector<double> perp(4 * (size_t)perp_off[nk]), g(6 * (size_t)nk);
+  std::vector<double> fperp(4 * (size_t)perp_off[nk]), fg(6 * (size_t)nk);
   std::vector<int32_t> gtype(nk), srow(3 * (size_t)nk), svid(3 * (size_t)nk), tids(nk);
   parallel_for(nk, threads, 4096, [&](int64_t k, int) {
     PrimData P;
     setup(idx[k], P);
     for (int j = 0; j < P.np; ++j) {
-      double *h = &perp[4 * (size_t)(perp_off[k] + j)];
+      double *h = &fperp[4 * (size_t)(perp_off[k] + j)];
       h[0] = P.perp[j].n.x;
       h[1] = P.perp[j].n.y;
       h[2] = P.perp[j].n.z;
@@ -950,7 +951,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     }
     gtype[k] = P.g.type;
     const double gg[6] = {P.g.a.x, P.g.a.y, P.g.a.z, P.g.u.x, P.g.u.y, P.g.u.z};
-    std::copy(gg, gg + 6, g.begin() + 6 * k);
+    std::copy(gg, gg + 6, fg.begin() + 6 * k);
     for (int j = 0; j < 3; ++j) {
       svid[3 * k + j] = j < P.ns ? P.seeds[j] : -1;
       srow[3 * k + j] = j < P.ns ? out.pos_of_vertex[P.seeds[j]] : -1;
@@ -967,9 +968,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   fl.nbo = out.nb_off.data();
   fl.nbs = out.nb.data();
   fl.perp_off = perp_off.data();
-  fl.perp = perp.data();
+  fl.perp = fperp.data();
   fl.gtype = gtype.data();
-  fl.g = g.data();
+  fl.g = fg.data();
   fl.seed_row = srow.data();
   fl.seed_vid = svid.data();
   fl.tid = tids.data();
@@ -989,7 +990,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     const int np_ = P.np;
     const PrimGeom &g = P.g;
     const int32_t *seeds = P.seeds;
-    const int ns = P.ns;
+    const int nseed = P.ns;
     const int32_t tid = P.tid;
     auto gval = [&](V3 x, V3 pv) {
       V3 w = x - g.a;
@@ -998,7 +999,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       return len2(x - pv) - dist2 + eta;
     };
     int64_t head = 0, tail = 0;
-    for (int s = 0; s < ns; ++s) {
+    for (int s = 0; s < nseed; ++s) {
       int64_t p = out.pos_of_vertex[seeds[s]];
       X.seen[p] = stamp;
       X.queue[tail++] = (int32_t)p;
@@ -1135,9 +1136,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     pb.nb_off = out.nb_off.data();
     pb.nb = out.nb.data();
     pb.perp_off = perp_off.data();
-    pb.perp = perp.data();
+    pb.perp = fperp.data();
     pb.gtype = gtype.data();
-    pb.g = g.data();
+    pb.g = fg.data();
     pb.seed_row = srow.data();
     pb.seed_vid = svid.data();
     pb.tid = tids.data();
@@ -1179,10 +1180,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       seen[w] = stamp;
       return true;
     }
-    void emit(int32_t row, int32_t tid, const float box[6]) {
+    void emit(int32_t row, int32_t typed_id, const float box[6]) {
       Rec r;
       r.row = row;
-      r.tid = tid;
+      r.tid = typed_id;
       for (int d = 0; d < 6; ++d) r.box[d] = box[d];
       recs->push_back(r);
     }
@@ -1322,9 +1323,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     for (int64_t j = 0; j < e - b; ++j)
       ks[j] = {(uint64_t)key(b[j]) << 32 | (uint32_t)b[j].tid, (uint32_t)j};
     std::sort(ks.begin(), ks.end());
-    auto &tmp = sort_tmp[t];
-    tmp.assign(b, e);
-    for (size_t j = 0; j < ks.size(); ++j) b[j] = tmp[ks[j].second];
+    auto &row_copy = sort_tmp[t];
+    row_copy.assign(b, e);
+    for (size_t j = 0; j < ks.size(); ++j) b[j] = row_copy[ks[j].second];
   });
   sort_keys.clear();
   sort_tmp.clear();

@@ -34,12 +34,12 @@ struct DevEnv : fc::Flat {
   unsigned long long *count;
   unsigned long long cap;
 
-  __device__ void emit(int32_t row, int32_t tid, const float box[6]) {
+  __device__ void emit(int32_t row, int32_t typed_id, const float box[6]) {
     const unsigned long long slot = atomicAdd(count, 1ull);
     if (slot < cap) {
       FloodRec r;
       r.row = row;
-      r.tid = tid;
+      r.tid = typed_id;
       for (int d = 0; d < 6; ++d) r.box[d] = box[d];
       rec[slot] = r;
     }
