@@ -55,6 +55,8 @@ def parse():
                     help="fixed p2m_tuning fields as JSON (profiling runs with --no-autotune)")
     ap.add_argument("--sweep", action="store_true",
                     help="extra workloads: mesh resolution, query box, soups, mixed primitives")
+    ap.add_argument("--list-stats", action="store_true",
+                    help="interception-list statistics of the workloads' tables (host build)")
     ap.add_argument("--layout", default=None,
                     help="load the built layout from this file if it exists, else build and "
                          "save it there")
@@ -681,10 +683,70 @@ def run_sweep(args):
     return 0
 
 
+def run_list_stats(args):
+    """Interception-list statistics of the built tables (host build; no GPU
+    needed, the certification runs on one when present): per workload the
+    vertices, faces, edges and table entries, the average and maximum
+    numbers of intercepted edges and faces per vertex (the per-vertex
+    columns of the paper's Table 2), list-length percentiles (the histogram
+    of Sec. 5.1), vertex inspections per flooded primitive and the share of
+    visited vertices that do not intercept, and the build time split
+    (Table 3).  One JSON line per case on stderr, then one line
+    with every case on stdout."""
+    import paper_2308_16084_gb300 as pg
+    cases = [
+        ("noisy icosphere L3 (workload 0)", lambda: dg.workload(0, n_queries=10)),
+        ("displaced icosphere L6 (workload 1 at level 6)",
+         lambda: dg.workload(1, n_queries=10, level=6)),
+        ("noisy icosphere L7 (workload 3)", lambda: dg.workload(3, n_queries=10)),
+        ("jittered height field 256^2 (workload 2 at 256^2)",
+         lambda: dg.workload(2, n_queries=10, grid=256)),
+        ("soup gapped L5", lambda: dg.soup_workload("gapped", level=5, n_queries=10)),
+        ("soup penetrating L5", lambda: dg.soup_workload("penetrating", level=5, n_queries=10)),
+        ("mesh L6 + wireframe L4", lambda: dg.mixed_workload(6, 4, n_queries=10)),
+    ]
+    rows = []
+    for name, make in cases:
+        m = make()
+        t0 = time.perf_counter()
+        mesh = pg.P2M(m.verts, m.tris, segs=m.meta.get("segs"), domain_scale=m.domain_scale,
+                      domain_margin=m.domain_margin)
+        build_s = time.perf_counter() - t0
+        st = mesh.stats()
+        ne = np.zeros(mesh.n_verts, np.int64)
+        nf = np.zeros(mesh.n_verts, np.int64)
+        for v in range(mesh.n_verts):
+            t, _, _ = mesh.interception_list(v)
+            ne[v] = int((t == 1).sum())
+            nf[v] = int((t == 2).sum())
+        ln = ne + nf
+        fs = mesh.flood_stats()
+        rows.append({
+            "case": name, "n_verts": mesh.n_verts, "n_tris": mesh.n_tris,
+            "n_edges": mesh.n_edges, "entries": int(st["n_entries"]),
+            "edges_per_vertex": {"avg": round(float(ne.mean()), 2), "max": int(ne.max())},
+            "faces_per_vertex": {"avg": round(float(nf.mean()), 2), "max": int(nf.max())},
+            "list_length": {"avg": round(float(ln.mean()), 2),
+                            **{f"p{q}": int(np.percentile(ln, q)) for q in (10, 50, 90, 99)},
+                            "max": int(ln.max())},
+            "inspections_per_primitive": round(st["inspections"] / max(1, sum(fs.values())), 2),
+            # share of the vertices the flooding visited that do not intercept
+            # (the paper reports about 85 %, Sec. 6)
+            "visited_rejected": round(1.0 - st["n_entries"] / max(1, st["inspections"]), 3),
+            "build_s": round(build_s, 2), "cells_ms": int(st["cells_ms"]),
+            "flooding_and_packing_ms": int(st["inspect_ms"]),
+        })
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"list_stats": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.list_stats:
+        return run_list_stats(args)
     if args.sweep:
         return run_sweep(args)
     if args.workload == 3:
