@@ -23,8 +23,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <limits>
 #include <memory>
+#include <mutex>
+#include <string>
 #include <thread>
 
 namespace p2m {
@@ -51,6 +54,9 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// fn(i, thread) for i in [0, n) on `threads` threads, chunk items at a time.
+// An exception thrown by fn (std::bad_alloc on a worker, say) stops the
+// other workers at their next chunk and is rethrown here once all joined.
 template <class F>
 void parallel_for(int64_t n, int threads, int64_t chunk, F &&fn) {
   if (threads <= 1 || n <= chunk) {
@@ -58,6 +64,8 @@ void parallel_for(int64_t n, int threads, int64_t chunk, F &&fn) {
     return;
   }
   std::atomic<int64_t> next{0};
+  std::exception_ptr failure;
+  std::mutex failure_mu;
   std::vector<std::thread> pool;
   for (int t = 0; t < threads; ++t)
     pool.emplace_back([&, t] {
@@ -65,10 +73,26 @@ void parallel_for(int64_t n, int threads, int64_t chunk, F &&fn) {
         int64_t s = next.fetch_add(chunk);
         if (s >= n) break;
         int64_t e = std::min(n, s + chunk);
-        for (int64_t i = s; i < e; ++i) fn(i, t);
+        try {
+          for (int64_t i = s; i < e; ++i) fn(i, t);
+        } catch (...) {
+          std::lock_guard<std::mutex> g(failure_mu);
+          if (!failure) failure = std::current_exception();
+          next.store(n);
+          break;
+        }
       }
     });
   for (auto &th : pool) th.join();
+  if (failure) std::rethrow_exception(failure);
+}
+
+// Host-side fault injection for tests: P2M_INJECT_BAD_ALLOC=<stage> makes a
+// worker of that build stage ("cells", "flooding" or "packing") throw
+// std::bad_alloc, as a failed allocation would.
+bool inject_at(const char *stage) {
+  const char *v = std::getenv("P2M_INJECT_BAD_ALLOC");
+  return v && std::strcmp(v, stage) == 0;
 }
 
 // ------------------------------------------------------------- polytope
@@ -628,7 +652,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   std::vector<CellWork> cells(nv);
   std::vector<CutScratch> scratch(threads);
   std::vector<Poly> tmp(threads);
+  const bool fail_cells = inject_at("cells");
   parallel_for(nv, threads, 64, [&](int64_t p, int t) {
+    if (fail_cells && p == nv / 2) throw std::bad_alloc();
     CellWork &C = cells[p];
     make_box(C.poly, Dlo, Dhi);
     int64_t ids[KSEED];
@@ -1204,7 +1230,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   const bool lanes = env_flag("P2M_FLOOD_LANES");
   std::vector<std::unique_ptr<fw::WarpWork>> lane_work(lanes ? threads : 0);
   for (auto &w : lane_work) w.reset(new fw::WarpWork);
+  const bool fail_flooding = inject_at("flooding");
   parallel_for(nk, threads, 32, [&](int64_t k, int t) {
+    if (fail_flooding && k == nk / 2) throw std::bad_alloc();
     if (!host_todo.empty() && !host_todo[k]) return;
     TLS &X = tls[t];
     HostEnv env;
@@ -1299,7 +1327,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   // row in that order (typed ids are distinct in a row: a total order)
   std::vector<std::vector<std::pair<uint64_t, uint32_t>>> sort_keys(threads);
   std::vector<std::vector<Rec>> sort_tmp(threads);
+  const bool fail_packing = inject_at("packing");
   parallel_for(nv, threads, 1024, [&](int64_t p, int t) {
+    if (fail_packing && p == nv / 2) throw std::bad_alloc();
     Rec *b = all.get() + out.row_off[p], *e = all.get() + out.row_off[p + 1];
     if (e - b < 2) return;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -365,6 +366,8 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
                            assist ? &dn : nullptr, assist ? on_tree_cb : nullptr, h.get(), h->L,
                            err);
   } catch (const std::bad_alloc &) {
+    return P2M_ERR_OOM;
+  } catch (const std::length_error &) {  // a host array beyond what can be allocated
     return P2M_ERR_OOM;
   }
   if (st) return (p2m_status)st;

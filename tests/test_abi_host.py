@@ -399,3 +399,18 @@ def test_build_options_and_stats_at_the_c_abi(pg):
     assert pg.lib.p2m_flood_stats(m._h, None) == 1
     assert pg.lib.p2m_flood_stats(m._h, out) == 0
     assert list(out[:3]) == [0, m.flood_stats()["host_bounded"], 0]
+
+
+@pytest.mark.parametrize("stage", ["cells", "flooding", "packing"])
+@pytest.mark.parametrize("threads", [1, 4])
+def test_out_of_memory_in_a_build_stage_is_reported(pg, stage, threads, monkeypatch):
+    """Host-side fault injection (P2M_INJECT_BAD_ALLOC=<stage>): an
+    allocation failure in a worker of a build stage comes back as
+    P2M_ERR_OOM, not a crash, and the next build is whole."""
+    m = dg.workload(2, n_queries=10, grid=40)
+    monkeypatch.setenv("P2M_INJECT_BAD_ALLOC", stage)
+    with pytest.raises(pg.P2MError) as e:
+        _host(pg, m, host_threads=threads)
+    assert e.value.code == 4
+    monkeypatch.delenv("P2M_INJECT_BAD_ALLOC")
+    _check_tables(pg, m)
