@@ -567,8 +567,9 @@ def run_ours(args):
     kname, kms, kbytes = max(cand, key=lambda c: c[1])
     peak, src = peaks()
     achieved = kbytes * n / (kms / 1e3) / 1e9
+    traffic = measured_traffic(kname, n)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": measured_traffic(kname, n),
+            "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured"
             else "fallback 6.8 TB/s",
             "kernel": kname, "kernel_ms": kms, "bytes_per_query": kbytes,
@@ -579,6 +580,11 @@ def run_ours(args):
             "phases": phases, "bytes_per_query_by_kernel": {"k_nn_pass": nn_b, "k_list_pass": list_b,
                                           "k_unpack": out_b},
             "work_per_query": {k: v / n for k, v in cnt.items()}}
+    if traffic:
+        # the DRAM side of the same launch: its ncu DRAM bytes over its live
+        # duration, against the same peak
+        roof["dram_achieved"] = traffic / (kms / 1e3) / 1e9
+        roof["dram_frac"] = roof["dram_achieved"] / peak
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
