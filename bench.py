@@ -696,8 +696,8 @@ def run_list_stats(args):
     numbers of intercepted edges and faces per vertex (the per-vertex
     columns of the paper's Table 2), list-length percentiles (the histogram
     of Sec. 5.1), vertex inspections per flooded primitive and the share of
-    visited vertices that do not intercept, and the build time split
-    (Table 3).  One JSON line per case on stderr, then one line
+    visited vertices that do not intercept, the layout's bytes by part
+    (Sec. 5.4) and the build time split (Table 3).  One JSON line per case on stderr, then one line
     with every case on stdout."""
     import paper_2308_16084_gb300 as pg
     cases = [
@@ -727,6 +727,18 @@ def run_list_stats(args):
             nf[v] = int((t == 2).sum())
         ln = ne + nf
         fs = mesh.flood_stats()
+        # layout bytes by part (the record sizes of the device layout; the
+        # seed grids and the query scratch come on top, on the device only)
+        chunks = (ln + 7) // 8
+        supers = (chunks + 7) // 8
+        nvp = mesh.n_verts + 1
+        parts = {
+            "kd_tree": 48 * (st["kd_leaves"] - 1) + 16 * mesh.n_verts,
+            "voronoi_neighbours": 4 * nvp + 20 * st["neighbour_pairs"],
+            "interception_entries": 16 * int(st["n_entries"]) + 4 * nvp,
+            "r_tree_boxes": 16 * int(chunks.sum() + supers.sum()) + 8 * nvp,
+            "geometry": 40 * mesh.n_edges + 64 * mesh.n_tris,
+        }
         rows.append({
             "case": name, "n_verts": mesh.n_verts, "n_tris": mesh.n_tris,
             "n_edges": mesh.n_edges, "entries": int(st["n_entries"]),
@@ -739,6 +751,7 @@ def run_list_stats(args):
             # share of the vertices the flooding visited that do not intercept
             # (the paper reports about 85 %, Sec. 6)
             "visited_rejected": round(1.0 - st["n_entries"] / max(1, st["inspections"]), 3),
+            "layout_mb": {k: round(v / 1e6, 2) for k, v in parts.items()},
             "build_s": round(build_s, 2), "cells_ms": int(st["cells_ms"]),
             "flooding_and_packing_ms": int(st["inspect_ms"]),
         })
