@@ -369,7 +369,12 @@ p2m_status p2m_get_list(const p2m_handle *h, int32_t vertex, int32_t *types, int
                         float *boxes, int64_t cap, int64_t *len);
 
 /* Serialise the built layout to a file (versioned header + checksum) and
- * load it back onto the current device.  Errors: IO, OOM, CUDA. */
+ * load it back onto the current device.  p2m_load checks, besides the
+ * checksum, every index the query kernels follow against the array it
+ * indexes (tree positions, rows, chunks, typed ids, neighbours), so a file
+ * whose contents do not fit is refused before anything reaches the device.
+ * Errors: IO (missing, short, corrupt, wrong version or inconsistent
+ * contents), OOM, CUDA. */
 p2m_status p2m_save(const p2m_handle *h, const char *path);
 p2m_status p2m_load(const char *path, p2m_handle **out);
 

@@ -1052,6 +1052,65 @@ bool get_vec(FILE *f, std::vector<T> &v, uint64_t &ck) {
   ck = fnv1a(ck, v.data(), n * sizeof(T));
   return true;
 }
+// Every index the query kernels follow, checked against the array it
+// indexes: a file whose checksum holds but whose contents do not (written by
+// another program, say) is refused instead of sending the kernels out of
+// bounds.  Sizes are checked by the caller.
+bool layout_consistent(const Layout &L) {
+  const int64_t nv = L.nv, nf = L.nf, ne = L.ne;
+  const int64_t K = Layout::kChunk;
+  if (nv < 1 || nf < 0 || ne < 0 || nv >= ((int64_t)1 << 30) || nf >= ((int64_t)1 << 30) ||
+      ne >= ((int64_t)1 << 30) || L.n_entries < 0)
+    return false;
+  if (L.kd_depth < 0 || L.kd_depth > 30 ||
+      (int64_t)L.kd_nodes.size() != 12 * (((int64_t)1 << L.kd_depth) - 1) ||
+      (int64_t)L.pos_of_vertex.size() != nv || (int64_t)L.edge_rec.size() != 8 * ne ||
+      (int64_t)L.face_rec.size() != 12 * nf || (int64_t)L.tris.size() != 4 * nf)
+    return false;
+  // tree positions: a permutation of the vertices and its inverse
+  for (int64_t p = 0; p < nv; ++p) {
+    int32_t v;
+    std::memcpy(&v, &L.kd_points[4 * p + 3], 4);
+    if (v < 0 || v >= nv || L.pos_of_vertex[v] != p) return false;
+  }
+  for (int64_t i = 0; i < 2 * ne; ++i)
+    if (L.edges[i] < 0 || L.edges[i] >= nv) return false;
+  for (int64_t f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k)
+      if (L.tris[4 * f + k] < 0 || L.tris[4 * f + k] >= nv) return false;
+  // rows, their chunks and super-chunks
+  if (L.row_off[0] != 0 || L.chunk_off[0] != 0 || L.super_off[0] != 0 ||
+      (int64_t)L.row_off[nv] != L.n_entries)
+    return false;
+  int64_t maxl = 0;
+  for (int64_t p = 0; p < nv; ++p) {
+    if (L.row_off[p + 1] < L.row_off[p] || L.chunk_off[p + 1] < L.chunk_off[p] ||
+        L.super_off[p + 1] < L.super_off[p])
+      return false;
+    const int64_t len = L.row_off[p + 1] - L.row_off[p];
+    const int64_t nc = L.chunk_off[p + 1] - L.chunk_off[p];
+    if (nc != (len + K - 1) / K || L.super_off[p + 1] - L.super_off[p] != (nc + K - 1) / K)
+      return false;
+    maxl = std::max(maxl, len);
+  }
+  if (maxl != L.max_list) return false;
+  // typed ids of the entries
+  for (int64_t j = 0; j < L.n_entries; ++j) {
+    const uint32_t w = L.entries[4 * j], type = w >> 30, id = w & ((1u << 30) - 1);
+    if (!((type == 1 && id < (uint64_t)ne) || (type == 2 && id < (uint64_t)nf))) return false;
+  }
+  // Voronoi neighbours and their inline copies
+  if (L.nb_off[0] != 0) return false;
+  for (int64_t p = 0; p < nv; ++p)
+    if (L.nb_off[p + 1] < L.nb_off[p]) return false;
+  for (size_t j = 0; j < L.nb.size(); ++j) {
+    uint32_t r;
+    std::memcpy(&r, &L.nbp[4 * j + 3], 4);
+    if (L.nb[j] >= (uint64_t)nv || r != L.nb[j]) return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1138,7 +1197,7 @@ p2m_status p2m_load(const char *path, p2m_handle **out) {
       (int64_t)L.chunk_off.size() != L.nv + 1 ||
       (int64_t)L.chunks.size() != 4 * (int64_t)L.chunk_off.back() ||
       L.nbp.size() != 4 * L.nb.size() || (int64_t)L.super_off.size() != L.nv + 1 ||
-      L.supers.size() != 4 * (size_t)L.super_off.back())
+      L.supers.size() != 4 * (size_t)L.super_off.back() || !layout_consistent(L))
     return P2M_ERR_IO;
   if (have_device() && cudaGetDevice(&h->device) == cudaSuccess) {
     cudaError_t e = h->upload_tree();

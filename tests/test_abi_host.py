@@ -414,3 +414,71 @@ def test_out_of_memory_in_a_build_stage_is_reported(pg, stage, threads, monkeypa
     assert e.value.code == 4
     monkeypatch.delenv("P2M_INJECT_BAD_ALLOC")
     _check_tables(pg, m)
+
+
+_LAYOUT_ARRAYS = ["kd_nodes", "kd_points", "pos_of_vertex", "row_off", "entries", "edge_rec",
+                  "face_rec", "edges", "tris", "nb_off", "nb", "chunk_off", "chunks", "nbp",
+                  "super_off", "supers"]
+
+
+def _layout_arrays(raw):
+    """Offsets of the arrays of a saved layout: a 184-byte header (magic,
+    version, 12 int64 scalars, 19 floats), then per array a uint64 count and
+    that many 4-byte elements, then the FNV-1a checksum of everything after
+    the version."""
+    pos, out = 184, {}
+    for name in _LAYOUT_ARRAYS:
+        n = int(np.frombuffer(bytes(raw[pos:pos + 8]), np.uint64)[0])
+        out[name] = (pos + 8, n)
+        pos += 8 + 4 * n
+    assert pos == len(raw) - 8
+    return out
+
+
+def _reseal(raw):
+    h = 1469598103934665603
+    for c in bytes(raw[12:-8]):
+        h = ((h ^ c) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    raw[-8:] = np.array([h], np.uint64).tobytes()
+
+
+def test_load_refuses_inconsistent_contents_with_a_valid_checksum(pg, tmp_path):
+    """p2m_load checks every index the kernels follow, not only the
+    checksum: a file re-sealed after an index was set out of range is
+    refused with P2M_ERR_IO; the untouched file (re-sealed the same way)
+    loads."""
+    m = dg.workload(0, n_queries=10, level=1)
+    h = _host(pg, m)
+    p = str(tmp_path / "m.p2m")
+    h.save(p)
+    raw = bytearray(open(p, "rb").read())
+    arr = _layout_arrays(raw)
+    ok = bytearray(raw)
+    _reseal(ok)
+    assert ok == raw
+    nv, nf = h.n_verts, h.n_tris
+
+    def u32(name, i, value):
+        off, n = arr[name]
+        assert 0 <= i < n
+        bad = bytearray(raw)
+        bad[off + 4 * i:off + 4 * i + 4] = np.array([value], np.uint32).tobytes()
+        _reseal(bad)
+        return bad
+
+    cases = [u32("entries", 0, (2 << 30) | nf),          # face id past the faces
+             u32("entries", 4, 3 << 30),                 # no such primitive type
+             u32("row_off", 1, 10 ** 6),                 # rows out of order
+             u32("nb", 0, nv), u32("nbp", 3, nv),        # neighbour past the vertices
+             u32("kd_points", 3, nv),                    # tree position of no vertex
+             u32("edges", 1, nv + 5), u32("tris", 2, nv),
+             u32("chunk_off", 1, 0)]
+    for k, bad in enumerate(cases):
+        q = str(tmp_path / f"bad{k}.p2m")
+        open(q, "wb").write(bad)
+        with pytest.raises(pg.P2MError) as e:
+            pg.P2M.load(q)
+        assert e.value.code == 7, k
+    q = str(tmp_path / "ok.p2m")
+    open(q, "wb").write(ok)
+    assert pg.P2M.load(q).stats()["n_entries"] == h.stats()["n_entries"]
