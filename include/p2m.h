@@ -95,7 +95,10 @@ typedef struct p2m_handle p2m_handle;
  * interception inspection (Alg. 1) with the convexity filter (Thm. 5/6),
  * Region bounding boxes (Sec. 4.6), packed as a CSR interception table.
  * The mesh is copied; `mesh` may be freed after the call.  Synchronous.
- * Errors: INVALID_ARG, INVALID_MESH, DUPLICATE_VERTEX, OOM, CUDA, NO_DEVICE.
+ * Errors: INVALID_ARG, INVALID_MESH, DUPLICATE_VERTEX, OOM, CUDA, NO_DEVICE,
+ * TOO_LARGE (2^30 vertices or 2^29 triangles or segments and beyond, a table
+ * of 2^32 entries, or a domain D reaching beyond +-1e18, where float32
+ * squared distances would overflow).
  */
 p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out);
 

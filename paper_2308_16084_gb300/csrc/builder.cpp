@@ -604,6 +604,13 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     Dlo[d] = c - h;
     Dhi[d] = c + h;
   }
+  // the device squares float32 coordinate differences: D must stay far
+  // inside sqrt(FLT_MAX) ~ 1.8e19
+  for (int d = 0; d < 3; ++d)
+    if (!(std::fabs(Dlo[d]) <= 1e18 && std::fabs(Dhi[d]) <= 1e18)) {
+      err = "domain D reaches beyond +-1e18";
+      return 9;
+    }
   const double diag = std::sqrt((Dhi[0] - Dlo[0]) * (Dhi[0] - Dlo[0]) +
                                 (Dhi[1] - Dlo[1]) * (Dhi[1] - Dlo[1]) +
                                 (Dhi[2] - Dlo[2]) * (Dhi[2] - Dlo[2]));

@@ -207,6 +207,21 @@ def test_invalid_meshes_return_status(pg, case, code):
     assert e.value.code == code
 
 
+def test_domain_beyond_float32_squares_is_too_large(pg):
+    """A coordinate (or a domain scale) that puts D beyond +-1e18, where the
+    device's float32 squared distances would overflow, is refused with
+    P2M_ERR_TOO_LARGE before anything is built."""
+    V, F = dg.octahedron()
+    V = V.astype(np.float32)
+    F = F.astype(np.int32)
+    for W, kw in ((np.where(np.arange(18).reshape(6, 3) == 0, 3e38, V).astype(np.float32), {}),
+                  (V, {"domain_scale": 1e19})):
+        with pytest.raises(pg.P2MError) as e:
+            pg.P2M(W, F, device_assist=False, **kw)
+        assert e.value.code == 9
+    pg.P2M(V * np.float32(1e15), F, device_assist=False, domain_scale=10.0)  # within the limit
+
+
 def test_bad_options_rejected(pg):
     V, F = dg.octahedron()
     for kw in ({"domain_scale": 0.0}, {"leaf_size": 1}, {"leaf_size": 64}, {"delta_rel": -1.0}):
