@@ -682,11 +682,44 @@ def run_sweep(args):
     mesh, bs = build(m, segs=m.meta["segs"])
     measure("mixed: mesh L6 + wireframe L4", mesh, torch.from_numpy(m.queries).cuda(),
             {"build_s": round(bs, 1), "n_segments": int(m.meta["segs"].shape[0])})
+    # per-list R-tree (Table 4 analogue): the same queries scanned with the
+    # Region box of every entry (chunked 0), chunk boxes first (1) and
+    # super-chunk boxes first (2), on meshes with long lists
+    for label, m in rtree_meshes(min(n, 2_000_000)):
+        mesh, bs = build(m)
+        qd = torch.from_numpy(m.queries).cuda()
+        for mode in (0, 1, 2):
+            mesh.tuning = {"chunked": mode}
+            measure(f"R-tree levels {mode}: {label}", mesh, qd,
+                    {"build_s": round(bs, 1), "max_list": int(mesh.stats()["max_list"])})
     line = {"metric": "point-to-mesh queries/sec by workload (sweep)", "unit": UNIT,
             "n_gpus": 1, "data": "synthetic", "dtype": "f32", "higher_is_better": True,
             "sweep": cases}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def rtree_meshes(n):
+    """Meshes with long interception lists for the R-tree comparison: the
+    displaced icosphere at level 6 (lists of 99 entries on average, up to
+    658) and a gapped soup of an exact, noise-free icosphere at level 3
+    (every face shrunk to 80 % about its centroid: the cells of its
+    cospherical vertices meet at the centre, so its lists hold most faces).
+    Queries: half uniform in the bbox scaled 1.2x, half near the surface."""
+    rq = np.random.default_rng(np.random.SeedSequence(dg.ROOT_SEED).spawn(9)[8])
+    out = [("displaced icosphere L6", dg.workload(1, n_queries=n, level=6))]
+    v, f = dg.icosphere(3)
+    tri = v[f]
+    c = tri.mean(1, keepdims=True)
+    sv = (c + 0.8 * (tri - c)).reshape(-1, 3)
+    sf = np.arange(sv.shape[0]).reshape(-1, 3)
+    half = n // 2
+    q = np.concatenate([dg.uniform_in_box(sv, 1.2, half, rq),
+                        dg.near_surface(sv, sf, n - half, 0.01 * dg.bbox_diagonal(sv), rq)], 0)
+    out.append(("exact-sphere gapped soup L3",
+                dg.Mesh("exact-sphere-gapped-soup-L3", sv.astype(np.float32),
+                        sf.astype(np.int32), q.astype(np.float32), 1.25, 0.02, meta={})))
+    return out
 
 
 def run_list_stats(args):
