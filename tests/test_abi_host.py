@@ -497,3 +497,21 @@ def test_load_refuses_inconsistent_contents_with_a_valid_checksum(pg, tmp_path):
     q = str(tmp_path / "ok.p2m")
     open(q, "wb").write(ok)
     assert pg.P2M.load(q).stats()["n_entries"] == h.stats()["n_entries"]
+
+
+def test_package_without_its_library_fails_to_import(tmp_path):
+    """No fallback: a copy of the package without libp2m.so raises
+    ImportError on import instead of running anything on the CPU."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2308_16084_gb300")
+    dst = tmp_path / "paper_2308_16084_gb300"
+    shutil.copytree(pkg, dst, ignore=shutil.ignore_patterns("_build", "__pycache__", "*.so"))
+    code = ("import sys; sys.path.insert(0, sys.argv[1])\n"
+            "try:\n    import paper_2308_16084_gb300\nexcept ImportError as e:\n"
+            "    print('IMPORTERROR', 'libp2m.so' in str(e)); sys.exit(0)\n"
+            "print('IMPORTED'); sys.exit(1)\n")
+    r = subprocess.run([sys.executable, "-c", code, str(tmp_path)], capture_output=True,
+                       text=True, timeout=120, cwd=str(tmp_path))
+    assert r.returncode == 0 and r.stdout.strip() == "IMPORTERROR True", r.stdout + r.stderr
