@@ -716,3 +716,59 @@ def test_spherical_surface_every_vertex_intercepts_every_face(row):
     for v in range(o.nv):
         faces = set(ii[off[v]:off[v + 1]][tt[off[v]:off[v + 1]] == 2].tolist())
         assert faces == set(range(per)), (name, v)
+
+
+def test_region_box_is_tight():
+    """Reading of Sec. 4.6: the Region box is the exact bounding box of
+    ConvexPoly ∩ {g > 0} (g = |x-v|^2 - Dist(x)^2 + eta), padded by delta.
+    A linear function over ConvexPoly minus a convex set peaks on the
+    polytope's boundary, down to its edges, so dense samples along every
+    edge of the polytope's convex hull (a different construction: scipy's
+    hull, points kept where g > 0) reach the box's faces to within the
+    sampling step.  Catches a box taken over the whole polytope."""
+    m = dg.workload(0, n_queries=10, level=2)
+    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    V = m.verts.astype(np.float64)
+    E = o.edges()
+    diag = np.linalg.norm(o.domain_hi - o.domain_lo)
+    eta = 2 * o.delta * diag + o.delta ** 2
+    off, t, ids, boxes = o.table()
+    tt = np.linspace(0.0, 1.0, 2001)[:, None]
+    n_seen = n_partial = 0
+    for j in range(0, off[-1], 11):
+        v = int(np.searchsorted(off, j, side="right") - 1)
+        cor = o.convexpoly(v, int(t[j]), int(ids[j]))
+        try:
+            hull = ConvexHull(cor)
+        except Exception:
+            continue  # a flat polytope
+        pairs = set()
+        for s in hull.simplices:
+            for a, b in ((s[0], s[1]), (s[1], s[2]), (s[0], s[2])):
+                pairs.add((min(a, b), max(a, b)))
+        pairs = np.array(sorted(pairs))
+        pts = (cor[pairs[:, 0]][None] * (1 - tt[..., None]) +
+               cor[pairs[:, 1]][None] * tt[..., None]).reshape(-1, 3)
+        step = np.linalg.norm(cor[pairs[:, 1]] - cor[pairs[:, 0]], axis=1).max() / 2000
+        if t[j] == oracle.EDGE:
+            a, b = V[E[ids[j]]]
+            u = (b - a) / np.linalg.norm(b - a)
+            w = pts - a
+            dist2 = (w * w).sum(1) - (w @ u) ** 2
+        else:
+            a, b, c = V[m.tris[ids[j]]]
+            n = np.cross(b - a, c - a)
+            n /= np.linalg.norm(n)
+            dist2 = ((pts - a) @ n) ** 2
+        g = ((pts - V[v]) ** 2).sum(1) - dist2 + eta
+        sel = pts[g > 0]
+        if sel.shape[0] == 0:
+            continue  # an incident primitive kept by Thm. 2 alone
+        bx = boxes[j].astype(np.float64)
+        lo, hi = bx[:3] + o.delta, bx[3:] - o.delta
+        tol = step + 1e-6 * diag  # sampling step, float32 rounding of the stored box
+        assert (sel.min(0) >= lo - tol).all() and (sel.max(0) <= hi + tol).all(), j
+        assert (np.abs(sel.min(0) - lo) <= tol).all() and (np.abs(sel.max(0) - hi) <= tol).all(), j
+        n_seen += 1
+        n_partial += bool((g <= 0).any())
+    assert n_seen > 100 and n_partial > 20
