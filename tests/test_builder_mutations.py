@@ -2,8 +2,8 @@
 below, planted in a copy of the library sources, makes the builder-versus-
 oracle table tests of tests/test_abi_host.py fail, while the unmodified
 copy passes them.  Each copy of the package is built into a temporary
-directory and tested in a subprocess; the committed sources are never
-touched."""
+directory and tested in a subprocess on the CPU (no GPU is visible to it);
+the committed sources are never touched."""
 import concurrent.futures as cf
 import os
 import shutil
@@ -42,7 +42,8 @@ def _host_tests_with_copy(base, name, fname, old, new):
         text = open(src).read()
         assert text.count(old) == 1, name
         open(src, "w").write(text.replace(old, new))
-    env = {**os.environ, "PYTHONPATH": work + os.pathsep + ROOT}
+    # CPU only: the copies never see a GPU
+    env = {**os.environ, "PYTHONPATH": work + os.pathsep + ROOT, "CUDA_VISIBLE_DEVICES": ""}
     b = subprocess.run([sys.executable, os.path.join(work, PKG, "build.py")], cwd=work,
                        env=env, capture_output=True, text=True, timeout=900)
     assert b.returncode == 0, b.stdout + b.stderr

@@ -60,7 +60,8 @@ def _pins_with_oracle_copy(base, name, old, new):
     if old is not None:
         assert text.count(old) == 1, name
         open(src, "w").write(text.replace(old, new))
-    env = {**os.environ, "PYTHONPATH": work + os.pathsep + ROOT}
+    # CPU only: the copies never see a GPU
+    env = {**os.environ, "PYTHONPATH": work + os.pathsep + ROOT, "CUDA_VISIBLE_DEVICES": ""}
     where = subprocess.run([sys.executable, "-c", "import oracle; print(oracle.__file__)"],
                            cwd=work, env=env, capture_output=True, text=True, timeout=300)
     assert where.stdout.strip().startswith(dst), where.stdout + where.stderr
