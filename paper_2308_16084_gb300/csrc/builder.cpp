@@ -709,7 +709,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     cert_queries += nq;
     const double t_round = now_ms();
     host_searches = 0;
-    std::vector<int64_t> viol_pos(nq, -1);
     bool used_device = false;
     if (nearest) {
       qbuf.resize(3 * nq);
@@ -729,8 +728,12 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     // exact double-precision search, on the device when it offers one
     std::vector<int64_t> exact(nq, -3);  // -3: not needed
     if (used_device) {
+      // the corners each row needs searched, then their points and bounds
+      // packed row by row at offsets from a prefix sum
       std::vector<uint8_t> need(nq, 0);
+      std::vector<int64_t> need_off(nv + 1, 0);
       parallel_for(nv, threads, 256, [&](int64_t p, int) {
+        int64_t c = 0;
         for (size_t i = 0; i < corner[p].size(); ++i) {
           const int64_t g = coff[p] + (int64_t)i;
           const V3 x = corner[p][i];
@@ -738,28 +741,34 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
           const int64_t prop = qans[g];
           const bool settled = prop == p || (prop >= 0 && len2(T.P[prop] - x) < r2);
           need[g] = settled ? 0 : 1;
+          c += need[g];
         }
+        need_off[p + 1] = c;
       });
-      std::vector<int64_t> idx;
-      for (int64_t g = 0; g < nq; ++g)
-        if (need[g]) idx.push_back(g);
-      if (!idx.empty()) {
-        std::vector<double> xs(3 * idx.size()), rs(idx.size());
-        std::vector<int64_t> ans(idx.size());
-        std::vector<int64_t> owner(nq);
-        for (int64_t p = 0; p < nv; ++p)
-          for (int64_t g = coff[p]; g < coff[p + 1]; ++g) owner[g] = p;
-        for (size_t k = 0; k < idx.size(); ++k) {
-          const int64_t g = idx[k], p = owner[g];
-          const V3 x = corner[p][g - coff[p]];
-          xs[3 * k] = x.x;
-          xs[3 * k + 1] = x.y;
-          xs[3 * k + 2] = x.z;
-          rs[k] = len2(x - T.P[p]) - epsc;
-        }
+      for (int64_t p = 0; p < nv; ++p) need_off[p + 1] += need_off[p];
+      const int64_t nneed = need_off[nv];
+      if (nneed > 0) {
+        std::vector<double> xs(3 * (size_t)nneed), rs(nneed);
+        std::vector<int64_t> ans(nneed);
+        parallel_for(nv, threads, 256, [&](int64_t p, int) {
+          int64_t k = need_off[p];
+          for (size_t i = 0; i < corner[p].size(); ++i)
+            if (need[coff[p] + (int64_t)i]) {
+              const V3 x = corner[p][i];
+              xs[3 * k] = x.x;
+              xs[3 * k + 1] = x.y;
+              xs[3 * k + 2] = x.z;
+              rs[k] = len2(x - T.P[p]) - epsc;
+              ++k;
+            }
+        });
         const double t_dev = now_ms();
-        if (nearest->within(xs.data(), rs.data(), (int64_t)idx.size(), ans.data()))
-          for (size_t k = 0; k < idx.size(); ++k) exact[idx[k]] = ans[k];
+        if (nearest->within(xs.data(), rs.data(), nneed, ans.data()))
+          parallel_for(nv, threads, 256, [&](int64_t p, int) {
+            int64_t k = need_off[p];
+            for (size_t i = 0; i < corner[p].size(); ++i)
+              if (need[coff[p] + (int64_t)i]) exact[coff[p] + (int64_t)i] = ans[k++];
+          });
         if (trace) std::fprintf(stderr, "p2m build:   exact device search %.0f ms\n", now_ms() - t_dev);
       }
     }
