@@ -678,6 +678,14 @@ def run_sweep(args):
         mesh, bs = build(m)
         measure(f"soup {kind} (5,120 faces)", mesh, torch.from_numpy(m.queries).cuda(),
                 {"build_s": round(bs, 1)})
+    # good and poor triangulations of one surface (Table 5 analogue)
+    for label, m in zip(("good: noisy icosphere L5", "poor: noisy lat-long sphere 32x320"),
+                        dg.triangulation_pair(min(n, 2_000_000))):
+        mesh, bs = build(m)
+        q_mean, slivers = dg.triangle_quality(m.verts, m.tris)
+        measure(f"triangulation {label}", mesh, torch.from_numpy(m.queries).cuda(),
+                {"build_s": round(bs, 1), "mean_Q": round(q_mean, 3),
+                 "min_angle_below_10deg": round(slivers, 3)})
     m = dg.mixed_workload(mesh_level=6, wire_level=4, n_queries=min(n, 2_000_000))
     mesh, bs = build(m, segs=m.meta["segs"])
     measure("mixed: mesh L6 + wireframe L4", mesh, torch.from_numpy(m.queries).cuda(),
@@ -730,7 +738,9 @@ def run_list_stats(args):
     columns of the paper's Table 2), list-length percentiles (the histogram
     of Sec. 5.1), vertex inspections per flooded primitive and the share of
     visited vertices that do not intercept, the layout's bytes by part
-    (Sec. 5.4) and the build time split (Table 3).  One JSON line per case on stderr, then one line
+    (Sec. 5.4), the build time split (Table 3) and the triangle quality of
+    Sec. 5.5 (a noisy icosphere and a noisy latitude-longitude sphere stand
+    in for Table 5's good and poor triangulations of one surface).  One JSON line per case on stderr, then one line
     with every case on stdout."""
     import paper_2308_16084_gb300 as pg
     cases = [
@@ -740,6 +750,10 @@ def run_list_stats(args):
         ("noisy icosphere L7 (workload 3)", lambda: dg.workload(3, n_queries=10)),
         ("jittered height field 256^2 (workload 2 at 256^2)",
          lambda: dg.workload(2, n_queries=10, grid=256)),
+        ("sphere, good triangulation: noisy icosphere L5",
+         lambda: dg.triangulation_pair(10)[0]),
+        ("sphere, poor triangulation: noisy lat-long 32x320",
+         lambda: dg.triangulation_pair(10)[1]),
         ("soup gapped L5", lambda: dg.soup_workload("gapped", level=5, n_queries=10)),
         ("soup penetrating L5", lambda: dg.soup_workload("penetrating", level=5, n_queries=10)),
         ("mesh L6 + wireframe L4", lambda: dg.mixed_workload(6, 4, n_queries=10)),
@@ -772,8 +786,11 @@ def run_list_stats(args):
             "r_tree_boxes": 16 * int(chunks.sum() + supers.sum()) + 8 * nvp,
             "geometry": 40 * mesh.n_edges + 64 * mesh.n_tris,
         }
+        q_mean, slivers = dg.triangle_quality(m.verts, m.tris) if m.tris.shape[0] else (0, 0)
         rows.append({
             "case": name, "n_verts": mesh.n_verts, "n_tris": mesh.n_tris,
+            "triangle_quality": {"mean_Q": round(q_mean, 3),
+                                 "min_angle_below_10deg": round(slivers, 3)},
             "n_edges": mesh.n_edges, "entries": int(st["n_entries"]),
             "edges_per_vertex": {"avg": round(float(ne.mean()), 2), "max": int(ne.max())},
             "faces_per_vertex": {"avg": round(float(nf.mean()), 2), "max": int(nf.max())},

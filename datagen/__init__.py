@@ -81,6 +81,38 @@ def noisy_icosphere(level: int, amplitude: float, rng):
     return v * r[:, None], f
 
 
+def uv_sphere(n_lat: int, n_lon: int, amplitude: float, rng):
+    """Unit sphere triangulated by latitude and longitude: two poles and
+    n_lat - 1 rings of n_lon vertices, each band of quads split along one
+    diagonal, triangle fans at the poles.  Near the poles the triangles are
+    long and thin: a poor triangulation of the surface icosphere() covers
+    well (the poor/good contrast of Sec. 5.5).  Radii 1 + U(-a, a), as
+    noisy_icosphere.  Faces are oriented outward."""
+    th = np.pi * np.arange(1, n_lat) / n_lat
+    ph = 2 * np.pi * np.arange(n_lon) / n_lon
+    ring = np.stack([np.sin(th)[:, None] * np.cos(ph)[None, :],
+                     np.sin(th)[:, None] * np.sin(ph)[None, :],
+                     np.cos(th)[:, None] * np.ones_like(ph)[None, :]], -1).reshape(-1, 3)
+    v = np.concatenate([[[0.0, 0.0, 1.0]], ring, [[0.0, 0.0, -1.0]]], 0)
+    south = v.shape[0] - 1
+
+    def at(i, j):  # ring i (0 = nearest the north pole), longitude j
+        return 1 + i * n_lon + j % n_lon
+
+    f = [[0, at(0, j), at(0, j + 1)] for j in range(n_lon)]
+    for i in range(n_lat - 2):
+        for j in range(n_lon):
+            a, b, c, d = at(i, j), at(i, j + 1), at(i + 1, j), at(i + 1, j + 1)
+            f += [[a, c, d], [a, d, b]]
+    f += [[south, at(n_lat - 2, j + 1), at(n_lat - 2, j)] for j in range(n_lon)]
+    f = np.array(f, dtype=np.int64)
+    v = v * (1.0 + rng.uniform(-amplitude, amplitude, size=(v.shape[0], 1)))
+    nrm = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+    flip = (nrm * v[f].mean(1)).sum(1) < 0
+    f[flip] = f[flip][:, ::-1]
+    return v, f
+
+
 def displaced_icosphere(level: int, amplitude: float, rng, n_terms: int = 8):
     """Icosphere with a smooth low-frequency radial displacement
     r(u) = 1 + a * s(u), s(u) = sum_j a_j cos(w_j d_j.u + phi_j), scaled so that
@@ -384,6 +416,25 @@ def soup_workload(kind: str, level: int = 5, n_queries: int = 1_000_000):
     q = np.concatenate([uniform_in_box(v, 1.2, nu, rq),
                         near_surface(v, f, n_queries - nu, 0.01 * bbox_diagonal(v), rq)], 0)
     return _finish(f"soup-{kind}-L{level}", v, f, q, 1.25, 0.02, meta={"kind": kind})
+
+
+def triangulation_pair(n_queries: int = 1_000_000):
+    """The same surface triangulated well and poorly (Sec. 5.5, Table 5):
+    a noisy icosphere at level 5 (10,242 vertices, mean Q 0.74, no triangle
+    with a smallest angle under 10 degrees) and a noisy latitude-longitude
+    sphere of 31 rings of 320 vertices (9,922 vertices, mean Q 0.44, 21 % of
+    its triangles under 10 degrees).  Both with radial noise 0.05; the same
+    queries for both: half uniform in the bbox scaled 1.2x, half within
+    0.01 x bbox diagonal of the icosphere."""
+    child = np.random.SeedSequence(ROOT_SEED).spawn(10)[9]
+    rg, rp, rq = [np.random.default_rng(s) for s in child.spawn(3)]
+    vg, fg = noisy_icosphere(5, 0.05, rg)
+    vp, fp = uv_sphere(32, 320, 0.05, rp)
+    nu = n_queries // 2
+    q = np.concatenate([uniform_in_box(vg, 1.2, nu, rq),
+                        near_surface(vg, fg, n_queries - nu, 0.01 * bbox_diagonal(vg), rq)], 0)
+    return (_finish("icosphere-L5-noise0.05", vg, fg, q, 1.25, 0.02),
+            _finish("latlong-sphere-32x320-noise0.05", vp, fp, q, 1.25, 0.02))
 
 
 def unique_edges(f):
