@@ -515,3 +515,18 @@ def test_package_without_its_library_fails_to_import(tmp_path):
     r = subprocess.run([sys.executable, "-c", code, str(tmp_path)], capture_output=True,
                        text=True, timeout=120, cwd=str(tmp_path))
     assert r.returncode == 0 and r.stdout.strip() == "IMPORTERROR True", r.stdout + r.stderr
+
+
+def test_builder_tables_equal_oracle_tables_on_a_lat_long_sphere(pg):
+    """A poorly triangulated closed surface (long thin triangles in pole
+    fans): a noisy latitude-longitude sphere, closed (Euler characteristic
+    2) and oriented outward, gives the oracle's tables."""
+    V, F = dg.uv_sphere(6, 48, 0.05, np.random.default_rng(1234))
+    assert V.shape[0] - dg.unique_edges(F).shape[0] + F.shape[0] == 2
+    nrm = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    assert ((nrm * V[F].mean(1)).sum(1) > 0).all()
+    q_mean, slivers = dg.triangle_quality(V, F)
+    assert slivers > 0.2
+    m = dg.Mesh("latlong-6x48", V.astype(np.float32), F.astype(np.int32),
+                np.zeros((1, 3), np.float32), 1.25, 0.02, meta={})
+    _check_tables(pg, m)
