@@ -334,8 +334,8 @@ def test_builder_tables_equal_oracle_tables_on_tiny_inputs(pg, name):
     _check_tables(pg, _tiny(name))
 
 
-@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan", "one-triangle",
-                                  "one-segment", "zero-area-face"])
+@pytest.mark.parametrize("name", ["sphere", "soup", "mixed", "fan", "lat-long",
+                                  "one-triangle", "one-segment", "zero-area-face"])
 def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, monkeypatch,
                                                                       tmp_path):
     """The device kernel's warp algorithm (flood_warp.h: one point or face
@@ -346,7 +346,8 @@ def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, 
     m = {"sphere": lambda: dg.workload(3, n_queries=10, level=3),
          "soup": lambda: dg.soup_workload("penetrating", level=3, n_queries=10),
          "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10),
-         "fan": lambda: dg.high_valence_fan(120)}.get(name, lambda: _tiny(name))()
+         "fan": lambda: dg.high_valence_fan(120),
+         "lat-long": lambda: dg.triangulation_pair(10)[1]}.get(name, lambda: _tiny(name))()
     a = _host(pg, m)
     monkeypatch.setenv("P2M_FLOOD_LANES", "1")
     b = _host(pg, m)
