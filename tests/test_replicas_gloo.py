@@ -6,7 +6,6 @@ import os
 import socket
 import tempfile
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

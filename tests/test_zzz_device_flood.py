@@ -8,7 +8,6 @@ code, neighbour list and the inspection count)."""
 import os
 import tempfile
 
-import numpy as np
 import pytest
 
 import datagen as dg
