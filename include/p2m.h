@@ -103,6 +103,18 @@ typedef struct p2m_handle p2m_handle;
 p2m_status p2m_build(const p2m_mesh *mesh, const p2m_build_opts *opts, p2m_handle **out);
 
 /*
+ * Environment variables p2m_build reads (diagnostics and tests; none
+ * changes the tables it builds):
+ *   P2M_BUILD_TRACE        set: time every build stage on stderr.
+ *   P2M_FLOOD_UNBOUNDED=1  flood every primitive with the unbounded host code.
+ *   P2M_FLOOD_LANES=1      flood on the host with the device kernel's warp
+ *                          algorithm, its 32 lanes run one after another.
+ *   P2M_INJECT_BAD_ALLOC=<stage>  host fault injection: a worker thread of
+ *                          the "cells", "flooding" or "packing" stage throws
+ *                          std::bad_alloc; p2m_build returns P2M_ERR_OOM.
+ */
+
+/*
  * Mixed primitives (Sec. 5, mixed segments and triangles): p2m_build with,
  * besides the mesh's triangles (n_tris may be 0, tris then NULL), n_segs
  * segments `segs` (2 vertex indices each, host memory) that are edges of no
