@@ -1,0 +1,181 @@
+// Host check of the product builder, compiled by tests/test_builder_sanitized.py
+// with AddressSanitizer and UBSan.  Reads one mesh file (counts, float32
+// vertices, int32 triangles and segments, domain scale and margin) and
+//   1. builds the layout on the host;
+//   2. builds it again through a stand-in for the device services: the
+//      certification searches answered by brute force under the same rules
+//      (float32 proposal of the nearest vertex; exact search = the nearest
+//      tree position strictly inside the bound, lowest position on ties),
+//      and the flooding run with the device kernel's warp algorithm
+//      (flood_warp.h, lanes one after another), and requires every table,
+//      box code, neighbour list and count to equal the host build's;
+//   3. injects an allocation failure into each build stage and requires
+//      std::bad_alloc to reach the caller.
+// Prints "OK" when every check holds.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "builder.h"
+#include "flood_core.h"
+#include "flood_warp.h"
+
+using namespace p2m;
+
+namespace {
+
+struct LaneEnv : fc::Flat {
+  std::vector<FloodRec> *rec;
+  void emit(int32_t row, int32_t typed_id, const float box[6]) {
+    FloodRec r;
+    r.row = row;
+    r.tid = typed_id;
+    for (int d = 0; d < 6; ++d) r.box[d] = box[d];
+    rec->push_back(r);
+  }
+};
+
+struct StandIn : NearestService {
+  const Layout *L = nullptr;
+  bool query(const float *xyz, int64_t n, int32_t *out) override {
+    for (int64_t i = 0; i < n; ++i) {
+      float best = INFINITY;
+      int32_t bi = -1;
+      for (int64_t p = 0; p < L->nv; ++p) {
+        const float dx = xyz[3 * i] - L->kd_points[4 * p], dy = xyz[3 * i + 1] - L->kd_points[4 * p + 1],
+                    dz = xyz[3 * i + 2] - L->kd_points[4 * p + 2];
+        const float d = dx * dx + dy * dy + dz * dz;
+        if (d < best) {
+          best = d;
+          bi = (int32_t)p;
+        }
+      }
+      out[i] = bi;
+    }
+    return true;
+  }
+  bool within(const double *xyz, const double *r2, int64_t n, int64_t *out) override {
+    for (int64_t i = 0; i < n; ++i) {
+      double best = r2[i];
+      int64_t bi = -1;
+      for (int64_t p = 0; p < L->nv; ++p) {
+        const double dx = xyz[3 * i] - (double)L->kd_points[4 * p],
+                     dy = xyz[3 * i + 1] - (double)L->kd_points[4 * p + 1],
+                     dz = xyz[3 * i + 2] - (double)L->kd_points[4 * p + 2];
+        const double d = dx * dx + dy * dy + dz * dz;
+        if (d < best) {
+          best = d;
+          bi = p;
+        }
+      }
+      out[i] = bi;
+    }
+    return true;
+  }
+  bool flood(const FloodProblem &pb, std::vector<FloodRec> &out, std::vector<uint8_t> &gave_up,
+             int64_t &inspections) override {
+    LaneEnv env;
+    env.pt_off = pb.cell_pt_off;
+    env.pt = (const fc::D3 *)pb.cell_pt;
+    env.beg_off = pb.cell_beg_off;
+    env.beg = pb.cell_beg;
+    env.pos = (const fc::D3 *)pb.pv;
+    env.vids = pb.vid;
+    env.nbo = pb.nb_off;
+    env.nbs = pb.nb;
+    env.perp_off = pb.perp_off;
+    env.perp = pb.perp;
+    env.gtype = pb.gtype;
+    env.g = pb.g;
+    env.seed_row = pb.seed_row;
+    env.seed_vid = pb.seed_vid;
+    env.tid = pb.tid;
+    env.rec = &out;
+    gave_up.assign(pb.n, 0);
+    inspections = 0;
+    std::unique_ptr<fw::WarpWork> S(new fw::WarpWork);
+    for (int64_t i = pb.n - 1; i >= 0; --i) {  // any order: the host sorts
+      int64_t k = 0;
+      const int r = fw::flood_warp(*S, env, i, pb.eps, pb.delta, pb.eta, k);
+      gave_up[i] = r != 0;  // records of a given-up primitive stay in: the host drops them
+      if (r == 0) inspections += k;
+    }
+    return true;
+  }
+};
+
+bool same(const Layout &A, const Layout &B) {
+  return A.entries == B.entries && A.chunks == B.chunks && A.supers == B.supers &&
+         A.row_off == B.row_off && A.chunk_off == B.chunk_off && A.super_off == B.super_off &&
+         A.nb == B.nb && A.nb_off == B.nb_off && A.nbp == B.nbp && A.kd_points == B.kd_points &&
+         A.kd_nodes == B.kd_nodes && A.edge_rec == B.edge_rec && A.face_rec == B.face_rec &&
+         A.inspections == B.inspections && A.n_entries == B.n_entries &&
+         A.max_list == B.max_list && A.neighbour_pairs == B.neighbour_pairs;
+}
+
+}  // namespace
+
+#define CHECK(c)                                         \
+  do {                                                   \
+    if (!(c)) {                                          \
+      std::printf("FAILED %s (line %d)\n", #c, __LINE__); \
+      return 1;                                          \
+    }                                                    \
+  } while (0)
+
+int main(int argc, char **argv) {
+  if (argc < 2) return 2;
+  FILE *f = std::fopen(argv[1], "rb");
+  if (!f) return 2;
+  int64_t nv, nf, ns;
+  CHECK(std::fread(&nv, 8, 1, f) == 1 && std::fread(&nf, 8, 1, f) == 1 &&
+        std::fread(&ns, 8, 1, f) == 1);
+  std::vector<float> V(3 * nv);
+  std::vector<int32_t> F(3 * nf + 1), S(2 * ns + 1);
+  double sc[2];
+  CHECK(std::fread(V.data(), 4, 3 * nv, f) == (size_t)(3 * nv));
+  CHECK(nf == 0 || std::fread(F.data(), 4, 3 * nf, f) == (size_t)(3 * nf));
+  CHECK(ns == 0 || std::fread(S.data(), 4, 2 * ns, f) == (size_t)(2 * ns));
+  CHECK(std::fread(sc, 8, 2, f) == 2);
+  std::fclose(f);
+  BuildParams prm;
+  prm.domain_scale = sc[0];
+  prm.domain_margin = sc[1];
+  prm.threads = 4;
+  const int32_t *Fp = nf ? F.data() : nullptr, *Sp = ns ? S.data() : nullptr;
+  std::string err;
+
+  Layout host;
+  CHECK(build_layout(V.data(), nv, Fp, nf, Sp, ns, prm, nullptr, nullptr, nullptr, host, err) == 0);
+
+  StandIn svc;
+  BuildParams prm2 = prm;
+  prm2.device_flood = true;
+  Layout dev;
+  auto on_tree = [](void *ctx, const Layout &L) {
+    ((StandIn *)ctx)->L = &L;
+    return true;
+  };
+  CHECK(build_layout(V.data(), nv, Fp, nf, Sp, ns, prm2, &svc, on_tree, &svc, dev, err) == 0);
+  CHECK(dev.flood_device > 0);
+  CHECK(same(host, dev));
+
+  for (const char *stage : {"cells", "flooding", "packing"}) {
+    setenv("P2M_INJECT_BAD_ALLOC", stage, 1);
+    Layout L;
+    bool thrown = false;
+    try {
+      build_layout(V.data(), nv, Fp, nf, Sp, ns, prm, nullptr, nullptr, nullptr, L, err);
+    } catch (const std::bad_alloc &) {
+      thrown = true;
+    }
+    CHECK(thrown);
+  }
+  unsetenv("P2M_INJECT_BAD_ALLOC");
+  std::printf("OK\n");
+  return 0;
+}
