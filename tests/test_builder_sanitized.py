@@ -1,9 +1,11 @@
-"""The product builder under AddressSanitizer (with leak checking) and
-UBSan, on the host: tests/builder_host_check.cpp builds each mesh on the
-host, again through stand-ins for the device services (brute-force
-certification searches, the device kernel's warp flooding run lane by lane
-on the host) and compares the layouts, then injects an allocation failure
-into each build stage.  Any sanitizer report fails the run."""
+"""The product builder and the oracle under AddressSanitizer (with leak
+checking) and UBSan, on the host.  tests/builder_host_check.cpp builds each
+mesh on the host, again through stand-ins for the device services
+(brute-force certification searches, the device kernel's warp flooding run
+lane by lane on the host) and compares the layouts, then injects an
+allocation failure into each build stage; tests/oracle_host_check.c runs
+the oracle's tables, brute force and queries.  Any sanitizer report fails
+the run."""
 import os
 import shutil
 import subprocess
@@ -32,6 +34,20 @@ def checker(tmp_path_factory):
     return exe
 
 
+@pytest.fixture(scope="module")
+def oracle_checker(tmp_path_factory):
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path_factory.mktemp("asan_oracle") / "oracle_host_check")
+    cmd = ["gcc", "-O1", "-g", "-std=gnu11", "-pthread", "-ffp-contract=off",
+           "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+           "-I", os.path.join(ROOT, "oracle"), os.path.join(ROOT, "tests", "oracle_host_check.c"),
+           os.path.join(ROOT, "oracle", "p2m_oracle.c"), "-lm", "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
 def _write(m, path):
     segs = m.meta.get("segs")
     S = np.zeros((0, 2), np.int32) if segs is None else np.asarray(segs, np.int32)
@@ -52,6 +68,19 @@ def test_builder_under_sanitizers(checker, name, tmp_path):
     path = str(tmp_path / "mesh.bin")
     _write(m, path)
     r = subprocess.run([checker, path], capture_output=True, text=True, timeout=900,
+                       env={**os.environ, "ASAN_OPTIONS": "detect_leaks=1"})
+    assert r.returncode == 0 and r.stdout.strip().endswith("OK"), \
+        r.stdout[-2000:] + r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("name", ["sphere", "mixed", "fan"])
+def test_oracle_under_sanitizers(oracle_checker, name, tmp_path):
+    m = {"sphere": lambda: dg.workload(0, n_queries=10, level=2),
+         "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10),
+         "fan": lambda: dg.high_valence_fan(60)}[name]()
+    path = str(tmp_path / "mesh.bin")
+    _write(m, path)
+    r = subprocess.run([oracle_checker, path], capture_output=True, text=True, timeout=900,
                        env={**os.environ, "ASAN_OPTIONS": "detect_leaks=1"})
     assert r.returncode == 0 and r.stdout.strip().endswith("OK"), \
         r.stdout[-2000:] + r.stderr[-3000:]
