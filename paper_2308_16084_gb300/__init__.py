@@ -21,17 +21,20 @@ Q_OUTSIDE_DOMAIN, Q_NONFINITE = 1, 2
 
 
 class BuildOpts(ctypes.Structure):
+    """p2m_build_opts of include/p2m.h."""
     _fields_ = [("domain_scale", ctypes.c_float), ("domain_margin", ctypes.c_float),
                 ("delta_rel", ctypes.c_float), ("host_threads", ctypes.c_int),
                 ("device_assist", ctypes.c_int), ("leaf_size", ctypes.c_int)]
 
 
 class MeshDesc(ctypes.Structure):
+    """p2m_mesh of include/p2m.h (host pointers and counts)."""
     _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int64),
                 ("tris", ctypes.c_void_p), ("n_tris", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
+    """p2m_tuning of include/p2m.h: the query path's launch configuration."""
     _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int),
                 ("chunked", ctypes.c_int), ("group_by_vertex", ctypes.c_int),
@@ -39,12 +42,14 @@ class Tuning(ctypes.Structure):
 
 
 class BatchIO(ctypes.Structure):
+    """p2m_batch_io of include/p2m.h: one mesh's device buffers in a batch."""
     _fields_ = [("q", ctypes.c_void_p), ("n", ctypes.c_int64), ("dist", ctypes.c_void_p),
                 ("closest", ctypes.c_void_p), ("prim_id", ctypes.c_void_p),
                 ("prim_type", ctypes.c_void_p)]
 
 
 class BatchTuning(ctypes.Structure):
+    """p2m_batch_tuning of include/p2m.h."""
     _fields_ = [("sort_bits", ctypes.c_int), ("tile", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
                 ("group_by_vertex", ctypes.c_int)]
@@ -105,14 +110,19 @@ class P2M:
 
     @classmethod
     def load(cls, path):
+        """A layout saved by save(), checked (checksum and every index the
+        kernels follow) and uploaded to the current device when there is
+        one."""
         h = ctypes.c_void_p()
         check(lib.p2m_load(os.fsencode(path), ctypes.byref(h)), "p2m_load")
         return cls(_handle=h)
 
     def save(self, path):
+        """Write the built layout to `path` (versioned, checksummed)."""
         check(lib.p2m_save(self._h, os.fsencode(path)), "p2m_save")
 
     def close(self):
+        """Release the handle and its device memory (idempotent)."""
         if self._h:
             lib.p2m_destroy(self._h)
             self._h = None
@@ -125,6 +135,10 @@ class P2M:
 
     # ----------------------------------------------------------------- info
     def stats(self):
+        """Statistics of the built layout (p2m_stats): sizes, table entries,
+        longest list, device bytes, KD tree, neighbour pairs, flooding
+        inspections, build times in ms, certification rounds and queries,
+        degenerate faces."""
         out = (ctypes.c_int64 * 16)()
         check(lib.p2m_stats(self._h, out), "p2m_stats")
         keys = ["n_verts", "n_tris", "n_edges", "n_entries", "max_list", "device_bytes",
@@ -140,11 +154,14 @@ class P2M:
         return {"device": out[0], "host_bounded": out[1], "host_unbounded": out[2]}
 
     def domain(self):
+        """(lo, hi, delta): the query domain D and the widening margin."""
         out = (ctypes.c_float * 7)()
         check(lib.p2m_domain(self._h, out), "p2m_domain")
         return np.array(out[:3]), np.array(out[3:6]), float(out[6])
 
     def edges(self):
+        """The canonical edge list, (E,2) int32: unique (min, max) vertex
+        pairs in lexicographic order; edge ids index it."""
         n = ctypes.c_int64()
         check(lib.p2m_get_edges(self._h, None, ctypes.byref(n)), "p2m_get_edges")
         E = np.zeros((n.value, 2), np.int32)
@@ -169,6 +186,9 @@ class P2M:
     # --------------------------------------------------------------- tuning
     @property
     def tuning(self):
+        """The query launch configuration as a dict (p2m_get_tuning);
+        assigning a dict with some of its fields changes those
+        (p2m_set_tuning range-checks them)."""
         t = Tuning()
         check(lib.p2m_get_tuning(self._h, ctypes.byref(t)), "p2m_get_tuning")
         return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
@@ -185,12 +205,16 @@ class P2M:
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):
+        """Time the launch configurations on the (N,3) CUDA queries q and
+        keep the fastest; returns its time in ms."""
         ms = ctypes.c_float()
         check(lib.p2m_autotune(self._h, _ptr(q), q.shape[0], reps, _stream(stream),
                                ctypes.byref(ms)), "p2m_autotune")
         return ms.value
 
     def set_timing(self, enable=True):
+        """Record CUDA events around every phase of the following queries
+        (read them with timing_summary())."""
         check(lib.p2m_set_timing(self._h, int(bool(enable))), "p2m_set_timing")
 
     def timing_summary(self):
@@ -213,6 +237,8 @@ class P2M:
         return dict(zip(["nodes", "points", "entries", "edges", "faces", "chunks"], list(out)))
 
     def reserve(self, n):
+        """Allocate the query scratch for batches of up to n points now, so
+        that later queries of that size allocate nothing."""
         check(lib.p2m_reserve(self._h, int(n)), "p2m_reserve")
 
     # ---------------------------------------------------------------- query
@@ -345,14 +371,18 @@ class P2MPipe:
         self._p = p
 
     def submit(self, q, dist, prim_id, closest=None, prim_type=None):
+        """Queue one batch: q (N,3) float32 in, dist / prim_id (and closest,
+        prim_type when given) out, all host buffers."""
         check(lib.p2m_pipe_submit(self._p, _host_ptr(q), int(q.shape[0]), _host_ptr(dist),
                                   _host_ptr(closest), _host_ptr(prim_id), _host_ptr(prim_type)),
               "p2m_pipe_submit")
 
     def wait(self):
+        """Block until every submitted batch's results are in its buffers."""
         check(lib.p2m_pipe_wait(self._p), "p2m_pipe_wait")
 
     def close(self):
+        """Release the pipe's slots (idempotent)."""
         if getattr(self, "_p", None):
             lib.p2m_pipe_destroy(self._p)
             self._p = None
@@ -392,13 +422,19 @@ class P2MBatch:
         self._b = b
 
     def run(self, stream=None):
+        """One launch over every mesh's queries; returns the per-mesh output
+        dicts (CUDA tensors, filled when the stream reaches them)."""
         check(lib.p2m_batch_run(self._b, _stream(stream)), "p2m_batch_run")
         return self.out
 
     def check(self, stream=None):
+        """Synchronise and raise (P2M_ERR_QUEUE_TIMEOUT) if the device error
+        word of the last runs reports a malformed work item."""
         check(lib.p2m_batch_check(self._b, _stream(stream)), "p2m_batch_check")
 
     def autotune(self, reps=3, stream=None):
+        """Time the batch launch configurations and keep the fastest;
+        returns its time in ms."""
         ms = ctypes.c_float()
         check(lib.p2m_batch_autotune(self._b, reps, _stream(stream), ctypes.byref(ms)),
               "p2m_batch_autotune")
@@ -406,6 +442,8 @@ class P2MBatch:
 
     @property
     def tuning(self):
+        """The batch launch configuration as a dict; assign a dict with some
+        of its fields to change those."""
         t = BatchTuning()
         check(lib.p2m_batch_get_tuning(self._b, ctypes.byref(t)), "p2m_batch_get_tuning")
         return {"sort_bits": t.sort_bits, "tile": t.tile, "block_threads": t.block_threads,
@@ -420,6 +458,7 @@ class P2MBatch:
         check(lib.p2m_batch_set_tuning(self._b, ctypes.byref(t)), "p2m_batch_set_tuning")
 
     def close(self):
+        """Release the batch (idempotent); the meshes stay valid."""
         if getattr(self, "_b", None):
             lib.p2m_batch_destroy(self._b)
             self._b = None
