@@ -603,7 +603,10 @@ def run_ours(args):
                 "l2": f"inputs larger than L2: layout {st['device_bytes'] / 1e9:.2f} GB + "
                       f"queries {12 * n / 1e6:.0f} MB per step",
                 "tuning": mesh.tuning, "autotune_ms": tuned_ms, "build_s": round(build_s, 1),
-                "table_entries": st["n_entries"], "max_list": st["max_list"]}),
+                "table_entries": st["n_entries"], "max_list": st["max_list"],
+                "build_split_ms": {"cells": st["cells_ms"],
+                                   "flooding_and_packing": st["inspect_ms"]},
+                "flooding": mesh.flood_stats()}),
             "clocks": clk, "e2e": e2e, "gpu_launches": kernels_per_step(mesh.tuning) * args.steps,
             "roofline": roof, "cpu_baseline": cpu}
     if rank == 0:
