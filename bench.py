@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="fixed p2m_tuning fields as JSON (profiling runs with --no-autotune)")
     ap.add_argument("--sweep", action="store_true",
-                    help="extra workloads: mesh resolution, query box, soups, mixed primitives")
+                    help="extra workloads: mesh resolution, query box, soups, good and poor "
+                         "triangulations, mixed primitives, R-tree levels")
     ap.add_argument("--list-stats", action="store_true",
                     help="interception-list statistics of the workloads' tables (host build)")
     ap.add_argument("--layout", default=None,
