@@ -625,9 +625,11 @@ def run_ours(args):
 
 def run_sweep(args):
     """Extra workloads (not the headline): mesh resolution, query box,
-    triangle soups and mixed primitives.  One JSON line with one entry per
-    case: build seconds, device-resident queries/s (CUDA events, 5 steps
-    after 2 warm-ups, fixed default tuning) and work per query."""
+    triangle soups, a good and a poor triangulation of one sphere, mixed
+    primitives, and the per-list R-tree levels on long-list meshes.  One
+    JSON line with one entry per case: build seconds, device-resident
+    queries/s (CUDA events, 5 steps after 2 warm-ups, default tuning but for
+    the R-tree cases) and work per query."""
     import torch
     import paper_2308_16084_gb300 as pg
     n = args.queries or 4_000_000
