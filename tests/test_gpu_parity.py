@@ -231,7 +231,10 @@ def test_edge_cases(pg):
     for q in (special[:1], special, np.repeat(special, 37, 0)[:257]):
         gpu = run(mesh, q)
         ref = o.bruteforce(q)
-        pu.check(m.verts, E, m.tris, q, gpu, ref, tau, "special")
+        # the edge midpoints lie on the shared boundary of an open edge and
+        # its open faces by construction: every one of them may come back as
+        # a boundary mismatch (its reported primitive is still checked)
+        pu.check(m.verts, E, m.tris, q, gpu, ref, tau, "special", boundary_frac=1.0)
     gpu = run(mesh, special)
     assert (gpu["dist"][:5] == 0).all() and (gpu["prim_type"][:5] == pg.VERTEX).all()
     np.testing.assert_array_equal(gpu["prim_id"][:5], np.arange(5))
@@ -466,8 +469,8 @@ def full1(pg):
 
 def test_full_size_displaced_sphere_sampled(pg, full1):
     """1.3M triangles, 10M queries in the launch configuration the benchmark
-    times: every output obeys the invariants, 3000 sampled outputs match the
-    brute-force oracle."""
+    times: every output obeys the invariants, 20,000 sampled outputs match
+    the brute-force oracle."""
     m, mesh = full1
     q = torch.from_numpy(m.queries).cuda()
     base = mesh.query(q, closest=True, prim_type=True, save=True)
@@ -482,7 +485,7 @@ def test_full_size_displaced_sphere_sampled(pg, full1):
     wts = r["save"][:, 1:]
     assert (wts >= -1e-6).all() and torch.allclose(wts.sum(1), torch.ones_like(d), atol=1e-5)
     rng = np.random.default_rng(1)
-    sel = np.sort(rng.choice(m.queries.shape[0], 3000, replace=False))
+    sel = np.sort(rng.choice(m.queries.shape[0], 20000, replace=False))
     o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
     ref = o.bruteforce(m.queries[sel])
     got = {"dist": d.cpu().numpy()[sel], "prim_id": r["prim_id"].cpu().numpy()[sel],
@@ -497,7 +500,7 @@ def test_full_size_displaced_sphere_sampled(pg, full1):
 
 def test_full_size_heightfield_sampled(pg):
     """2,093,058-triangle jittered height field with slivers, 16M queries
-    Gaussian about the surface: invariants on every output, 2000 sampled
+    Gaussian about the surface: invariants on every output, 20,000 sampled
     outputs against the brute-force oracle."""
     m = dg.workload(2)
     mesh = build(pg, m)
@@ -507,7 +510,7 @@ def test_full_size_heightfield_sampled(pg):
     d = r["dist"]
     assert torch.isfinite(d).all()
     assert torch.allclose(torch.linalg.norm(q - r["closest"], dim=1), d, atol=2e-6, rtol=1e-5)
-    sel = np.sort(np.random.default_rng(2).choice(m.queries.shape[0], 2000, replace=False))
+    sel = np.sort(np.random.default_rng(2).choice(m.queries.shape[0], 20000, replace=False))
     o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
     ref = o.bruteforce(m.queries[sel])
     got = {"dist": d.cpu().numpy()[sel], "prim_id": r["prim_id"].cpu().numpy()[sel],
@@ -518,7 +521,7 @@ def test_full_size_heightfield_sampled(pg):
 
 def test_full_size_fwd_bwd_sampled(pg):
     """327,680-triangle noisy icosphere, 4M near-surface queries, loss
-    sum w_i d_i: forward outputs and the query gradient of 2000 sampled
+    sum w_i d_i: forward outputs and the query gradient of 20,000 sampled
     queries against the oracle (away from ties and d = 0), and the vertex
     gradient against the scatter of the oracle's per-query terms."""
     m = dg.workload(3)
@@ -529,11 +532,13 @@ def test_full_size_fwd_bwd_sampled(pg):
     d, pid = pg.distance(q, verts, mesh)
     (w * d).sum().backward()
     torch.cuda.synchronize()
-    sel = np.sort(np.random.default_rng(3).choice(m.queries.shape[0], 2000, replace=False))
+    sel = np.sort(np.random.default_rng(3).choice(m.queries.shape[0], 20000, replace=False))
     o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
     ref = o.bruteforce(m.queries[sel])
     got = {"dist": d.detach().cpu().numpy()[sel], "prim_id": pid.cpu().numpy()[sel]}
-    got["prim_type"] = mesh.query(q.detach()[sel], prim_type=True)["prim_type"].cpu().numpy()
+    again = mesh.query(q.detach()[sel], closest=True, prim_type=True)
+    got["prim_type"] = again["prim_type"].cpu().numpy()
+    got["closest"] = again["closest"].cpu().numpy()
     pu.check(m.verts, o.edges(), m.tris, m.queries[sel], got, ref, pu.tolerance(m.verts), "full3")
     gq_ref, _, _ = oracle.gradient(m.queries[sel].astype(np.float64), ref,
                                    m.weights[sel].astype(np.float64))
@@ -549,7 +554,7 @@ def test_full_size_fwd_bwd_sampled(pg):
 
 def test_full_size_batch_sampled(pg):
     """All 64 meshes of the batch workload (about 5.2M triangles, 24M
-    queries) in one persistent launch: 300 sampled outputs per mesh against
+    queries) in one persistent launch: 2,000 sampled outputs per mesh against
     the brute-force oracle, and bitwise equality with per-mesh queries."""
     ms = dg.batch_workload(64)
     meshes = [build(pg, m) for m in ms]
@@ -562,7 +567,7 @@ def test_full_size_batch_sampled(pg):
     for m, mesh, q, r in zip(ms, meshes, qs, out):
         single = mesh.query(q, closest=False, prim_type=False)
         assert torch.equal(single["dist"], r["dist"]) and torch.equal(single["prim_id"], r["prim_id"])
-        sel = np.sort(rng.choice(m.queries.shape[0], min(300, m.queries.shape[0]), replace=False))
+        sel = np.sort(rng.choice(m.queries.shape[0], min(2000, m.queries.shape[0]), replace=False))
         o = oracle.OracleMesh(m.verts, m.tris, build_tables=False)
         ref = o.bruteforce(m.queries[sel])
         got = {k: v.cpu().numpy()[sel] for k, v in r.items()}

@@ -40,8 +40,16 @@ def test_noalloc_matches_query_on_two_calls():
                "closest": torch.zeros(n, 3, device="cuda"),
                "prim_id": torch.full((n,), -7, dtype=torch.int32, device="cuda"),
                "prim_type": torch.full((n,), 9, dtype=torch.uint8, device="cuda")}
+        torch.cuda.synchronize()
+        # the first call of the process may load this library's device code
+        # (and with it the static array); from the second call on, nothing
+        # the call does may change the device's free memory or torch's pool
+        free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         assert _call(pg, mesh, q, out) == 0, f"call {call}"
         torch.cuda.synchronize()
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0, "device memory changed"
+            assert torch.cuda.memory_allocated() == alloc0
         assert (out["dist"] - ref["dist"]).abs().max().item() <= tau
         assert (out["closest"] - ref["closest"]).abs().max().item() <= tau
         assert torch.equal(out["prim_id"], ref["prim_id"])
