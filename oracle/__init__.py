@@ -65,6 +65,10 @@ def _load():
             lib.orc_create_mixed.argtypes = [P, i64, P, i64, P, i64, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, P]
+            lib.orc_create_ex.restype = P
+            lib.orc_create_ex.argtypes = [P, i64, P, i64, P, i64, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, P, P, P]
             lib.orc_destroy.argtypes = [P]
             lib.orc_info.argtypes = [P, P, P]
             lib.orc_edges.argtypes = [P, P]
@@ -92,6 +96,19 @@ def default_threads() -> int:
     return os.cpu_count() or 1
 
 
+def delaunay_neighbors(V):
+    """Delaunay neighbours of every vertex as CSR (offsets int64, ids int32),
+    from qhull's 3-D Delaunay triangulation (scipy.spatial.Delaunay, a
+    library step like the TetGen call of the paper's preprocessing, Sec. 5).
+    The bisectors of a vertex's Delaunay neighbours bound its Voronoi cell."""
+    from scipy.spatial import Delaunay
+    d = Delaunay(np.asarray(V, np.float64))
+    indptr, idx = d.vertex_neighbor_vertices
+    off = np.ascontiguousarray(indptr, np.int64)
+    ids = np.ascontiguousarray(idx, np.int32)
+    return off, ids
+
+
 class OracleMesh:
     """Oracle state for one mesh: topology, KD tree and (optionally) the
     Voronoi cells, the interception table and the Region boxes (Alg. A.1).
@@ -100,18 +117,32 @@ class OracleMesh:
     kept as it is, for finite-difference tests)."""
 
     def __init__(self, verts, tris, domain_scale=10.0, domain_margin=0.0,
-                 delta_rel=4e-6, build_tables=True, threads=None, segs=None):
+                 delta_rel=4e-6, build_tables=True, threads=None, segs=None,
+                 voronoi="certified"):
+        """voronoi: "certified" (k-nearest seeding, every cell corner
+        certified by a nearest-vertex search) or "delaunay" (the cell of v
+        clipped by the bisectors of its Delaunay neighbours from qhull, for
+        large meshes).  Either gives the Voronoi cells of V clipped to D."""
         self._lib = _load()
         self.V = self._widen(verts)
         self.F = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
         self.S = np.ascontiguousarray(
             np.zeros((0, 2), np.int32) if segs is None else np.asarray(segs, np.int32).reshape(-1, 2))
         self.threads = default_threads() if threads is None else int(threads)
+        if voronoi not in ("certified", "delaunay"):
+            raise ValueError(f"oracle: unknown Voronoi construction {voronoi!r}")
+        cand_off = cand = None
+        self.delaunay_s = 0.0
+        if build_tables and voronoi == "delaunay":
+            import time
+            t0 = time.perf_counter()
+            cand_off, cand = delaunay_neighbors(self.V)
+            self.delaunay_s = time.perf_counter() - t0
         st = ctypes.c_int(0)
-        self._h = self._lib.orc_create_mixed(
+        self._h = self._lib.orc_create_ex(
             _p(self.V), self.V.shape[0], _p(self.F), self.F.shape[0], _p(self.S),
             self.S.shape[0], float(domain_scale), float(domain_margin), float(delta_rel),
-            int(bool(build_tables)), self.threads, ctypes.byref(st))
+            int(bool(build_tables)), self.threads, _p(cand_off), _p(cand), ctypes.byref(st))
         self.status = st.value
         if not self._h:
             raise ValueError(f"oracle: invalid mesh ({STATUS.get(st.value, st.value)})")

@@ -352,6 +352,9 @@ struct orc_mesh {
   double *tb;
   int64_t ninspect;
   double tms[4];
+  /* optional inputs of orc_create_ex */
+  const int64_t *cand_off; /* nv+1: Delaunay neighbours of each vertex (CSR) */
+  const int32_t *cand;     /* or NULL: k-nearest seeding + corner certification */
 };
 
 /* ------------------------------------------------------------------ */
@@ -731,8 +734,24 @@ static void bisector_plane(const orc_mesh *m, int32_t v, int32_t w, double widen
 
 #define KNN_SEED 24
 
-static int compute_cell(const orc_mesh *m, int32_t v, opoly *exact, opoly *tmp,
-                        int32_t **nbs, int *nnb) {
+/* Cell(v) from a complete candidate list: the Voronoi cell of v is the
+ * intersection of the bisector half-spaces of its Delaunay neighbours (every
+ * other bisector is redundant), so clipping D by those alone gives it with
+ * no certification.  The candidates come from a Delaunay triangulation of V
+ * computed by a library (the paper's preprocessing takes its Voronoi
+ * diagram from TetGen, Sec. 5; here qhull through scipy). */
+static void compute_cell_from_candidates(const orc_mesh *m, int32_t v, opoly *exact,
+                                         opoly *tmp) {
+  poly_box(exact, m->dlo, m->dhi);
+  for (int64_t j = m->cand_off[v]; j < m->cand_off[v + 1]; ++j) {
+    double pl[4];
+    bisector_plane(m, v, m->cand[j], 0.0, pl);
+    poly_clip(exact, pl, m->cand[j], tmp, m->eps);
+    poly_copy(exact, tmp);
+  }
+}
+
+static void compute_cell_certified(const orc_mesh *m, int32_t v, opoly *exact, opoly *tmp) {
   const double *pv = m->V + 3 * v;
   poly_box(exact, m->dlo, m->dhi);
   int32_t ids[KNN_SEED];
@@ -781,6 +800,14 @@ static int compute_cell(const orc_mesh *m, int32_t v, opoly *exact, opoly *tmp,
     if (!changed) break;
   }
   free(applied);
+}
+
+static int compute_cell(const orc_mesh *m, int32_t v, opoly *exact, opoly *tmp,
+                        int32_t **nbs, int *nnb) {
+  if (m->cand)
+    compute_cell_from_candidates(m, v, exact, tmp);
+  else
+    compute_cell_certified(m, v, exact, tmp);
   /* neighbours: generators of the surviving bisector faces */
   int k = 0;
   int32_t *out = (int32_t *)malloc(sizeof(int32_t) * (exact->nf + 1));
@@ -1114,10 +1141,31 @@ orc_mesh *orc_create_mixed(const double *V, int64_t nv, const int32_t *F, int64_
                            const int32_t *S, int64_t ns, double domain_scale,
                            double domain_margin, double delta_rel, int build_tables,
                            int n_threads, int *status) {
-  int st = (!V || nv <= 0 || (nf > 0 && !F) || (ns > 0 && !S)) ? ORC_BAD_ARG
-                                                                 : validate(V, nv, F, nf, S, ns);
+  return orc_create_ex(V, nv, F, nf, S, ns, domain_scale, domain_margin, delta_rel,
+                       build_tables, n_threads, NULL, NULL, status);
+}
+
+orc_mesh *orc_create_ex(const double *V, int64_t nv, const int32_t *F, int64_t nf,
+                        const int32_t *S, int64_t ns, double domain_scale, double domain_margin,
+                        double delta_rel, int build_tables, int n_threads,
+                        const int64_t *cand_off, const int32_t *cand, int *status) {
+  int st = (!V || nv <= 0 || (nf > 0 && !F) || (ns > 0 && !S) || (!cand_off != !cand))
+               ? ORC_BAD_ARG
+               : validate(V, nv, F, nf, S, ns);
+  if (!st && cand) {
+    if (cand_off[0] != 0) st = ORC_BAD_ARG;
+    for (int64_t i = 0; i < nv && !st; ++i)
+      if (cand_off[i + 1] < cand_off[i]) st = ORC_BAD_ARG;
+    for (int64_t j = 0; !st && j < cand_off[nv]; ++j)
+      if (cand[j] < 0 || cand[j] >= nv) st = ORC_BAD_INDEX;
+    for (int64_t i = 0; i < nv && !st; ++i)
+      for (int64_t j = cand_off[i]; j < cand_off[i + 1]; ++j)
+        if (cand[j] == (int32_t)i) st = ORC_BAD_ARG;
+  }
   if (st) { if (status) *status = st; return NULL; }
   orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
+  m->cand_off = cand_off;
+  m->cand = cand;
   m->nv = nv;
   m->nf = nf;
   m->ns = ns;
@@ -1193,6 +1241,8 @@ orc_mesh *orc_create_mixed(const double *V, int64_t nv, const int32_t *F, int64_
   }
   free(nbs);
   free(nnb);
+  m->cand_off = NULL; /* borrowed from the caller for the cell stage only */
+  m->cand = NULL;
   double t3 = now_ms();
 
   /* flooding inspection over every edge and every face */

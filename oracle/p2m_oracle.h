@@ -66,6 +66,17 @@ orc_mesh *orc_create_mixed(const double *V, int64_t nv, const int32_t *F, int64_
                            const int32_t *S, int64_t ns, double domain_scale,
                            double domain_margin, double delta_rel, int build_tables,
                            int n_threads, int *status);
+/* orc_create_mixed with the Voronoi neighbours given (off in orc_create
+ * and orc_create_mixed): cand_off[nv+1], cand[] hold the Delaunay
+ * neighbours of every vertex (CSR, no self entries), e.g. from a library
+ * triangulation.  The Voronoi cell of v is then D clipped by the bisectors of
+ * exactly these vertices, with no k-nearest seeding and no corner
+ * certification.  The arrays are read during the call only.  NULL, NULL:
+ * the certified construction. */
+orc_mesh *orc_create_ex(const double *V, int64_t nv, const int32_t *F, int64_t nf,
+                        const int32_t *S, int64_t ns, double domain_scale, double domain_margin,
+                        double delta_rel, int build_tables, int n_threads,
+                        const int64_t *cand_off, const int32_t *cand, int *status);
 void orc_destroy(orc_mesh *m);
 
 /* info[0..15]: nv, nf, ne, n_table_entries, n_degenerate_faces,

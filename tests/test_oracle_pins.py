@@ -284,6 +284,55 @@ def test_voronoi_cells_equal_all_bisector_cells():
     assert abs(vol_all - np.prod(hi - lo)) < 1e-9 * np.prod(hi - lo)
 
 
+def test_voronoi_cells_from_delaunay_equal_all_bisector_cells():
+    """Cell(v) clipped by the bisectors of its qhull Delaunay neighbours ==
+    D cut by the bisectors of ALL other vertices (same volume, same
+    neighbours): the construction the large-mesh oracle builds use."""
+    r_ = rng(8)
+    n = 180
+    V = r_.uniform(-1, 1, size=(n, 3)).astype(np.float32)
+    F = np.stack([np.arange(0, n, 3), np.arange(1, n, 3), np.arange(2, n, 3)], 1).astype(np.int32)
+    o = oracle.OracleMesh(V, F, domain_scale=1.5, delta_rel=0.0, voronoi="delaunay")
+    Vd = V.astype(np.float64)
+    lo, hi = o.domain_lo, o.domain_hi
+    for v in range(0, n, 7):
+        w = np.array([i for i in range(n) if i != v])
+        nrm = Vd[w] - Vd[v]
+        nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+        c = (nrm * (0.5 * (Vd[w] + Vd[v]))).sum(1)
+        corners = oracle.clip_box(lo, hi, np.concatenate([nrm, c[:, None]], 1))
+        vol = ConvexHull(corners).volume
+        assert abs(vol - o.cell_volume(v)) <= 1e-9 * vol
+        on = np.abs(corners @ nrm.T - c[None, :]) < 1e-9
+        assert set(w[on.sum(0) >= 3].tolist()) == set(o.cell_neighbors(v).tolist()), v
+
+
+@pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 4}), (2, {"grid": 40}),
+                                    (3, {"level": 4})])
+def test_delaunay_cells_give_the_certified_tables(idx, kw):
+    """The oracle built from qhull's Delaunay neighbours has the certified
+    construction's Voronoi neighbours and cell volumes, the same
+    interception lists with Region boxes equal to rounding, and its Alg. A.2
+    query equals the brute force bit for bit."""
+    m = dg.workload(idx, n_queries=20000, **kw)
+    a = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
+    b = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin, voronoi="delaunay")
+    assert a.n_neighbor_pairs == b.n_neighbor_pairs
+    for v in range(0, a.nv, 3):
+        assert set(a.cell_neighbors(v).tolist()) == set(b.cell_neighbors(v).tolist()), v
+        va = a.cell_volume(v)
+        assert abs(va - b.cell_volume(v)) <= 1e-9 * va
+    ta, tb = _table_set(a), _table_set(b)
+    assert ta.keys() == tb.keys()
+    diag = float(np.linalg.norm(a.domain_hi - a.domain_lo))
+    worst = max(np.abs(ta[k] - tb[k]).max() for k in ta)
+    assert worst <= 1e-12 * diag
+    bf = b.bruteforce(m.queries)
+    r = b.query(m.queries, use_boxes=True)
+    np.testing.assert_array_equal(r["dist"], bf["dist"])
+    np.testing.assert_array_equal(r["pid"], bf["pid"])
+
+
 def test_voronoi_volume_sum_workload0():
     m = dg.workload(0, n_queries=10)
     o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
