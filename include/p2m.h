@@ -236,7 +236,12 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  when that is finer), so the lanes of a warp start their
  *                  Voronoi walks near the same vertex (needs
  *                  group_by_vertex = 1; otherwise the Morton sort runs;
- *                  sort_bits unused).  Results do not depend on it. */
+ *                  sort_bits unused).  Results do not depend on it.
+ *   lanes_per_query  threads per query in the list pass of the two-pass
+ *                  path: 1, 2, 4 or 8 adjacent lanes split a query's
+ *                  interception list (every G-th group of 64 entries) and
+ *                  keep the best with a warp shuffle.  Results do not
+ *                  depend on it. */
 typedef struct {
   int sort_bits;
   int block_threads;
@@ -245,6 +250,7 @@ typedef struct {
   int chunked;
   int group_by_vertex;
   int sort_key;
+  int lanes_per_query;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
@@ -290,6 +296,33 @@ p2m_status p2m_backward(p2m_handle *h, const float *q, const float *dist, const 
                         const float *save, const float *grad_dist, int64_t n, float *grad_q,
                         float *grad_verts, void *stream);
 
+/*
+ * Move the mesh's vertices (the differentiable path's geometry refresh):
+ * the vertex-dependent parts of the device layout are recomputed from new
+ * positions on `stream` -- the KD-tree points and child boxes, the Voronoi
+ * neighbours' positions and the edge and face records -- while the
+ * interception lists and Region boxes (Alg. A.1, Sec. 4.6) stay those of
+ * the build.  The distance a later query returns is then the exact distance
+ * to the best primitive among its nearest vertex and that vertex's list
+ * (Alg. A.2 on the moved geometry), an upper bound of the true distance that
+ * equals it wherever the build's list and box still cover the moved closest
+ * primitive, which small moves keep for nearly every query; rebuild the
+ * handle after large moves.  Positions equal to the build's leave every
+ * record unchanged bit for bit.
+ *   verts        device, n_verts*3 float, original vertex order (read during
+ *                the call's kernels only; the caller keeps ownership)
+ *   n_verts      must equal the mesh's vertex count
+ *   refresh_seed_grid  1: also recompute the seed grids of the nearest-vertex
+ *                walk (one exact search per grid cell, slower); 0: keep them
+ *                (the walk then starts from the build's seeds)
+ * The host copy of the layout (p2m_save, p2m_get_list) and the domain D are
+ * not changed.  Asynchronous on `stream`; no allocation.
+ * Errors: INVALID_ARG (NULL verts, wrong count, refresh flag not 0/1),
+ * NO_DEVICE, CUDA.
+ */
+p2m_status p2m_update_vertices(p2m_handle *h, const float *verts, int64_t n_verts,
+                               int refresh_seed_grid, void *stream);
+
 /* One mesh's slice of a batched query (device pointers, n points). */
 typedef struct {
   const float *q;     /* n*3 */
@@ -309,13 +342,16 @@ typedef struct {
  *   group_by_vertex  1: nearest-vertex pass over all meshes, regroup the
  *              queries by (mesh, nearest vertex), then the persistent list
  *              pass (needs sum of (vertex count + 1) <= 2^24); 0: one
- *              persistent pass per query */
+ *              persistent pass per query
+ *   lanes_per_query  threads per query in the persistent list pass (1, 2
+ *              or 4; with group_by_vertex = 1), as in p2m_tuning */
 typedef struct {
   int sort_bits;
   int tile;
   int block_threads;
   int grid_ctas;
   int group_by_vertex;
+  int lanes_per_query;
 } p2m_batch_tuning;
 
 typedef struct p2m_batch p2m_batch;

@@ -38,7 +38,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int),
                 ("chunked", ctypes.c_int), ("group_by_vertex", ctypes.c_int),
-                ("sort_key", ctypes.c_int)]
+                ("sort_key", ctypes.c_int), ("lanes_per_query", ctypes.c_int)]
 
 
 class BatchIO(ctypes.Structure):
@@ -52,7 +52,7 @@ class BatchTuning(ctypes.Structure):
     """p2m_batch_tuning of include/p2m.h."""
     _fields_ = [("sort_bits", ctypes.c_int), ("tile", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("grid_ctas", ctypes.c_int),
-                ("group_by_vertex", ctypes.c_int)]
+                ("group_by_vertex", ctypes.c_int), ("lanes_per_query", ctypes.c_int)]
 
 
 def _stream(stream=None):
@@ -194,14 +194,15 @@ class P2M:
         return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
                 "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk,
                 "chunked": t.chunked, "group_by_vertex": t.group_by_vertex,
-                "sort_key": t.sort_key}
+                "sort_key": t.sort_key, "lanes_per_query": t.lanes_per_query}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
         t = Tuning(cur["sort_bits"], cur["block_threads"], cur["warp_cooperative"],
-                   cur["nn_walk"], cur["chunked"], cur["group_by_vertex"], cur["sort_key"])
+                   cur["nn_walk"], cur["chunked"], cur["group_by_vertex"], cur["sort_key"],
+                   cur["lanes_per_query"])
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):
@@ -293,6 +294,14 @@ class P2M:
         queries."""
         return P2MPipe(self, max_n, depth)
 
+    def update_vertices(self, verts, refresh_seed_grid=False, stream=None):
+        """Move the vertices to `verts` ((V,3) float32 CUDA tensor, original
+        order): KD tree, neighbour positions and edge and face records are
+        recomputed on the device; the interception tables stay those of the
+        build (p2m_update_vertices).  refresh_seed_grid also recomputes the
+        seed grids of the nearest-vertex walk."""
+        _update_vertices(self, verts, refresh_seed_grid, stream)
+
     def backward(self, q, res, grad_dist, grad_q=True, grad_verts=None, stream=None):
         """Gradients of sum(grad_dist * dist): returns (grad_q, grad_verts);
         grad_verts is accumulated into the given (V,3) tensor if passed."""
@@ -303,6 +312,16 @@ class P2M:
                                _ptr(res["save"]), _ptr(grad_dist), n, _ptr(gq), _ptr(grad_verts),
                                _stream(stream)), "p2m_backward")
         return gq, grad_verts
+
+
+def _update_vertices(mesh, verts, refresh_seed_grid=False, stream=None):
+    import torch
+    assert verts.is_cuda and verts.dtype == torch.float32, "verts: float32 CUDA tensor"
+    v = verts.detach().contiguous()
+    assert v.shape == (mesh.n_verts, 3), f"verts: expected ({mesh.n_verts}, 3)"
+    check(lib.p2m_update_vertices(mesh._h, _ptr(v), mesh.n_verts, int(bool(refresh_seed_grid)),
+                                  _stream(stream)), "p2m_update_vertices")
+    return v
 
 
 def _torch_autograd():
@@ -316,7 +335,12 @@ def _torch_autograd():
 
         @staticmethod
         def forward(ctx, q, verts, mesh):
+            # the query runs on the positions it is given: the mesh's vertex
+            # records are refreshed from `verts` first (p2m_update_vertices;
+            # the interception tables stay those of the build)
+            keep = _update_vertices(mesh, verts)
             r = mesh.query(q.contiguous(), closest=True, prim_type=False, save=True)
+            ctx.keep = keep  # the refresh's source stays alive until its kernels ran
             ctx.mesh = mesh
             ctx.n_verts = verts.shape[0]
             ctx.save_for_backward(q, r["dist"], r["closest"], r["save"])
@@ -341,7 +365,10 @@ _autograd_cls = None
 
 
 def distance(q, verts, mesh):
-    """Differentiable point-to-mesh distance: returns (dist, prim_id)."""
+    """Differentiable point-to-mesh distance: returns (dist, prim_id).  The
+    query runs on the vertex positions `verts` (the mesh's geometry is
+    refreshed from them, its interception tables are the build's), and
+    gradients flow to q and to verts."""
     global _autograd_cls
     if _autograd_cls is None:
         _autograd_cls = _torch_autograd()
@@ -447,14 +474,15 @@ class P2MBatch:
         t = BatchTuning()
         check(lib.p2m_batch_get_tuning(self._b, ctypes.byref(t)), "p2m_batch_get_tuning")
         return {"sort_bits": t.sort_bits, "tile": t.tile, "block_threads": t.block_threads,
-                "grid_ctas": t.grid_ctas, "group_by_vertex": t.group_by_vertex}
+                "grid_ctas": t.grid_ctas, "group_by_vertex": t.group_by_vertex,
+                "lanes_per_query": t.lanes_per_query}
 
     @tuning.setter
     def tuning(self, d):
         cur = self.tuning
         cur.update(d)
         t = BatchTuning(cur["sort_bits"], cur["tile"], cur["block_threads"], cur["grid_ctas"],
-                        cur["group_by_vertex"])
+                        cur["group_by_vertex"], cur["lanes_per_query"])
         check(lib.p2m_batch_set_tuning(self._b, ctypes.byref(t)), "p2m_batch_set_tuning")
 
     def close(self):

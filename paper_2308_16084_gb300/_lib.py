@@ -55,6 +55,7 @@ _SIGS = {
     "p2m_timing_summary": (_INT, [_P, _P]),
     "p2m_query_counters": (_INT, [_P, _P, _I64, _P, _P]),
     "p2m_backward": (_INT, [_P, _P, _P, _P, _P, _P, _I64, _P, _P, _P]),
+    "p2m_update_vertices": (_INT, [_P, _P, _I64, _INT, _P]),
     "p2m_batch_create": (_INT, [_P, _P, _INT, _P]),
     "p2m_batch_run": (_INT, [_P, _P]),
     "p2m_batch_get_tuning": (_INT, [_P, _P]),

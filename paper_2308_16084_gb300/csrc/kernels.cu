@@ -545,16 +545,19 @@ __device__ __forceinline__ void scan_chunk(const DevView &m, float qx, float qy,
 // mode 0: every entry box.  The three levels test the same query codes
 // against nested code boxes (an entry that admits q lies in a chunk and a
 // super-chunk that admit q), so every mode finds the same candidates.
+// With G lanes per query, lane `sub` takes every G-th super-chunk (mode 2)
+// or chunk (modes 0, 1) of the list, starting at its own index.
 template <bool COUNT>
 __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, float qz, int v,
-                                          int mode, Best &r, Work *wk) {
+                                          int mode, Best &r, Work *wk, uint32_t sub = 0,
+                                          uint32_t G = 1) {
   const uint32_t j0 = __ldg(&m.row_off[v]), j1 = __ldg(&m.row_off[v + 1]);
   const uint32_t c0 = __ldg(&m.chunk_off[v]), c1 = __ldg(&m.chunk_off[v + 1]);
   uint32_t gw[3];
   q_query_words(qx, qy, qz, m.qlo, m.qinv, gw);
   if (mode == 2 && m.supers) {
     const uint32_t s0 = __ldg(&m.super_off[v]), s1 = __ldg(&m.super_off[v + 1]);
-    for (uint32_t s = s0; s < s1; ++s) {
+    for (uint32_t s = s0 + sub; s < s1; s += G) {
       if (COUNT) ++wk->chunks;
       const uint4 sw = __ldg(&m.supers[s]);
       if (!q_pass(gw, sw.x, sw.y, sw.z)) continue;
@@ -568,10 +571,32 @@ __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, 
     return;
   }
   if (COUNT && mode == 1) wk->chunks += (int)(c1 - c0);
-  for (uint32_t c = c0; c < c1; ++c) {
+  for (uint32_t c = c0 + sub; c < c1; c += G) {
     const uint32_t first = j0 + 8 * (c - c0);
     scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), mode != 0, gw, r, wk);
   }
+}
+
+// The G lanes of one query (G a power of two, adjacent lanes of a warp)
+// each hold the best of their slice of the list; the query's best is the
+// minimum of (d^2, typed id) over the lanes, the same order test_entry keeps
+// (smaller distance, then lower typed id), so the result does not depend on
+// G.  Returns true in the one lane whose own best is the query's (the
+// lowest such lane), which writes the record.
+template <int G>
+__device__ __forceinline__ bool group_best(const Best &r) {
+  if (G == 1) return true;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(unsigned)(G - 1)));
+  const unsigned long long key = ((unsigned long long)__float_as_uint(r.d2) << 32) | r.tid;
+  unsigned long long best = key;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(gmask, best, o, G);
+    best = other < best ? other : best;
+  }
+  const unsigned hold = __ballot_sync(gmask, key == best) & gmask;
+  return (int)lane == __ffs(hold) - 1;
 }
 
 template <bool COUNT = false>
@@ -854,16 +879,23 @@ __global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
 // (closest xyz, distance), rec[2o+1] = (type << 30 | id, w1, w2, status):
 // a whole sector per query, where separate outputs would each dirty part of
 // one.  k_unpack then streams the records into the requested outputs.
+// G threads per query (1, 2, 4 or 8): the G adjacent lanes of a query split
+// its list (scan_list) and keep the best with one shuffle reduction
+// (group_best); whole groups enter and leave together.
+template <int G>
 __global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS)
 k_list_pass(DevView m, const float4 *__restrict__ gq, const uint32_t *__restrict__ gv, int64_t n,
             int chunked, float4 *__restrict__ rec) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / G;
+  const uint32_t sub = (uint32_t)(t & (G - 1));
   if (i >= n) return;
   const float4 s = gq[i];
   const int64_t o = __float_as_int(s.w);
   const bool ok = finite3(s.x, s.y, s.z);
   uint32_t st = ok ? 0u : 2u;
   if (!ok) {
+    if (sub) return;
     const float nan = __int_as_float(0x7fc00000);
     rec[2 * o] = make_float4(nan, nan, nan, nan);
     rec[2 * o + 1] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, __uint_as_float(st));
@@ -884,7 +916,8 @@ k_list_pass(DevView m, const float4 *__restrict__ gq, const uint32_t *__restrict
   r.w0 = 1.f;
   r.w1 = 0.f;
   r.w2 = 0.f;
-  scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr);
+  scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr, sub, G);
+  if (!group_best<G>(r)) return;
   rec[2 * o] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
   rec[2 * o + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(st));
 }
@@ -951,6 +984,126 @@ __global__ void k_seed_grid(DevView m, uint32_t *__restrict__ seed) {
   const float y = m.dom_lo[1] + (iy + 0.5f) * (m.dom_hi[1] - m.dom_lo[1]) / (float)G;
   const float z = m.dom_lo[2] + (iz + 0.5f) * (m.dom_hi[2] - m.dom_lo[2]) / (float)G;
   seed[i] = (uint32_t)nearest_pos(m, x, y, z);
+}
+
+// --------------------------------------------- moved vertices (a9 support)
+// p2m_update_vertices: the vertex-dependent records of the layout from new
+// positions, with the builder's arithmetic (float differences; double
+// products, sums and quotients rounded one by one, as the host builder
+// compiled without contraction), so that unchanged positions give unchanged
+// records bit for bit.  The interception lists and Region boxes stay those
+// of the build.
+__global__ void k_update_points(float4 *__restrict__ kd_points, int64_t nv,
+                                const float *__restrict__ verts) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nv) return;
+  float4 c = kd_points[p];
+  const int64_t v = __float_as_int(c.w);
+  c.x = verts[3 * v];
+  c.y = verts[3 * v + 1];
+  c.z = verts[3 * v + 2];
+  kd_points[p] = c;
+}
+
+__global__ void k_update_neighbours(float4 *__restrict__ nbp, const uint32_t *__restrict__ nb,
+                                    int64_t count, const float4 *__restrict__ kd_points) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const float4 c = kd_points[nb[k]];
+  float4 o = nbp[k];
+  o.x = c.x;
+  o.y = c.y;
+  o.z = c.z;
+  nbp[k] = o;
+}
+
+__global__ void k_update_edges(float4 *__restrict__ edge_rec, const int2 *__restrict__ edges,
+                               int64_t ne, const float *__restrict__ verts) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int2 ab = edges[e];
+  const float *a = verts + 3 * (int64_t)ab.x, *b = verts + 3 * (int64_t)ab.y;
+  const float dx = __fsub_rn(b[0], a[0]), dy = __fsub_rn(b[1], a[1]), dz = __fsub_rn(b[2], a[2]);
+  const double l2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  edge_rec[2 * e] = make_float4(a[0], a[1], a[2], __double2float_rn(__ddiv_rn(1.0, l2)));
+  edge_rec[2 * e + 1] = make_float4(dx, dy, dz, 0.f);
+}
+
+__global__ void k_update_faces(float4 *__restrict__ face_rec, const int4 *__restrict__ tris,
+                               int64_t nf, const float *__restrict__ verts) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int4 t = tris[f];
+  const float *a = verts + 3 * (int64_t)t.x, *b = verts + 3 * (int64_t)t.y,
+              *c = verts + 3 * (int64_t)t.z;
+  double e1[3], e2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = __dsub_rn((double)b[d], (double)a[d]);
+    e2[d] = __dsub_rn((double)c[d], (double)a[d]);
+  }
+  auto dot = [](const double *x, const double *y) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x[0], y[0]), __dmul_rn(x[1], y[1])),
+                     __dmul_rn(x[2], y[2]));
+  };
+  const double d00 = dot(e1, e1), d01 = dot(e1, e2), d11 = dot(e2, e2);
+  const double den = __dsub_rn(__dmul_rn(d00, d11), __dmul_rn(d01, d01));
+  // a face the build found degenerate keeps its NaN weights (it is in no list)
+  const bool degenerate = isnan(face_rec[3 * f].w);
+  const float nan = __int_as_float(0x7fc00000);
+  face_rec[3 * f] = make_float4(a[0], a[1], a[2],
+                                degenerate ? nan : __double2float_rn(__ddiv_rn(d11, den)));
+  face_rec[3 * f + 1] = make_float4(__double2float_rn(e1[0]), __double2float_rn(e1[1]),
+                                    __double2float_rn(e1[2]),
+                                    degenerate ? nan : __double2float_rn(__ddiv_rn(d01, den)));
+  face_rec[3 * f + 2] = make_float4(__double2float_rn(e2[0]), __double2float_rn(e2[1]),
+                                    __double2float_rn(e2[2]),
+                                    degenerate ? nan : __double2float_rn(__ddiv_rn(d00, den)));
+}
+
+// child boxes of the internal nodes first .. first + count - 1 (one level
+// of the tree), from their children: the points of a leaf, or the two boxes
+// an internal child stores (filled by the previous launch)
+__global__ void k_update_kd_level(float4 *__restrict__ kd_nodes,
+                                  const float4 *__restrict__ kd_points, int64_t nv, int depth,
+                                  int64_t first, int64_t count) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t i = first + t;
+  const int64_t nleaf0 = ((int64_t)1 << depth) - 1;
+  float lo[2][3], hi[2][3];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int64_t c = 2 * i + 1 + k;
+    for (int d = 0; d < 3; ++d) {  // an empty leaf keeps the builder's (+inf, -inf)
+      lo[k][d] = __int_as_float(0x7f800000);
+      hi[k][d] = __int_as_float(0xff800000);
+    }
+    if (c >= nleaf0) {
+      const int64_t j = c - nleaf0;
+      const int64_t p0 = (j * nv) >> depth, p1 = ((j + 1) * nv) >> depth;
+      for (int64_t p = p0; p < p1; ++p) {
+        const float4 q = kd_points[p];
+        lo[k][0] = fminf(lo[k][0], q.x);
+        lo[k][1] = fminf(lo[k][1], q.y);
+        lo[k][2] = fminf(lo[k][2], q.z);
+        hi[k][0] = fmaxf(hi[k][0], q.x);
+        hi[k][1] = fmaxf(hi[k][1], q.y);
+        hi[k][2] = fmaxf(hi[k][2], q.z);
+      }
+    } else {
+      const float4 A = kd_nodes[3 * c], B = kd_nodes[3 * c + 1], C = kd_nodes[3 * c + 2];
+      lo[k][0] = fminf(A.x, B.z);
+      lo[k][1] = fminf(A.y, B.w);
+      lo[k][2] = fminf(A.z, C.x);
+      hi[k][0] = fmaxf(A.w, C.y);
+      hi[k][1] = fmaxf(B.x, C.z);
+      hi[k][2] = fmaxf(B.y, C.w);
+    }
+  }
+  kd_nodes[3 * i] = make_float4(lo[0][0], lo[0][1], lo[0][2], hi[0][0]);
+  kd_nodes[3 * i + 1] = make_float4(hi[0][1], hi[0][2], lo[1][0], lo[1][1]);
+  kd_nodes[3 * i + 2] = make_float4(lo[1][2], hi[1][0], hi[1][1], hi[1][2]);
 }
 
 // ------------------------------------------------------------------ a9
@@ -1123,6 +1276,7 @@ __global__ void k_batch_nn(BatchDesc d, const float4 *__restrict__ sorted, int64
   key_rank[i] = count_key((uint32_t)d.voff[k] + v, vhist);
 }
 
+template <int G>
 __global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS)
 k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__restrict__ gv,
              int64_t total, int tile, float4 *__restrict__ rec, unsigned int *queue_head,
@@ -1138,13 +1292,16 @@ k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__
     const int64_t it = s_item;
     if (it >= n_items) break;
     const int64_t base = it * (int64_t)tile;
-    for (int t = threadIdx.x; t < tile; t += blockDim.x) {
-      const int64_t pos = base + t;
+    // G adjacent threads per query: the G lanes of a query share its
+    // position, so they take every branch below together
+    for (int u = threadIdx.x; u < tile * G; u += blockDim.x) {
+      const int64_t pos = base + u / G;
+      const uint32_t sub = (uint32_t)(u & (G - 1));
       if (pos >= total) break;
       const float4 s = grouped[pos];
       const int64_t gi = __float_as_int(s.w);
       if (gi < 0 || gi >= total) {
-        atomicOr(error_word, 1u);
+        if (!sub) atomicOr(error_word, 1u);
         continue;
       }
       const int k = mesh_of(s_off, d.n_meshes, gi);
@@ -1152,6 +1309,7 @@ k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__
       const int64_t v = (int64_t)gv[pos] - d.voff[k];
       const bool ok = finite3(s.x, s.y, s.z);
       if (!ok || v < 0 || v >= m.nv) {
+        if (sub) continue;
         if (ok) atomicOr(error_word, 2u);
         const float nan = __int_as_float(0x7fc00000);
         rec[2 * gi] = make_float4(nan, nan, nan, nan);
@@ -1169,7 +1327,8 @@ k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__
       r.w0 = 1.f;
       r.w1 = 0.f;
       r.w2 = 0.f;
-      scan_list<false>(m, s.x, s.y, s.z, (int)v, 2, r, nullptr);
+      scan_list<false>(m, s.x, s.y, s.z, (int)v, 2, r, nullptr, sub, G);
+      if (!group_best<G>(r)) continue;
       rec[2 * gi] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
       rec[2 * gi + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(0u));
     }
@@ -1290,7 +1449,16 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
     k_vertex_scatter<<<blocks_for(n, T), T, 0, stream>>>(sorted, n, key_rank, voff, grouped_q,
                                                          gv);
     if (ev) cudaEventRecord(ev[3], stream);
-    k_list_pass<<<blocks_for(n, bt), bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
+    const int G = tune.lanes_per_query;
+    const unsigned lb = blocks_for(n * G, bt);
+    if (G == 8)
+      k_list_pass<8><<<lb, bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
+    else if (G == 4)
+      k_list_pass<4><<<lb, bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
+    else if (G == 2)
+      k_list_pass<2><<<lb, bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
+    else
+      k_list_pass<1><<<lb, bt, 0, stream>>>(m, grouped_q, gv, n, tune.chunked, rec);
     if (ev) cudaEventRecord(ev[4], stream);
     k_unpack<<<blocks_for(n, T), T, 0, stream>>>(rec, n, dist, closest, prim_id, prim_type, save,
                                                  status);
@@ -1353,6 +1521,26 @@ cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
   return cudaGetLastError();
 }
 
+cudaError_t launch_update_vertices(const GeometryRefs &g, const float *verts,
+                                   cudaStream_t stream) {
+  const int T = 256;
+  if (g.nv <= 0) return cudaSuccess;
+  k_update_points<<<blocks_for(g.nv, T), T, 0, stream>>>(g.kd_points, g.nv, verts);
+  if (g.n_nb > 0 && g.nbp && g.nb)
+    k_update_neighbours<<<blocks_for(g.n_nb, T), T, 0, stream>>>(g.nbp, g.nb, g.n_nb,
+                                                                  g.kd_points);
+  if (g.ne > 0)
+    k_update_edges<<<blocks_for(g.ne, T), T, 0, stream>>>(g.edge_rec, g.edges, g.ne, verts);
+  if (g.nf > 0)
+    k_update_faces<<<blocks_for(g.nf, T), T, 0, stream>>>(g.face_rec, g.tris, g.nf, verts);
+  for (int l = g.depth - 1; l >= 0; --l) {
+    const int64_t first = ((int64_t)1 << l) - 1, count = (int64_t)1 << l;
+    k_update_kd_level<<<blocks_for(count, T), T, 0, stream>>>(g.kd_nodes, g.kd_points, g.nv,
+                                                              g.depth, first, count);
+  }
+  return cudaGetLastError();
+}
+
 size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits, int64_t nv_keys) {
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t nb = (size_t)n_meshes << sort_bits;
@@ -1367,8 +1555,8 @@ size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits, int64_t n
 
 int batch_occupancy(int block_threads, int group_by_vertex) {
   int blocks = 0;
-  if (group_by_vertex)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_list, block_threads, 0);
+  if (group_by_vertex)  // the G variants differ only in index arithmetic
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_list<1>, block_threads, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_query, block_threads, 0);
   return blocks > 0 ? blocks : 1;
@@ -1418,8 +1606,15 @@ cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_
     bucket_scan(vhist, voff, tiles, (int)nv_keys, stream);
     k_vertex_scatter<<<blocks_for(total, T), T, 0, stream>>>(sorted, total, key_rank, voff,
                                                              grouped, gv);
-    k_batch_list<<<grid, t.block_threads, 0, stream>>>(d, grouped, gv, total, t.tile, rec,
-                                                       queue_head, error_word);
+    if (t.lanes_per_query == 4)
+      k_batch_list<4><<<grid, t.block_threads, 0, stream>>>(d, grouped, gv, total, t.tile, rec,
+                                                            queue_head, error_word);
+    else if (t.lanes_per_query == 2)
+      k_batch_list<2><<<grid, t.block_threads, 0, stream>>>(d, grouped, gv, total, t.tile, rec,
+                                                            queue_head, error_word);
+    else
+      k_batch_list<1><<<grid, t.block_threads, 0, stream>>>(d, grouped, gv, total, t.tile, rec,
+                                                            queue_head, error_word);
     k_batch_unpack<<<blocks_for(total, T), T, 0, stream>>>(d, rec, total);
     return cudaGetLastError();
   }

@@ -49,6 +49,7 @@ struct QueryTuning {
                             // vertex, then the list pass (two kernels)
   int sort_key = 0;  // 0: Morton buckets (2^sort_bits); 1: the seed-grid vertex of
                      // the query's cell (with group_by_vertex and a seed grid)
+  int lanes_per_query = 1;  // threads per query in the list pass (1, 2, 4, 8)
 };
 
 // Scratch needed by launch_query for n points, in bytes (nv: vertices of
@@ -75,6 +76,25 @@ cudaError_t launch_nearest(const DevView &m, const float *xyz, int64_t n, int32_
 // Fill the seed grid: nearest vertex (row) of every cell centre of the
 // G^3 grid over D (G = 2^view.grid_bits), by KD-tree backtracking.
 cudaError_t launch_seed_grid(const DevView &m, uint32_t *seed, cudaStream_t stream);
+
+// Mutable device arrays of the vertex-dependent geometry (p2m_update_vertices).
+struct GeometryRefs {
+  float4 *kd_points;   // nv
+  float4 *kd_nodes;    // (2^depth - 1) * 3
+  float4 *nbp;         // n_nb
+  const uint32_t *nb;  // n_nb
+  float4 *edge_rec;    // 2 * ne
+  float4 *face_rec;    // 3 * nf
+  const int2 *edges;   // ne
+  const int4 *tris;    // nf
+  int64_t nv, n_nb, ne, nf;
+  int depth;
+};
+
+// New vertex positions (original order, nv x 3 float, device): KD points and
+// child boxes, neighbour positions, edge and face records.
+cudaError_t launch_update_vertices(const GeometryRefs &g, const float *verts,
+                                   cudaStream_t stream);
 
 // Backward scatter (a9).
 cudaError_t launch_backward(const DevView &m, const float *q, const float *dist,
@@ -106,6 +126,7 @@ struct BatchTuning {
   int block_threads = 256;
   int grid_ctas = 0;
   int group_by_vertex = 1;  // two-pass: nearest vertex, regroup, persistent list pass
+  int lanes_per_query = 1;  // threads per query in the persistent list pass (1, 2, 4)
 };
 size_t batch_scratch_bytes(int64_t total, int n_meshes, int sort_bits, int64_t nv_keys = 0);
 cudaError_t launch_batch(const BatchDesc &d, int64_t total, void *scratch, size_t scratch_bytes,

@@ -391,6 +391,7 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   t->chunked = h->tune.chunked;
   t->group_by_vertex = h->tune.group_by_vertex;
   t->sort_key = h->tune.sort_key;
+  t->lanes_per_query = h->tune.lanes_per_query;
   return P2M_OK;
 }
 
@@ -404,6 +405,10 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
   if (t->chunked < 0 || t->chunked > 2) return P2M_ERR_INVALID_ARG;
   if (t->group_by_vertex != 0 && t->group_by_vertex != 1) return P2M_ERR_INVALID_ARG;
   if (t->sort_key != 0 && t->sort_key != 1) return P2M_ERR_INVALID_ARG;
+  if (t->lanes_per_query != 1 && t->lanes_per_query != 2 && t->lanes_per_query != 4 &&
+      t->lanes_per_query != 8)
+    return P2M_ERR_INVALID_ARG;
+  h->tune.lanes_per_query = t->lanes_per_query;
   h->tune.group_by_vertex = t->group_by_vertex;
   h->tune.sort_key = t->sort_key;
   h->tune.nn_walk = t->nn_walk;
@@ -690,6 +695,39 @@ p2m_status p2m_backward(p2m_handle *h, const float *q, const float *dist, const 
                                         grad_dist, n, grad_q, grad_verts, (cudaStream_t)stream));
 }
 
+p2m_status p2m_update_vertices(p2m_handle *h, const float *verts, int64_t n_verts,
+                               int refresh_seed_grid, void *stream) {
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (!verts || n_verts != h->L.nv) return P2M_ERR_INVALID_ARG;
+  if (refresh_seed_grid != 0 && refresh_seed_grid != 1) return P2M_ERR_INVALID_ARG;
+  p2m::GeometryRefs g{};
+  g.kd_points = (float4 *)h->kd_points.p;
+  g.kd_nodes = (float4 *)h->kd_nodes.p;
+  g.nbp = (float4 *)h->nbp.p;
+  g.nb = h->nb.p;
+  g.edge_rec = (float4 *)h->edge_rec.p;
+  g.face_rec = (float4 *)h->face_rec.p;
+  g.edges = (const int2 *)h->edges.p;
+  g.tris = (const int4 *)h->tris.p;
+  g.nv = h->L.nv;
+  g.n_nb = (int64_t)h->nb.n;
+  g.ne = h->L.ne;
+  g.nf = h->L.nf;
+  g.depth = h->L.kd_depth;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = p2m::launch_update_vertices(g, verts, st);
+  if (e == cudaSuccess && refresh_seed_grid && h->seed.p) {
+    e = p2m::launch_seed_grid(h->view, h->seed.p, st);
+    if (e == cudaSuccess && h->sort_seed.p) {
+      p2m::DevView v2 = h->view;
+      v2.grid_bits = h->sort_grid_bits;
+      e = p2m::launch_seed_grid(v2, h->sort_seed.p, st);
+    }
+  }
+  return from_cuda(e);
+}
+
 p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges) {
   if (!h || !n_edges) return P2M_ERR_INVALID_ARG;
   *n_edges = h->L.ne;
@@ -871,6 +909,7 @@ p2m_status p2m_batch_get_tuning(const p2m_batch *b, p2m_batch_tuning *t) {
   t->block_threads = b->tune.block_threads;
   t->grid_ctas = b->tune.grid_ctas;
   t->group_by_vertex = b->tune.group_by_vertex;
+  t->lanes_per_query = b->tune.lanes_per_query;
   return P2M_OK;
 }
 
@@ -881,6 +920,8 @@ p2m_status p2m_batch_set_tuning(p2m_batch *b, const p2m_batch_tuning *t) {
     return P2M_ERR_INVALID_ARG;
   if (t->tile <= 0 || t->tile % t->block_threads) return P2M_ERR_INVALID_ARG;
   if (t->group_by_vertex != 0 && t->group_by_vertex != 1) return P2M_ERR_INVALID_ARG;
+  if (t->lanes_per_query != 1 && t->lanes_per_query != 2 && t->lanes_per_query != 4)
+    return P2M_ERR_INVALID_ARG;
   if (((int64_t)b->n << t->sort_bits) > ((int64_t)1 << 24)) return P2M_ERR_TOO_LARGE;
   if (t->group_by_vertex && b->nv_keys > ((int64_t)1 << 24)) return P2M_ERR_TOO_LARGE;
   p2m_status s = b->ensure(t->sort_bits, t->group_by_vertex);
@@ -890,6 +931,7 @@ p2m_status p2m_batch_set_tuning(p2m_batch *b, const p2m_batch_tuning *t) {
   b->tune.block_threads = t->block_threads;
   b->tune.grid_ctas = t->grid_ctas;
   b->tune.group_by_vertex = t->group_by_vertex;
+  b->tune.lanes_per_query = t->lanes_per_query;
   return P2M_OK;
 }
 
@@ -919,14 +961,16 @@ p2m_status p2m_batch_autotune(p2m_batch *b, int reps, void *stream, float *best_
   const int tile_c[] = {256, 1024, 4096};
   const int block_c[] = {128, 256};
   p2m_status status = P2M_OK;
+  // threads per query (lanes) is tried on the grouped path only
   for (int group = 1; group >= 0; --group)
+   for (int lanes = 1; lanes <= (group ? 4 : 1); lanes *= 2)
     for (int bits : bits_c)
       for (int tile : tile_c)
         for (int bt : block_c) {
           if (tile % bt) continue;
           if (((int64_t)b->n << bits) > ((int64_t)1 << 22)) continue;
           if (group && b->nv_keys > ((int64_t)1 << 24)) continue;
-          p2m_batch_tuning t{bits, tile, bt, 0, group};
+          p2m_batch_tuning t{bits, tile, bt, 0, group, lanes};
         if (p2m_batch_set_tuning(b, &t) != P2M_OK) continue;
         if ((status = p2m_batch_run(b, st))) goto done;
         cudaEventRecord(e0, st);
@@ -984,15 +1028,23 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   float bms = 1e30f;
   const int bits_c[] = {12, 15, 18, 21, 24};
   const int block_c[] = {128, 256};
+  // threads per query: in the one-pass kernel, one thread per query (wm = 0)
+  // or a warp answering 32 queries together (wm = 1); in the two-pass path,
+  // 1, 2, 4 or 8 lanes splitting each query's list (lanes)
   for (int gv = 0; gv < 2; ++gv)
   for (int ch = 2; ch < 3; ++ch)
-  for (int wm = 0; wm < 1; ++wm)
+  for (int wm = 0; wm < 2; ++wm)
+  for (int lanes = 1; lanes <= 8; lanes *= 2)
   for (int key = 0; key < 2; ++key)
   for (int bits : bits_c)
     for (int bt : block_c) {
+      if (wm == 1 && gv == 1) continue;
+      if (lanes > 1 && gv == 0) continue;
       // sorting by seed vertex ignores sort_bits and needs the regrouping
       if (key == 1 && (gv == 0 || bits != bits_c[0] || !h->seed.p)) continue;
-      p2m_tuning t{bits, bt, wm, 2, ch, gv, key};
+      // the lane split is tried with the first sort's best-known settings only
+      if (lanes > 1 && (key != 1 && bits != bits_c[2])) continue;
+      p2m_tuning t{bits, bt, wm, 2, ch, gv, key, lanes};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);
