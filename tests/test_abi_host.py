@@ -12,6 +12,7 @@ import pytest
 
 import datagen as dg
 import oracle
+from tests.table_util import check_tables_against_oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -140,36 +141,7 @@ def test_invalid_segments_return_status(pg):
 
 
 def _check_tables(pg, m):
-    h = _host(pg, m)
-    o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin,
-                          segs=m.meta.get("segs"))
-    np.testing.assert_array_equal(h.edges(), o.edges())
-    st = h.stats()
-    assert st["n_entries"] == o.n_entries
-    assert st["neighbour_pairs"] == o.n_neighbor_pairs
-    off, tt, ii, bb = o.table()
-    delta = h.domain()[2]
-    assert abs(delta - o.delta) <= 1e-6 * o.delta
-    for v in range(o.nv):
-        t, i, b = h.interception_list(v)
-        a = set(zip(t.tolist(), i.tolist()))
-        r = set(zip(tt[off[v]:off[v + 1]].tolist(), ii[off[v]:off[v + 1]].tolist()))
-        assert a == r, v
-        # float32 Region boxes contain the oracle's FP64 boxes, up to the
-        # scatter of two independent computations of crossing points, which
-        # near tangential crossings is of order sqrt(eps) and stays far below
-        # the delta padding of every box
-        order_r = np.lexsort((ii[off[v]:off[v + 1]], tt[off[v]:off[v + 1]]))
-        order_a = np.lexsort((i, t))
-        ob = bb[off[v]:off[v + 1]][order_r]
-        hb = b[order_a].astype(np.float64)
-        tol = 1e-2 * delta
-        assert (hb[:, :3] <= ob[:, :3] + tol).all() and (hb[:, 3:] >= ob[:, 3:] - tol).all()
-        # and the integer box codes stay tight: a few codes of the chunk's
-        # frame (at most 2^-12 of the domain) beyond the FP64 box
-        slack = 2.0 ** -12 * (np.asarray(h.domain()[1]) - np.asarray(h.domain()[0]))
-        assert (hb[:, :3] >= ob[:, :3] - slack - tol).all()
-        assert (hb[:, 3:] <= ob[:, 3:] + slack + tol).all()
+    check_tables_against_oracle(_host(pg, m), m)
 
 
 def test_builder_thread_count_does_not_change_tables(pg):
@@ -280,11 +252,12 @@ def test_tuning_fields_are_validated(pg):
     h = _host(pg, m)
     base = h.tuning
     assert set(base) == {"sort_bits", "block_threads", "warp_cooperative", "nn_walk",
-                         "chunked", "group_by_vertex", "sort_key"}
+                         "chunked", "group_by_vertex", "sort_key", "lanes_per_query"}
     h.tuning = {"sort_key": 1, "block_threads": 128, "sort_bits": 12}
     assert h.tuning["sort_key"] == 1 and h.tuning["block_threads"] == 128
     for bad in ({"sort_key": 2}, {"group_by_vertex": 3}, {"chunked": 3}, {"nn_walk": -1},
-                {"block_threads": 96}, {"sort_bits": 25}, {"warp_cooperative": 2}):
+                {"block_threads": 96}, {"sort_bits": 25}, {"warp_cooperative": 2},
+                {"lanes_per_query": 3}, {"lanes_per_query": 16}, {"lanes_per_query": 0}):
         with pytest.raises(pg.P2MError) as e:
             h.tuning = bad
         assert e.value.code == 1

@@ -195,6 +195,29 @@ def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked, 
         np.testing.assert_array_equal(got[k], base[k])
 
 
+@pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 6}), (2, {"grid": 96})])
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("chunked", [0, 1, 2])
+@pytest.mark.parametrize("threads", [64, 512])
+def test_lanes_per_query_give_identical_results(pg, idx, kw, lanes, chunked, threads):
+    """Splitting each query's list over 2, 4 or 8 lanes (the threads-per-
+    query axis of the autotuner) changes the order of work, not one bit of
+    the outputs; a ragged query count leaves a partial group at the end."""
+    m = dg.workload(idx, n_queries=40003, **kw)
+    mesh = build(pg, m)
+    mesh.tuning = {"chunked": chunked, "block_threads": threads, "lanes_per_query": 1}
+    base = run(mesh, m.queries)
+    mesh.tuning = {"lanes_per_query": lanes}
+    assert mesh.tuning["lanes_per_query"] == lanes
+    got = run(mesh, m.queries)
+    for k in ("dist", "closest", "prim_id", "prim_type", "status"):
+        np.testing.assert_array_equal(got[k], base[k])
+    r = mesh.query(torch.from_numpy(m.queries).cuda(), closest=True, prim_type=True, save=True)
+    mesh.tuning = {"lanes_per_query": 1}
+    r1 = mesh.query(torch.from_numpy(m.queries).cuda(), closest=True, prim_type=True, save=True)
+    assert torch.equal(r["save"], r1["save"])
+
+
 @pytest.mark.parametrize("idx,kw", [(0, {}), (2, {"grid": 96}), (1, {"level": 5})])
 @pytest.mark.parametrize("threads", [64, 256])
 @pytest.mark.parametrize("chunked", [0, 2])
@@ -355,7 +378,8 @@ def test_backward_against_oracle_gradient(pg):
     gq_ref, bv, gv = oracle.gradient(m.queries.astype(np.float64), ref, m.weights.astype(np.float64))
     keep = (ref["dist"] > 1e-4) & (ref["second"] - ref["dist"] > 1e-4)
     gq = q.grad.cpu().numpy()
-    assert np.abs(gq[keep] - gq_ref[keep]).max() < 2e-3
+    gerr = np.abs(gq[keep] - gq_ref[keep]).max(1)
+    assert (gerr <= pu.grad_tolerance(ref["dist"][keep], m.verts)).all(), gerr.max()
     # vertex gradient: scatter the oracle's per-query contributions of the
     # same (non-tie) queries and compare with a second GPU pass on them
     qs = torch.from_numpy(m.queries[keep]).cuda()
@@ -404,15 +428,15 @@ def _batch_meshes(pg, n_meshes=6):
     return ms, meshes
 
 
-@pytest.mark.parametrize("group", [1, 0])
-def test_batched_matches_single_and_oracle(pg, group):
+@pytest.mark.parametrize("group,lanes", [(1, 1), (0, 1), (1, 2), (1, 4)])
+def test_batched_matches_single_and_oracle(pg, group, lanes):
     ms, meshes = _batch_meshes(pg)
     qs = [torch.from_numpy(m.queries).cuda() for m in ms]
     # a few non-finite queries in one mesh
     qs[1][:3] = torch.tensor([[float("nan"), 0, 0], [0, float("inf"), 0], [0, 0, -float("inf")]])
     b = pg.P2MBatch(meshes, qs, closest=True, prim_type=True)
-    b.tuning = {"group_by_vertex": group}
-    assert b.tuning["group_by_vertex"] == group
+    b.tuning = {"group_by_vertex": group, "lanes_per_query": lanes}
+    assert b.tuning["group_by_vertex"] == group and b.tuning["lanes_per_query"] == lanes
     out = b.run()
     b.check()
     torch.cuda.synchronize()
@@ -543,7 +567,8 @@ def test_full_size_fwd_bwd_sampled(pg):
     gq_ref, _, _ = oracle.gradient(m.queries[sel].astype(np.float64), ref,
                                    m.weights[sel].astype(np.float64))
     keep = (ref["dist"] > 1e-4) & (ref["second"] - ref["dist"] > 1e-4)
-    assert np.abs(q.grad.cpu().numpy()[sel][keep] - gq_ref[keep]).max() < 2e-3
+    gerr = np.abs(q.grad.cpu().numpy()[sel][keep] - gq_ref[keep]).max(1)
+    assert (gerr <= pu.grad_tolerance(ref["dist"][keep], m.verts)).all(), gerr.max()
     g = verts.grad
     assert torch.isfinite(g).all()
     # every query's weight reaches the vertices: sum of vertex gradients
