@@ -505,7 +505,8 @@ def forward_roofline(mesh, q, n, tsum, ms_step, steps):
     cnt = mesh.counters(q)
     nn_b, list_b, out_b = phase_bytes(cnt, n)
     calls = max(1, tsum["calls"])
-    grouped = tsum["nn_ms"] > 0
+    tune = mesh.tuning
+    grouped = bool(tune["group_by_vertex"]) and not tune["warp_cooperative"]
     phases = {"sort_ms": tsum["sort_ms"] / calls, "nn_pass_ms": tsum["nn_ms"] / calls,
               "regroup_ms": tsum["regroup_ms"] / calls, "list_pass_ms": tsum["list_ms"] / calls,
               "output_ms": tsum["output_ms"] / calls}

@@ -8,9 +8,12 @@ code, neighbour list and the inspection count)."""
 import os
 import tempfile
 
+import numpy as np
 import pytest
 
 import datagen as dg
+from tests import parity_util as pu
+from tests.table_util import check_tables_against_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -56,3 +59,27 @@ def test_device_flood_builds_the_host_layout(pg, name):
         ba, bb = open(pa, "rb").read(), open(pb, "rb").read()
     assert len(ba) == len(bb)
     assert ba == bb
+
+
+@pytest.mark.parametrize("name", ["sphere-L3", "displaced-L4", "heightfield-40",
+                                  "soup-penetrating-L3", "mixed-L2-wire-L1"])
+def test_device_flood_tables_equal_the_oracle_and_queries_match_bruteforce(pg, name):
+    """The device-flooded build against the oracle directly: the same
+    interception lists with boxes containing the oracle's, and queries on
+    it matching the FP64 brute force."""
+    import torch
+    m = CASES[name]()
+    a = pg.P2M(m.verts, m.tris, device_assist=2, segs=m.meta.get("segs"),
+               domain_scale=m.domain_scale, domain_margin=m.domain_margin)
+    assert a.flood_stats()["device"] > 0
+    o = check_tables_against_oracle(a, m, same_neighbour_count=False)
+    rng = np.random.default_rng(31)
+    v64 = m.verts.astype(np.float64)
+    q = np.concatenate([dg.uniform_in_box(v64, 1.2, 20000, rng),
+                        v64[rng.integers(0, v64.shape[0], 5001)] +
+                        rng.normal(0, 0.01 * dg.bbox_diagonal(v64), (5001, 3))]).astype(np.float32)
+    r = a.query(torch.from_numpy(q).cuda(), closest=True, prim_type=True)
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in r.items()}
+    ref = o.bruteforce(q)
+    pu.check(m.verts, o.edges(), m.tris, q, gpu, ref, pu.tolerance(m.verts), f"device flood {name}")
