@@ -1100,7 +1100,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
             grow(x0);
           }
           if ((g0 > 0) != (g1 > 0)) {
-            // g restricted to the edge is a quadratic in t: exact roots
+            // g restricted to the edge is a quadratic in t: bracket its zero
             V3 d = x1 - x0, w0 = x0 - g.a, r0 = x0 - pv;
             double du = dot(d, g.u), wu = dot(w0, g.u);
             double A, B, Cc;
@@ -1113,23 +1113,10 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
               B = 2 * dot(r0, d) - 2 * wu * du;
               Cc = len2(r0) - wu * wu + eta;
             }
-            double roots[2];
-            int nr = 0;
-            if (std::fabs(A) <= 1e-14 * (std::fabs(B) + std::fabs(Cc))) {
-              if (B != 0) roots[nr++] = -Cc / B;
-            } else {
-              double disc = std::max(0.0, B * B - 4 * A * Cc);
-              double sq = std::sqrt(disc);
-              double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
-              if (qq != 0) roots[nr++] = Cc / qq;
-              roots[nr++] = qq / A;
-            }
-            for (int r = 0; r < nr; ++r) {
-              double tt = roots[r];
-              if (!(tt >= -1e-9 && tt <= 1 + 1e-9)) continue;
-              tt = std::min(1.0, std::max(0.0, tt));
-              grow(x0 + tt * d);
-            }
+            double tb[2];
+            fc::edge_crossing(A, B, Cc, g0 > 0, &tb[0], &tb[1]);
+            grow(x0 + tb[0] * d);
+            grow(x0 + tb[1] * d);
           }
         }
       }

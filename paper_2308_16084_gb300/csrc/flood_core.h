@@ -7,10 +7,10 @@
 // ConvexPoly(v, p) = Cell(v) ∩ Space-perp(p) by cutting v's widened cell with
 // p's half-spaces (Sec. 4.4), applies the relaxed filter of Thm. 5/6 at the
 // polytope's corners, and for an intercepting pair emits the Region box of
-// Sec. 4.6: the corners where the filter function is positive plus the exact
-// roots of the filter's quadratic along every polytope edge that changes
-// sign, widened by delta and rounded outward to float32.  Only intercepting
-// vertices spread the flood.
+// Sec. 4.6: the corners where the filter function is positive plus a tight
+// bracket of the filter's zero along every polytope edge that changes sign
+// (edge_crossing), widened by delta and rounded outward to float32.  Only
+// intercepting vertices spread the flood.
 //
 // Every step is plain IEEE double arithmetic (+, -, *, /, sqrt) in a fixed
 // order, and both compilers are told not to fuse multiply-adds, so the warp
@@ -52,6 +52,52 @@ P2M_HD bool lex_less(D3 a, D3 b) {
 // the selection rules of std::min / std::max (first argument on ties)
 P2M_HD double dmin(double a, double b) { return b < a ? b : a; }
 P2M_HD double dmax(double a, double b) { return a < b ? b : a; }
+
+// Where the filter crosses zero on one polytope edge x(t) = x0 + t (x1 - x0),
+// 0 <= t <= 1, whose end values g(x0), g(x1) lie on opposite sides of zero
+// (pos0: g(x0) > 0).  Along the edge the filter is the quadratic
+// p(t) = (A t + B) t + C with A >= 0 (its Hessian is positive semidefinite),
+// so the sign change brackets exactly one root.  The root is enclosed by a
+// regula falsi iteration that keeps the bracket, with the Illinois rule (the
+// retained end's value is halved when the same end is kept twice), until
+// the bracket is 2^-40 of the edge or 64 steps have passed; [*ta, *tb]
+// receives it.  The caller adds the points at both ends of the bracket to
+// the Region box: their box contains the segment between them, hence the
+// crossing, whatever the rounding of p.  If p disagrees with the end values
+// at an end (rounding at a crossing that close to it) that end is returned
+// as a zero-width bracket.
+P2M_HD void edge_crossing(double A, double B, double C, bool pos0, double *ta, double *tb) {
+  const double sg = pos0 ? 1.0 : -1.0;  // f = sg * p: positive at t = 0
+  double lo = 0.0, hi = 1.0;
+  double flo = sg * C, fhi = sg * ((A + B) + C);
+  if (!(flo > 0.0)) {
+    *ta = *tb = 0.0;
+    return;
+  }
+  if (fhi > 0.0) {
+    *ta = *tb = 1.0;
+    return;
+  }
+  int kept = 0;  // +1: lo moved last, -1: hi moved last
+  for (int it = 0; it < 64 && hi - lo > 0x1p-40; ++it) {
+    double t = (lo * fhi - hi * flo) / (fhi - flo);
+    if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+    const double ft = sg * ((A * t + B) * t + C);
+    if (ft > 0.0) {
+      lo = t;
+      flo = ft;
+      if (kept == 1) fhi *= 0.5;
+      kept = 1;
+    } else {
+      hi = t;
+      fhi = ft;
+      if (kept == -1) flo *= 0.5;
+      kept = -1;
+    }
+  }
+  *ta = lo;
+  *tb = hi;
+}
 
 // half-space n.x <= c
 struct HS {
@@ -342,7 +388,7 @@ P2M_HD int flood_prim(const Prim &P, double eps, double delta, double eta, Env &
           have = true;
         }
         if ((g0 > 0) != (g1 > 0)) {
-          // the filter along the edge is a quadratic in t: its exact roots
+          // the filter along the edge is a quadratic in t: bracket its zero
           const D3 d = x1 - x0, w0 = x0 - P.ga, r0 = x0 - pv;
           const double du = dot(d, P.gu), wu = dot(w0, P.gu);
           double A, B, Cc;
@@ -355,22 +401,10 @@ P2M_HD int flood_prim(const Prim &P, double eps, double delta, double eta, Env &
             B = 2 * dot(r0, d) - 2 * wu * du;
             Cc = len2(r0) - wu * wu + eta;
           }
-          double roots[2];
-          int nr = 0;
-          if (fabs(A) <= 1e-14 * (fabs(B) + fabs(Cc))) {
-            if (B != 0) roots[nr++] = -Cc / B;
-          } else {
-            const double disc = dmax(0.0, B * B - 4 * A * Cc);
-            const double sq = sqrt(disc);
-            const double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
-            if (qq != 0) roots[nr++] = Cc / qq;
-            roots[nr++] = qq / A;
-          }
-          for (int r = 0; r < nr; ++r) {
-            double tt = roots[r];
-            if (!(tt >= -1e-9 && tt <= 1 + 1e-9)) continue;
-            tt = dmin(1.0, dmax(0.0, tt));
-            const D3 x = x0 + tt * d;
+          double tb[2];
+          edge_crossing(A, B, Cc, g0 > 0, &tb[0], &tb[1]);
+          for (int r = 0; r < 2; ++r) {
+            const D3 x = x0 + tb[r] * d;
             blo[0] = dmin(blo[0], x.x); bhi[0] = dmax(bhi[0], x.x);
             blo[1] = dmin(blo[1], x.y); bhi[1] = dmax(bhi[1], x.y);
             blo[2] = dmin(blo[2], x.z); bhi[2] = dmax(bhi[2], x.z);

@@ -49,6 +49,7 @@ namespace fw {
 using fc::D3;
 using fc::dmax;
 using fc::dmin;
+using fc::edge_crossing;
 using fc::dot;
 using fc::len2;
 
@@ -358,22 +359,10 @@ P2M_HD int flood_warp(WarpWork &S, Env &env, int64_t k, double eps, double delta
             B = 2 * dot(r0, d) - 2 * wu * du;
             Cc = len2(r0) - wu * wu + eta;
           }
-          double roots[2];
-          int nr = 0;
-          if (fabs(A) <= 1e-14 * (fabs(B) + fabs(Cc))) {
-            if (B != 0) roots[nr++] = -Cc / B;
-          } else {
-            const double disc = dmax(0.0, B * B - 4 * A * Cc);
-            const double sq = sqrt(disc);
-            const double qq = -0.5 * (B + (B >= 0 ? sq : -sq));
-            if (qq != 0) roots[nr++] = Cc / qq;
-            roots[nr++] = qq / A;
-          }
-          for (int r = 0; r < nr; ++r) {
-            double tt = roots[r];
-            if (!(tt >= -1e-9 && tt <= 1 + 1e-9)) continue;
-            tt = dmin(1.0, dmax(0.0, tt));
-            const D3 x = x0 + tt * d;
+          double tb[2];
+          edge_crossing(A, B, Cc, g0 > 0, &tb[0], &tb[1]);
+          for (int r = 0; r < 2; ++r) {
+            const D3 x = x0 + tb[r] * d;
             lo[0] = dmin(lo[0], x.x); hi[0] = dmax(hi[0], x.x);
             lo[1] = dmin(lo[1], x.y); hi[1] = dmax(hi[1], x.y);
             lo[2] = dmin(lo[2], x.z); hi[2] = dmax(hi[2], x.z);
