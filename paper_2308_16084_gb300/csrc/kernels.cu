@@ -563,9 +563,24 @@ __device__ __forceinline__ void scan_list(const DevView &m, float qx, float qy, 
       if (!q_pass(gw, sw.x, sw.y, sw.z)) continue;
       const uint32_t cb = c0 + 8 * (s - s0), ce = min(cb + 8u, c1);
       if (COUNT) wk->chunks += (int)(ce - cb);
-      for (uint32_t c = cb; c < ce; ++c) {
+      // the boxes of the super-chunk's chunks are all tested first, their
+      // loads in flight together, then the admitted chunks are scanned (one
+      // chunk box tested and scanned at a time left the list pass 5 % slower
+      // on the 1.3M-triangle workload; the order does not change the result)
+      uint32_t cpass = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t c = cb + k;
+        if (c < ce) {
+          const uint4 cw = __ldg(&m.chunks[c]);
+          if (q_pass(gw, cw.x, cw.y, cw.z)) cpass |= 1u << k;
+        }
+      }
+      while (cpass) {
+        const uint32_t c = cb + (uint32_t)(__ffs(cpass) - 1);
+        cpass &= cpass - 1;
         const uint32_t first = j0 + 8 * (c - c0);
-        scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), true, gw, r, wk);
+        scan_chunk<COUNT>(m, qx, qy, qz, c, first, min(first + 8u, j1), false, gw, r, wk);
       }
     }
     return;
@@ -1276,8 +1291,14 @@ __global__ void k_batch_nn(BatchDesc d, const float4 *__restrict__ sorted, int64
   key_rank[i] = count_key((uint32_t)d.voff[k] + v, vhist);
 }
 
+// resident 512-thread CTAs per SM the persistent batch list kernel is
+// compiled for (its register cap), as P2M_LIST_MIN_BLOCKS for k_list_pass
+#ifndef P2M_BATCH_LIST_MIN_BLOCKS
+#define P2M_BATCH_LIST_MIN_BLOCKS P2M_LIST_MIN_BLOCKS
+#endif
+
 template <int G>
-__global__ void __launch_bounds__(512, P2M_LIST_MIN_BLOCKS)
+__global__ void __launch_bounds__(512, P2M_BATCH_LIST_MIN_BLOCKS)
 k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__restrict__ gv,
              int64_t total, int tile, float4 *__restrict__ rec, unsigned int *queue_head,
              unsigned int *error_word) {
