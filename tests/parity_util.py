@@ -92,6 +92,14 @@ def closed_distance(V, E, F, q, ptype, pid):
     return closed_closest(V, E, F, q, ptype, pid)[1]
 
 
+def grad_tolerance(dist, verts, base=2e-3):
+    """Per-query bound on |grad_q - grad_q_oracle| for grad_q = (q - c)/d:
+    a base error plus the direction error that a float32 closest point
+    carries, about 8 ulps of the largest coordinate divided by d."""
+    scale = float(np.abs(np.asarray(verts, np.float64)).max())
+    return base + 8.0 * 2.0 ** -23 * scale / np.asarray(dist, np.float64)
+
+
 def _log(label, summary):
     path = os.environ.get("P2M_PARITY_LOG")
     if path:
