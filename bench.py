@@ -65,6 +65,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-timeout", type=float, default=1500.0,
                     help="seconds to wait for the CPU oracle's tables after the GPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pipe-depth", type=int, default=2,
+                    help="slots of the pipelined host API in the end-to-end figure")
     ap.add_argument("--only", default=None,
                     choices=["headline", "cfg0", "cfg2", "fwd_bwd", "batched"],
                     help="measure one part only (profiling runs)")
@@ -577,7 +579,7 @@ def out_buffers(torch, n):
             "prim_type": torch.empty(n, dtype=torch.uint8, device="cuda")}
 
 
-def pipe_e2e(mesh, m, steps, dist=None):
+def pipe_e2e(mesh, m, steps, dist=None, depth=2):
     """End to end through the host APIs on pinned host buffers: every step
     copies its queries in and all four outputs out inside the timed region.
     Serial: p2m_query_host (copy in, query, copy out, synchronise).
@@ -590,7 +592,7 @@ def pipe_e2e(mesh, m, steps, dist=None):
     outs_h = [(torch.empty(n, dtype=torch.float32).pin_memory(),
                torch.empty(n, dtype=torch.int32).pin_memory(),
                torch.empty(n, 3, dtype=torch.float32).pin_memory(),
-               torch.empty(n, dtype=torch.uint8).pin_memory()) for _ in range(2)]
+               torch.empty(n, dtype=torch.uint8).pin_memory()) for _ in range(depth)]
     for _ in range(2):
         mesh.query_host(qh, *outs_h[0])
     if dist:
@@ -599,15 +601,15 @@ def pipe_e2e(mesh, m, steps, dist=None):
     for _ in range(steps):
         mesh.query_host(qh, *outs_h[0])
     serial_s = time.perf_counter() - t0
-    pipe = mesh.pipeline(n, depth=2)
-    for k in range(2):
+    pipe = mesh.pipeline(n, depth=depth)
+    for k in range(depth):
         pipe.submit(qh, *outs_h[k])
     pipe.wait()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for k in range(steps):
-        pipe.submit(qh, *outs_h[k % 2])
+        pipe.submit(qh, *outs_h[k % depth])
     pipe.wait()
     e2e_s = time.perf_counter() - t0
     pipe.close()
@@ -665,7 +667,7 @@ def measure_forward(pg, m, args, local, *, steps, warmup, flush=None, dist=None,
     ms = max_over_ranks([ms], dist)[0]
     tsum = phase_times(mesh, q, out, steps, flush)
     roof = forward_roofline(mesh, q, n, tsum, ms / steps, steps)
-    e2e_s, serial_s = pipe_e2e(mesh, m, steps, dist)
+    e2e_s, serial_s = pipe_e2e(mesh, m, steps, dist, args.pipe_depth)
     e2e_s, serial_s = max_over_ranks([e2e_s, serial_s], dist)
     res = {"value": replica_throughput(n, steps, world, ms / 1e3), "unit": UNIT,
            "ms_per_step": ms / steps, "steps": steps, "warmup": max(3, warmup),
@@ -673,7 +675,7 @@ def measure_forward(pg, m, args, local, *, steps, warmup, flush=None, dist=None,
            "e2e": {"value": replica_throughput(n, steps, world, e2e_s), "unit": UNIT,
                    "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 21 * n,
                    "outputs": "dist, prim_id, closest, prim_type (all of them, 21 B per query)",
-                   "api": "p2m_pipe_submit, 2 slots (pinned host buffers)",
+                   "api": f"p2m_pipe_submit, {args.pipe_depth} slots (pinned host buffers)",
                    "serial_value": replica_throughput(n, steps, world, serial_s),
                    "serial_api": "p2m_query_host (synchronous per step)"},
            "gpu_launches": kernels_per_step(mesh.tuning) * steps,

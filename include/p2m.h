@@ -79,8 +79,9 @@ typedef struct {
                           2 = that and the flooding (Alg. 1) on the GPU too (one warp per
                           primitive, the same double-precision steps, no fused
                           multiply-adds), 0 = CPU only.
-                          Every setting gives the same tables bit for bit (default 1;
-                          0 works without a GPU)                                       */
+                          Every setting gives the same tables bit for bit (default 2,
+                          the fastest build on a GB300; without a GPU every setting
+                          builds on the host)                                          */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
 } p2m_build_opts;
 

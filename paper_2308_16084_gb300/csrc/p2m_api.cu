@@ -304,7 +304,7 @@ void p2m_default_opts(p2m_build_opts *o) {
   o->domain_margin = 0.f;
   o->delta_rel = 4e-6f;
   o->host_threads = 0;
-  o->device_assist = 1;
+  o->device_assist = 2;
   o->leaf_size = 8;
 }
 
@@ -1031,8 +1031,9 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   // threads per query: in the one-pass kernel, one thread per query (wm = 0)
   // or a warp answering 32 queries together (wm = 1); in the two-pass path,
   // 1, 2, 4 or 8 lanes splitting each query's list (lanes)
+  // list scan: the two-level R-tree (ch = 2) or chunk boxes only (ch = 1)
   for (int gv = 0; gv < 2; ++gv)
-  for (int ch = 2; ch < 3; ++ch)
+  for (int ch = 1; ch < 3; ++ch)
   for (int wm = 0; wm < 2; ++wm)
   for (int lanes = 1; lanes <= 8; lanes *= 2)
   for (int key = 0; key < 2; ++key)
@@ -1042,8 +1043,9 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
       if (lanes > 1 && gv == 0) continue;
       // sorting by seed vertex ignores sort_bits and needs the regrouping
       if (key == 1 && (gv == 0 || bits != bits_c[0] || !h->seed.p)) continue;
-      // the lane split is tried with the first sort's best-known settings only
-      if (lanes > 1 && (key != 1 && bits != bits_c[2])) continue;
+      // the lane split and the one-level scan are tried with the first sort's
+      // best-known settings only
+      if ((lanes > 1 || ch == 1) && (key != 1 && bits != bits_c[2])) continue;
       p2m_tuning t{bits, bt, wm, 2, ch, gv, key, lanes};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;

@@ -243,6 +243,11 @@ def test_queries_on_host_only_handle_fail_loudly(pg):
     with pytest.raises(pg.P2MError) as e:
         h.pipeline(n)
     assert e.value.code == 8
+    # moving the vertices needs the device layout too (checked through the
+    # C ABI: the pointer is never read when the handle has no device)
+    v = np.zeros((h.n_verts, 3), np.float32)
+    assert pg.lib.p2m_update_vertices(h._h, ctypes.c_void_p(v.ctypes.data), h.n_verts, 0,
+                                      None) == 8
 
 
 def test_tuning_fields_are_validated(pg):
