@@ -65,7 +65,7 @@ def parse(argv=None):
     ap.add_argument("--cpu-timeout", type=float, default=1500.0,
                     help="seconds to wait for the CPU oracle's tables after the GPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pipe-depth", type=int, default=2,
+    ap.add_argument("--pipe-depth", type=int, default=4,
                     help="slots of the pipelined host API in the end-to-end figure")
     ap.add_argument("--only", default=None,
                     choices=["headline", "cfg0", "cfg2", "fwd_bwd", "batched"],
@@ -454,10 +454,16 @@ def algorithmic_bytes(c, n):
         36 * c["faces"] / n, nn, lst
 
 
-def kernels_per_step(tuning):
-    sort = 5 if tuning["sort_bits"] > 0 else 1  # count, 3 scan kernels, scatter
+def kernels_per_step(tuning, n=0):
+    """This library's kernels per query call: the sort (count, 3 scan kernels,
+    scatter), then either the one-pass kernel or, per concurrent range of the
+    sorted queries (tuning field streams, ranges of >= 2^18), the nn pass, 3
+    scan kernels, the vertex scatter and the list pass, and one output
+    write."""
+    sort = 5 if tuning["sort_bits"] > 0 else 1
     if tuning.get("group_by_vertex") and not tuning.get("warp_cooperative"):
-        return sort + 7  # nn pass, 3 scan kernels, vertex scatter, list pass, output write
+        ranges = max(1, min(tuning.get("streams", 1), n >> 18))
+        return sort + 6 * ranges + 1
     return sort + 1
 
 
@@ -579,6 +585,36 @@ def out_buffers(torch, n):
             "prim_type": torch.empty(n, dtype=torch.uint8, device="cuda")}
 
 
+def concurrent_steps(mesh, q, n, steps, depth):
+    """The same steps device-resident, issued round robin on the `depth`
+    slots of a pipe (p2m_pipe_submit_device: each slot its own stream,
+    scratch and outputs), so that the kernels of neighbouring steps overlap,
+    as they do in the pipelined end-to-end figure.  CUDA events on the
+    launching stream: every step waits for the start event, and the stream
+    joins every slot (p2m_pipe_join) before the end event."""
+    import torch
+    cur = torch.cuda.current_stream()
+    outs = [out_buffers(torch, n) for _ in range(depth)]
+    pipe = mesh.pipeline(n, depth=depth)
+    for k in range(2 * depth):
+        pipe.submit_device(q, outs[k % depth])
+    pipe.join()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for k in range(steps):
+        pipe.submit_device(q, outs[k % depth])
+    pipe.join()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    pipe.close()
+    ms = e0.elapsed_time(e1)
+    return {"value": n * steps / (ms / 1e3), "unit": UNIT, "slots": depth,
+            "ms_per_step": ms / steps,
+            "api": "p2m_pipe_submit_device round robin on the slots, p2m_pipe_join"}
+
+
 def pipe_e2e(mesh, m, steps, dist=None, depth=2):
     """End to end through the host APIs on pinned host buffers: every step
     copies its queries in and all four outputs out inside the timed region.
@@ -665,6 +701,9 @@ def measure_forward(pg, m, args, local, *, steps, warmup, flush=None, dist=None,
         dist.barrier()
     clk = clocks.stop()
     ms = max_over_ranks([ms], dist)[0]
+    conc = None
+    if flush is None and world == 1:
+        conc = concurrent_steps(mesh, q, n, steps, args.pipe_depth)
     tsum = phase_times(mesh, q, out, steps, flush)
     roof = forward_roofline(mesh, q, n, tsum, ms / steps, steps)
     e2e_s, serial_s = pipe_e2e(mesh, m, steps, dist, args.pipe_depth)
@@ -678,7 +717,8 @@ def measure_forward(pg, m, args, local, *, steps, warmup, flush=None, dist=None,
                    "api": f"p2m_pipe_submit, {args.pipe_depth} slots (pinned host buffers)",
                    "serial_value": replica_throughput(n, steps, world, serial_s),
                    "serial_api": "p2m_query_host (synchronous per step)"},
-           "gpu_launches": kernels_per_step(mesh.tuning) * steps,
+           "gpu_launches": kernels_per_step(mesh.tuning, n) * steps,
+           "concurrent_steps": conc,
            "run": {"tuning": mesh.tuning, "autotune_ms": tuned_ms, "build_s": round(build_s, 1),
                    "layout_gb": round(st["device_bytes"] / 1e9, 3),
                    "table_entries": st["n_entries"], "max_list": st["max_list"],
@@ -806,7 +846,7 @@ def run_fwd_bwd(pg, args, local):
                     "d2h_bytes_per_step": 12 * n + 12 * int(m.verts.shape[0]) + 4,
                     "api": "pg.distance (torch.autograd.Function) from pinned host queries; "
                            "grad_q, grad_verts and the loss copied back"},
-            "gpu_launches": (kernels_per_step(mesh.tuning) + 1) * args.steps,
+            "gpu_launches": (kernels_per_step(mesh.tuning, n) + 1) * args.steps,
             "config": {"workload": m.name, "n_tris": int(m.tris.shape[0]),
                        "n_queries": n, "loss": "sum w_i d_i, w ~ U(0,1)",
                        "grads": "queries and vertex positions",
@@ -946,6 +986,7 @@ def run_ours(args):
             line.update({"value": h["value"], "ms_per_step": h["ms_per_step"],
                          "clocks": h["clocks"], "e2e": h["e2e"],
                          "gpu_launches": h["gpu_launches"], "roofline": h["roofline"],
+                         "concurrent_steps": h["concurrent_steps"],
                          "run": dict(h["run"], parallelism="replicas only" if world > 1
                                      else "single GPU")})
         if world == 1:

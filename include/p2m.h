@@ -180,6 +180,19 @@ typedef struct p2m_pipe p2m_pipe;
 p2m_status p2m_pipe_create(p2m_handle *h, int64_t max_n, int depth, p2m_pipe **out);
 p2m_status p2m_pipe_submit(p2m_pipe *p, const float *q, int64_t n, float *dist, float *closest,
                            int32_t *prim_id, uint8_t *prim_type);
+/* A batch on DEVICE buffers on the pipe's next slot: the query of the n
+ * device points q runs on the slot's stream with the slot's scratch (no
+ * copies), after the work enqueued so far on `stream`, writing the device
+ * outputs (dist and prim_id required; closest, prim_type may be NULL).  It
+ * returns without waiting, except for the slot's previous batch.  Batches on
+ * different slots may run concurrently, which keeps the SMs busier than one
+ * batch at a time; the outputs are complete after p2m_pipe_wait, or on a
+ * stream after p2m_pipe_join.  Errors as p2m_pipe_submit. */
+p2m_status p2m_pipe_submit_device(p2m_pipe *p, const float *q, int64_t n, float *dist,
+                                  float *closest, int32_t *prim_id, uint8_t *prim_type,
+                                  void *stream);
+/* Makes `stream` wait for every batch submitted so far (no host wait). */
+p2m_status p2m_pipe_join(p2m_pipe *p, void *stream);
 /* Waits for every submitted batch; their host outputs are then complete. */
 p2m_status p2m_pipe_wait(p2m_pipe *p);
 void p2m_pipe_destroy(p2m_pipe *p);
@@ -242,7 +255,18 @@ p2m_status p2m_query_noalloc(p2m_handle *h, const float *q, int64_t n, float *di
  *                  path: 1, 2, 4 or 8 adjacent lanes split a query's
  *                  interception list (every G-th group of 64 entries) and
  *                  keep the best with a warp shuffle.  Results do not
- *                  depend on it. */
+ *                  depend on it.
+ *   streams        1..4 (two-pass path): after the first sort, the
+ *                  nearest-vertex pass, the regrouping and the list pass run
+ *                  as up to this many contiguous ranges of the sorted
+ *                  queries (each at least 2^18), the first on the caller's
+ *                  stream and the others on streams the handle forks from it
+ *                  with an event and joins back to it, so that the ranges'
+ *                  kernels run concurrently; the output write follows the
+ *                  join.  The call still ends on the caller's stream (graph
+ *                  capture works as for one stream, after p2m_reserve);
+ *                  results do not depend on it.  While per-phase timing is
+ *                  on (p2m_set_timing) a call runs as one pipeline. */
 typedef struct {
   int sort_bits;
   int block_threads;
@@ -252,6 +276,7 @@ typedef struct {
   int group_by_vertex;
   int sort_key;
   int lanes_per_query;
+  int streams;
 } p2m_tuning;
 p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t);
 p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t);
@@ -277,7 +302,8 @@ p2m_status p2m_query_counters(p2m_handle *h, const float *q, int64_t n, int64_t 
 
 /* Pre-size the handle's scratch arena for queries of up to n points, so that
  * later p2m_query calls with n or fewer points allocate nothing (needed
- * before capturing p2m_query into a CUDA graph). */
+ * before capturing p2m_query into a CUDA graph); it also creates the forked
+ * streams of split calls (tuning field streams). */
 p2m_status p2m_reserve(p2m_handle *h, int64_t n);
 
 /*

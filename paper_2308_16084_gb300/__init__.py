@@ -38,7 +38,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("sort_bits", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("warp_cooperative", ctypes.c_int), ("nn_walk", ctypes.c_int),
                 ("chunked", ctypes.c_int), ("group_by_vertex", ctypes.c_int),
-                ("sort_key", ctypes.c_int), ("lanes_per_query", ctypes.c_int)]
+                ("sort_key", ctypes.c_int), ("lanes_per_query", ctypes.c_int),
+                ("streams", ctypes.c_int)]
 
 
 class BatchIO(ctypes.Structure):
@@ -194,7 +195,8 @@ class P2M:
         return {"sort_bits": t.sort_bits, "block_threads": t.block_threads,
                 "warp_cooperative": t.warp_cooperative, "nn_walk": t.nn_walk,
                 "chunked": t.chunked, "group_by_vertex": t.group_by_vertex,
-                "sort_key": t.sort_key, "lanes_per_query": t.lanes_per_query}
+                "sort_key": t.sort_key, "lanes_per_query": t.lanes_per_query,
+                "streams": t.streams}
 
     @tuning.setter
     def tuning(self, d):
@@ -202,7 +204,7 @@ class P2M:
         cur.update(d)
         t = Tuning(cur["sort_bits"], cur["block_threads"], cur["warp_cooperative"],
                    cur["nn_walk"], cur["chunked"], cur["group_by_vertex"], cur["sort_key"],
-                   cur["lanes_per_query"])
+                   cur["lanes_per_query"], cur["streams"])
         check(lib.p2m_set_tuning(self._h, ctypes.byref(t)), "p2m_set_tuning")
 
     def autotune(self, q, reps=3, stream=None):
@@ -403,6 +405,21 @@ class P2MPipe:
         check(lib.p2m_pipe_submit(self._p, _host_ptr(q), int(q.shape[0]), _host_ptr(dist),
                                   _host_ptr(closest), _host_ptr(prim_id), _host_ptr(prim_type)),
               "p2m_pipe_submit")
+
+    def submit_device(self, q, out, stream=None):
+        """Queue one batch on DEVICE tensors: q (N,3) float32, out a dict with
+        dist and prim_id (and closest, prim_type) CUDA tensors.  It starts
+        after the work enqueued so far on `stream` (default: the current
+        one); batches on different slots may run concurrently."""
+        check(lib.p2m_pipe_submit_device(self._p, _ptr(q), int(q.shape[0]), _ptr(out["dist"]),
+                                         _ptr(out.get("closest")), _ptr(out["prim_id"]),
+                                         _ptr(out.get("prim_type")), _stream(stream)),
+              "p2m_pipe_submit_device")
+
+    def join(self, stream=None):
+        """Make `stream` (default: the current one) wait for every batch
+        submitted so far."""
+        check(lib.p2m_pipe_join(self._p, _stream(stream)), "p2m_pipe_join")
 
     def wait(self):
         """Block until every submitted batch's results are in its buffers."""

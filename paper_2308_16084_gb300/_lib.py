@@ -45,6 +45,8 @@ _SIGS = {
     "p2m_nearest_vertex": (_INT, [_P, _P, _I64, _P, _P]),
     "p2m_pipe_create": (_INT, [_P, _I64, _INT, _P]),
     "p2m_pipe_submit": (_INT, [_P, _P, _I64, _P, _P, _P, _P]),
+    "p2m_pipe_submit_device": (_INT, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+    "p2m_pipe_join": (_INT, [_P, _P]),
     "p2m_pipe_wait": (_INT, [_P]),
     "p2m_pipe_destroy": (None, [_P]),
     "p2m_query_noalloc": (_INT, [_P, _P, _I64, _P, _P, _P, _P, _P]),

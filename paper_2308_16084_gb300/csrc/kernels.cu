@@ -1383,7 +1383,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv) {
+size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv, int ranges) {
   size_t nb = sort_bits > 0 ? ((size_t)1 << sort_bits) : 0;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t base = al(16 * (size_t)n) + al(8 * (size_t)n) + 2 * al(4 * nb) + al(4 * kMaxScanTiles);
@@ -1391,6 +1391,8 @@ size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv) {
                // records, vertex histogram and offsets
     base += al(4 * (size_t)n) + al(16 * (size_t)n) + al(32 * (size_t)n) +
             2 * al(4 * (size_t)(nv + 1));
+  if (nv > 0 && ranges > 1)  // every further range: its histogram, offsets, scan tiles
+    base += (size_t)(ranges - 1) * (2 * al(4 * (size_t)(nv + 1)) + al(4 * kMaxScanTiles));
   return base + 256;
 }
 
@@ -1398,7 +1400,7 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
                          float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
                          uint8_t *status, void *scratch, size_t scratch_bytes,
                          const QueryTuning &tune, cudaStream_t stream, cudaEvent_t *ev,
-                         unsigned long long *counters) {
+                         unsigned long long *counters, const SplitStreams *split) {
   if (n <= 0) return cudaSuccess;
   if (scratch_bytes < query_scratch_bytes(n, tune.sort_bits)) return cudaErrorInvalidValue;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -1461,6 +1463,60 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
   }
   const int bt = tune.block_threads;
   if (ev) cudaEventRecord(ev[1], stream);
+  const int ranges = (grouped && split && !ev) ? 1 + split->n_aux : 1;
+  if (ranges > 1) {
+    // The passes after the first sort as `ranges` contiguous ranges of the
+    // sorted stream, concurrently: a range of queries sorted by seed vertex
+    // is a compact region, so its lanes still share lists, while the ranges'
+    // kernels fill the SM time one pipeline leaves idle (small scans,
+    // kernel tails).  Each range has its own vertex histogram, offsets and
+    // scan tiles (after the single-range scratch); the records land in the
+    // caller's order, so one k_unpack on the launching stream follows the
+    // join.  Results do not depend on the split.
+    if (scratch_bytes < query_scratch_bytes(n, tune.sort_bits, m.nv, ranges))
+      return cudaErrorInvalidValue;
+    const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
+    char *extra = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255) +
+                  (query_scratch_bytes(n, tune.sort_bits, m.nv) - 256);
+    const size_t ext = 2 * al(4 * (size_t)(m.nv + 1)) + al(4 * kMaxScanTiles);
+    const int64_t cn = (n + ranges - 1) / ranges;
+    cudaError_t e = cudaEventRecord(split->fork, stream);
+    for (int r = 0; r < ranges && e == cudaSuccess; ++r) {
+      const int64_t a = r * cn, b = min(n, a + cn);
+      if (a >= b) break;
+      const int64_t nr = b - a;
+      cudaStream_t sr = r == 0 ? stream : split->aux[r - 1];
+      uint32_t *vh = vhist, *vo = voff, *tl = tiles2;
+      if (r > 0) {
+        char *x = extra + (size_t)(r - 1) * ext;
+        vh = (uint32_t *)x;
+        vo = (uint32_t *)(x + al(4 * (size_t)(m.nv + 1)));
+        tl = (uint32_t *)(x + 2 * al(4 * (size_t)(m.nv + 1)));
+        e = cudaStreamWaitEvent(sr, split->fork, 0);
+      }
+      cudaMemsetAsync(vh, 0, 4 * (size_t)(m.nv + 1), sr);
+      k_nn_pass<<<blocks_for(nr, bt), bt, 0, sr>>>(m, sorted + a, nr, walk, vh, key_rank + a);
+      bucket_scan(vh, vo, tl, (int)(m.nv + 1), sr);
+      k_vertex_scatter<<<blocks_for(nr, T), T, 0, sr>>>(sorted + a, nr, key_rank + a, vo,
+                                                         grouped_q + a, gv + a);
+      const int G = tune.lanes_per_query;
+      const unsigned lb = blocks_for(nr * G, bt);
+      if (G == 8)
+        k_list_pass<8><<<lb, bt, 0, sr>>>(m, grouped_q + a, gv + a, nr, tune.chunked, rec);
+      else if (G == 4)
+        k_list_pass<4><<<lb, bt, 0, sr>>>(m, grouped_q + a, gv + a, nr, tune.chunked, rec);
+      else if (G == 2)
+        k_list_pass<2><<<lb, bt, 0, sr>>>(m, grouped_q + a, gv + a, nr, tune.chunked, rec);
+      else
+        k_list_pass<1><<<lb, bt, 0, sr>>>(m, grouped_q + a, gv + a, nr, tune.chunked, rec);
+      if (r > 0 && e == cudaSuccess) e = cudaEventRecord(split->join[r - 1], sr);
+      if (r > 0 && e == cudaSuccess) e = cudaStreamWaitEvent(stream, split->join[r - 1], 0);
+    }
+    if (e != cudaSuccess) return e;
+    k_unpack<<<blocks_for(n, T), T, 0, stream>>>(rec, n, dist, closest, prim_id, prim_type, save,
+                                                 status);
+    return cudaGetLastError();
+  }
   if (grouped) {
     const int walk = !m.nb_off ? 0 : (tune.nn_walk == 2 && !m.seed ? 1 : tune.nn_walk);
     cudaMemsetAsync(vhist, 0, 4 * (size_t)(m.nv + 1), stream);

@@ -50,11 +50,24 @@ struct QueryTuning {
   int sort_key = 0;  // 0: Morton buckets (2^sort_bits); 1: the seed-grid vertex of
                      // the query's cell (with group_by_vertex and a seed grid)
   int lanes_per_query = 1;  // threads per query in the list pass (1, 2, 4, 8)
+  int streams = 1;  // after the first sort, the passes of the two-pass path run as up to
+                    // this many contiguous ranges of the sorted queries on forked streams
 };
 
 // Scratch needed by launch_query for n points, in bytes (nv: vertices of
-// the mesh, for the regrouping by nearest vertex; 0 = no regrouping).
-size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv = 0);
+// the mesh, for the regrouping by nearest vertex; 0 = no regrouping; ranges:
+// concurrent ranges of the sorted stream, each with its own vertex histogram).
+size_t query_scratch_bytes(int64_t n, int sort_bits, int64_t nv = 0, int ranges = 1);
+
+// Streams for the concurrent ranges of a split query: range r > 0 runs on
+// aux[r - 1], which waits on `fork` (recorded on the launching stream after
+// the first sort) and is joined back through join[r - 1]; n_aux + 1 ranges.
+struct SplitStreams {
+  const cudaStream_t *aux;
+  const cudaEvent_t *join;
+  cudaEvent_t fork;
+  int n_aux;
+};
 
 // Morton bucket sort (a1) + query (a2..a8).  All pointers device.
 // ev (6 events or NULL) marks: start, sorted, nearest vertices found,
@@ -66,7 +79,8 @@ cudaError_t launch_query(const DevView &m, const float *q, int64_t n, float *dis
                          float *closest, int32_t *prim_id, uint8_t *prim_type, float4 *save,
                          uint8_t *status, void *scratch, size_t scratch_bytes,
                          const QueryTuning &tune, cudaStream_t stream,
-                         cudaEvent_t *ev = nullptr, unsigned long long *counters = nullptr);
+                         cudaEvent_t *ev = nullptr, unsigned long long *counters = nullptr,
+                         const SplitStreams *split = nullptr);
 
 // Nearest vertex (KD-tree position) of each point: used by the builder to
 // certify Voronoi cells.

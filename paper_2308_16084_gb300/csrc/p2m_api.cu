@@ -68,6 +68,13 @@ p2m_status from_cuda(cudaError_t e) {
   return P2M_ERR_CUDA;
 }
 
+// concurrent ranges of a split query: at most `streams`, each of at least
+// 2^18 queries
+int split_count(int64_t n, int streams) {
+  const int64_t by_size = n >> 18;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(streams, by_size));
+}
+
 bool have_device() {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess) {
@@ -100,11 +107,44 @@ struct p2m_handle {
   std::vector<cudaEvent_t> ring;
   int64_t ring_next = 0, ring_read = 0;
   unsigned long long *counters = nullptr;
+  // forked streams of a split p2m_query (tuning field streams): range k > 0
+  // of the sorted queries runs on aux[k - 1], which waits on fork (recorded
+  // on the caller's stream after the first sort) and is joined back through
+  // join[k - 1]
+  static constexpr int kMaxStreams = 4;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 
   ~p2m_handle() {
+    for (cudaStream_t st : aux) cudaStreamSynchronize(st);
     if (scratch) cudaFree(scratch);
     if (counters) cudaFree(counters);
     for (auto &e : ring) cudaEventDestroy(e);
+    for (cudaEvent_t e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (cudaStream_t st : aux) cudaStreamDestroy(st);
+  }
+
+  // streams and events for up to k concurrent ranges (created once;
+  // before any capture, by p2m_set_tuning and p2m_reserve)
+  p2m_status ensure_aux(int k) {
+    if (!fork && cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+      fork = nullptr;
+      return P2M_ERR_CUDA;
+    }
+    while ((int)aux.size() < k - 1) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return P2M_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return P2M_ERR_CUDA;
+      }
+      aux.push_back(st);
+      join.push_back(ev);
+    }
+    return P2M_OK;
   }
 
   p2m_status ensure_scratch(size_t bytes) {
@@ -392,6 +432,7 @@ p2m_status p2m_get_tuning(const p2m_handle *h, p2m_tuning *t) {
   t->group_by_vertex = h->tune.group_by_vertex;
   t->sort_key = h->tune.sort_key;
   t->lanes_per_query = h->tune.lanes_per_query;
+  t->streams = h->tune.streams;
   return P2M_OK;
 }
 
@@ -408,6 +449,12 @@ p2m_status p2m_set_tuning(p2m_handle *h, const p2m_tuning *t) {
   if (t->lanes_per_query != 1 && t->lanes_per_query != 2 && t->lanes_per_query != 4 &&
       t->lanes_per_query != 8)
     return P2M_ERR_INVALID_ARG;
+  if (t->streams < 1 || t->streams > p2m_handle::kMaxStreams) return P2M_ERR_INVALID_ARG;
+  if (t->streams > 1) {
+    p2m_status s = h->ensure_aux(t->streams);
+    if (s) return s;
+  }
+  h->tune.streams = t->streams;
   h->tune.lanes_per_query = t->lanes_per_query;
   h->tune.group_by_vertex = t->group_by_vertex;
   h->tune.sort_key = t->sort_key;
@@ -424,7 +471,12 @@ p2m_status p2m_reserve(p2m_handle *h, int64_t n) {
   if (s) return s;
   if (n < 0) return P2M_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
-  return h->ensure_scratch(p2m::query_scratch_bytes(n, 24, h->L.nv) + 24 * (size_t)n + 4096);
+  // one pipeline (plus the staging of p2m_query_host), or the largest split
+  const size_t one = p2m::query_scratch_bytes(n, 24, h->L.nv) + 24 * (size_t)n + 4096;
+  const size_t split =
+      p2m::query_scratch_bytes(n, 24, h->L.nv, split_count(n, p2m_handle::kMaxStreams));
+  if ((s = h->ensure_aux(p2m_handle::kMaxStreams))) return s;
+  return h->ensure_scratch(std::max(one, split));
 }
 
 p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, float *closest,
@@ -436,17 +488,27 @@ p2m_status p2m_query(p2m_handle *h, const float *q, int64_t n, float *dist, floa
   if (n == 0) return P2M_OK;
   if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return P2M_ERR_TOO_LARGE;
-  size_t need = p2m::query_scratch_bytes(n, h->tune.sort_bits,
-                                         h->tune.group_by_vertex ? h->L.nv : 0);
+  const int64_t nvk = h->tune.group_by_vertex ? h->L.nv : 0;
+  // concurrent ranges after the first sort (tuning field streams); with
+  // per-phase timing on, one pipeline on the caller's stream
+  const int R = (h->ring.empty() && nvk > 0 && !h->tune.warp_mode)
+                    ? split_count(n, h->tune.streams) : 1;
+  size_t need = p2m::query_scratch_bytes(n, h->tune.sort_bits, nvk, R);
   if ((s = h->ensure_scratch(need))) return s;
   cudaEvent_t *ev = nullptr;
   if (!h->ring.empty()) {
     ev = &h->ring[p2m_handle::kEv * (h->ring_next % p2m_handle::kRing)];
     ++h->ring_next;
   }
+  p2m::SplitStreams split{};
+  if (R > 1) {
+    if ((s = h->ensure_aux(R))) return s;
+    split = {h->aux.data(), h->join.data(), h->fork, R - 1};
+  }
   return from_cuda(p2m::launch_query(h->view, q, n, dist, closest, prim_id, prim_type,
                                      (float4 *)save, status, h->scratch, h->scratch_bytes,
-                                     h->tune, (cudaStream_t)stream, ev));
+                                     h->tune, (cudaStream_t)stream, ev, nullptr,
+                                     R > 1 ? &split : nullptr));
 }
 
 p2m_status p2m_set_timing(p2m_handle *h, int enable) {
@@ -569,6 +631,7 @@ struct p2m_pipe {
   struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t after = nullptr;  // p2m_pipe_submit_device: the caller's stream so far
     void *mem = nullptr;
     size_t bytes = 0;
     bool busy = false;
@@ -582,6 +645,7 @@ struct p2m_pipe {
       if (s.stream) cudaStreamSynchronize(s.stream);
       if (s.mem) cudaFree(s.mem);
       if (s.done) cudaEventDestroy(s.done);
+      if (s.after) cudaEventDestroy(s.after);
       if (s.stream) cudaStreamDestroy(s.stream);
     }
   }
@@ -667,6 +731,48 @@ p2m_status p2m_pipe_submit(p2m_pipe *p, const float *q, int64_t n, float *dist, 
   if (e != cudaSuccess) return from_cuda(e);
   sl.busy = true;
   ++p->next;
+  return P2M_OK;
+}
+
+p2m_status p2m_pipe_submit_device(p2m_pipe *p, const float *q, int64_t n, float *dist,
+                                  float *closest, int32_t *prim_id, uint8_t *prim_type,
+                                  void *stream) {
+  if (!p) return P2M_ERR_INVALID_ARG;
+  p2m_handle *h = p->h;
+  p2m_status s = check_ready(h);
+  if (s) return s;
+  if (n < 0) return P2M_ERR_INVALID_ARG;
+  if (n == 0) return P2M_OK;
+  if (!q || !dist || !prim_id) return P2M_ERR_INVALID_ARG;
+  if (n > p->max_n) return P2M_ERR_TOO_LARGE;
+  p2m_pipe::Slot &sl = p->slots[p->next % (int64_t)p->slots.size()];
+  cudaError_t e = sl.busy ? cudaEventSynchronize(sl.done) : cudaSuccess;
+  if (e != cudaSuccess) return from_cuda(e);
+  sl.busy = false;
+  // the batch starts after the work enqueued so far on `stream`
+  if (!sl.after && cudaEventCreateWithFlags(&sl.after, cudaEventDisableTiming) != cudaSuccess) {
+    sl.after = nullptr;
+    return P2M_ERR_CUDA;
+  }
+  e = cudaEventRecord(sl.after, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sl.stream, sl.after, 0);
+  if (e == cudaSuccess)
+    e = p2m::launch_query(h->view, q, n, dist, closest, prim_id, prim_type, nullptr, nullptr,
+                          sl.mem, p->query_bytes(), h->tune, sl.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  sl.busy = true;
+  ++p->next;
+  return P2M_OK;
+}
+
+p2m_status p2m_pipe_join(p2m_pipe *p, void *stream) {
+  if (!p) return P2M_ERR_INVALID_ARG;
+  for (auto &sl : p->slots) {
+    if (!sl.busy) continue;
+    cudaError_t e = cudaStreamWaitEvent((cudaStream_t)stream, sl.done, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
   return P2M_OK;
 }
 
@@ -1036,17 +1142,22 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   for (int ch = 1; ch < 3; ++ch)
   for (int wm = 0; wm < 2; ++wm)
   for (int lanes = 1; lanes <= 8; lanes *= 2)
+  for (int ns = 1; ns <= p2m_handle::kMaxStreams; ++ns)
   for (int key = 0; key < 2; ++key)
   for (int bits : bits_c)
     for (int bt : block_c) {
       if (wm == 1 && gv == 1) continue;
       if (lanes > 1 && gv == 0) continue;
+      // concurrent ranges: with one lane and the best-known sorts
+      if (ns > 1 && (lanes > 1 || ch != 2 || split_count(n, ns) < ns ||
+                     (key != 1 && bits != bits_c[2])))
+        continue;
       // sorting by seed vertex ignores sort_bits and needs the regrouping
       if (key == 1 && (gv == 0 || bits != bits_c[0] || !h->seed.p)) continue;
       // the lane split and the one-level scan are tried with the first sort's
       // best-known settings only
       if ((lanes > 1 || ch == 1) && (key != 1 && bits != bits_c[2])) continue;
-      p2m_tuning t{bits, bt, wm, 2, ch, gv, key, lanes};
+      p2m_tuning t{bits, bt, wm, 2, ch, gv, key, lanes, ns};
       p2m_set_tuning(h, &t);
       if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st))) goto done;
       cudaEventRecord(e0, st);

@@ -257,12 +257,14 @@ def test_tuning_fields_are_validated(pg):
     h = _host(pg, m)
     base = h.tuning
     assert set(base) == {"sort_bits", "block_threads", "warp_cooperative", "nn_walk",
-                         "chunked", "group_by_vertex", "sort_key", "lanes_per_query"}
+                         "chunked", "group_by_vertex", "sort_key", "lanes_per_query",
+                         "streams"}
     h.tuning = {"sort_key": 1, "block_threads": 128, "sort_bits": 12}
     assert h.tuning["sort_key"] == 1 and h.tuning["block_threads"] == 128
     for bad in ({"sort_key": 2}, {"group_by_vertex": 3}, {"chunked": 3}, {"nn_walk": -1},
                 {"block_threads": 96}, {"sort_bits": 25}, {"warp_cooperative": 2},
-                {"lanes_per_query": 3}, {"lanes_per_query": 16}, {"lanes_per_query": 0}):
+                {"lanes_per_query": 3}, {"lanes_per_query": 16}, {"lanes_per_query": 0},
+                {"streams": 0}, {"streams": 5}):
         with pytest.raises(pg.P2MError) as e:
             h.tuning = bad
         assert e.value.code == 1

@@ -195,6 +195,42 @@ def test_tunings_give_identical_results(pg, bits, threads, warp, walk, chunked, 
         np.testing.assert_array_equal(got[k], base[k])
 
 
+@pytest.mark.parametrize("streams", [2, 3, 4])
+@pytest.mark.parametrize("group", [0, 1])
+def test_split_query_gives_identical_results(pg, streams, group):
+    """The passes after the first sort run as 2-4 concurrent ranges of the
+    sorted queries on forked streams (a ragged count, so the last range is
+    shorter; the one-pass path ignores the split): the outputs of one
+    pipeline bit for bit, also replayed from a CUDA graph."""
+    m = dg.workload(1, n_queries=(1 << 20) + 4097, level=5)
+    mesh = build(pg, m)
+    mesh.tuning = {"group_by_vertex": group, "streams": 1}
+    q = torch.from_numpy(m.queries).cuda()
+    base = mesh.query(q, closest=True, prim_type=True, save=True, status=True)
+    mesh.tuning = {"streams": streams}
+    assert mesh.tuning["streams"] == streams
+    got = mesh.query(q, closest=True, prim_type=True, save=True, status=True)
+    torch.cuda.synchronize()
+    for k in base:
+        assert torch.equal(got[k], base[k]), k
+    mesh.reserve(q.shape[0])
+    out = {k: torch.empty_like(v) for k, v in base.items()}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        mesh.query(q, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        mesh.query(q, out=out)
+    for v in out.values():
+        v.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for k in base:
+        assert torch.equal(out[k], base[k]), k
+
+
 @pytest.mark.parametrize("idx,kw", [(0, {}), (1, {"level": 6}), (2, {"grid": 96})])
 @pytest.mark.parametrize("lanes", [2, 4, 8])
 @pytest.mark.parametrize("chunked", [0, 1, 2])
@@ -358,6 +394,32 @@ def test_pipeline_matches_device_api(pg):
         pipe.submit(big, torch.empty(30001).pin_memory(),
                     torch.empty(30001, dtype=torch.int32).pin_memory())
     assert e.value.code == 9
+    pipe.close()
+
+
+def test_device_pipeline_matches_device_api(pg):
+    """Device-buffer batches on the pipe's slots (round robin, ragged sizes,
+    overlapping on their streams) give the bits of p2m_query; the launching
+    stream joins them before reading."""
+    m = dg.workload(1, n_queries=300_000, level=4)
+    mesh = build(pg, m)
+    q = torch.from_numpy(m.queries).cuda()
+    pieces = [q[:300_000], q[7:123_457], q[1000:1001], q[:200_000].flip(0).contiguous()]
+    pipe = mesh.pipeline(300_000, depth=3)
+    outs = []
+    for qb in pieces:
+        o = {"dist": torch.empty(qb.shape[0], device="cuda"),
+             "prim_id": torch.empty(qb.shape[0], dtype=torch.int32, device="cuda"),
+             "closest": torch.empty(qb.shape[0], 3, device="cuda"),
+             "prim_type": torch.empty(qb.shape[0], dtype=torch.uint8, device="cuda")}
+        pipe.submit_device(qb, o)
+        outs.append(o)
+    pipe.join()
+    for qb, o in zip(pieces, outs):
+        ref = mesh.query(qb, closest=True, prim_type=True)
+        for k in ("dist", "prim_id", "closest", "prim_type"):
+            assert torch.equal(o[k], ref[k]), k
+    pipe.wait()
     pipe.close()
 
 
