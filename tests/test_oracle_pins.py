@@ -333,6 +333,43 @@ def test_delaunay_cells_give_the_certified_tables(idx, kw):
     np.testing.assert_array_equal(r["pid"], bf["pid"])
 
 
+def test_delaunay_candidates_are_validated():
+    """orc_create_ex refuses a neighbour list it cannot use: offsets that do
+    not start at 0 or decrease, ids out of range, a vertex listed as its own
+    neighbour, or offsets without ids."""
+    import ctypes
+    lib = oracle._load()
+    m = dg.workload(0, n_queries=10, level=1)
+    V = m.verts.astype(np.float64)
+    F = np.ascontiguousarray(m.tris, np.int32)
+    nv = V.shape[0]
+    good_off, good_ids = oracle.delaunay_neighbors(V)
+
+    def create(off, ids):
+        st = ctypes.c_int(0)
+        h = lib.orc_create_ex(V.ctypes.data, nv, F.ctypes.data, F.shape[0], None, 0, 1.25, 0.0,
+                              4e-6, 1, 1, None if off is None else off.ctypes.data,
+                              None if ids is None else ids.ctypes.data, ctypes.byref(st))
+        if h:
+            lib.orc_destroy(h)
+        return st.value
+
+    assert create(good_off, good_ids) == 0
+    bad = good_off.copy()
+    bad[0] = 1
+    assert create(bad, good_ids) == 1
+    bad = good_off.copy()
+    bad[5] = bad[6] + 1
+    assert create(bad, good_ids) == 1
+    ids = good_ids.copy()
+    ids[3] = nv
+    assert create(good_off, ids) == 2
+    ids = good_ids.copy()
+    ids[good_off[4]] = 4
+    assert create(good_off, ids) == 1
+    assert create(good_off, None) == 1
+
+
 def test_voronoi_volume_sum_workload0():
     m = dg.workload(0, n_queries=10)
     o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin)
