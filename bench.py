@@ -619,7 +619,7 @@ def pipe_e2e(mesh, m, steps, dist=None, depth=2):
     """End to end through the host APIs on pinned host buffers: every step
     copies its queries in and all four outputs out inside the timed region.
     Serial: p2m_query_host (copy in, query, copy out, synchronise).
-    Pipelined: p2m_pipe_submit on two slots, so one step's copies overlap
+    Pipelined: p2m_pipe_submit on `depth` slots, so one step's copies overlap
     the other step's kernels; the clock stops when the last step's results
     are in host memory.  Returns the two times in seconds."""
     import torch
