@@ -449,12 +449,86 @@ __global__ void k_identity(const float *__restrict__ q, int64_t n, float4 *__res
 }
 
 // ------------------------------------------------------------ a2..a8
+// The running best of a query's scan keeps the squared distance and the
+// typed id only (fewer live registers in the latency-bound list scan); the
+// winner's closest point and barycentric weights are evaluated once at the
+// end (closest_of) with the same arithmetic that tested it.
 struct Best {
   float d2;
-  float cx, cy, cz;
   uint32_t tid;  // type << 30 | id
-  float w0, w1, w2;
 };
+
+struct Closest {
+  float cx, cy, cz;
+  float w1, w2;  // weights of the primitive's 2nd and 3rd vertex; w0 = (1 - w1) - w2
+};
+
+// foot of q on the line of edge record {a, 1/|d|^2}, {d = b - a}: returns
+// its parameter t (closest point a + t d)
+__device__ __forceinline__ float edge_foot(const float4 &a, const float4 &d, float qx, float qy,
+                                           float qz, float &cx, float &cy, float &cz) {
+  const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+  const float t = (wx * d.x + wy * d.y + wz * d.z) * a.w;
+  cx = a.x + t * d.x;
+  cy = a.y + t * d.y;
+  cz = a.z + t * d.z;
+  return t;
+}
+
+// foot of q on the plane of face record {a, A}, {e1, B}, {e2, C}: its
+// parameters (s, t) (closest point a + s e1 + t e2)
+__device__ __forceinline__ void face_foot(const float4 &a, const float4 &e1, const float4 &e2,
+                                          float qx, float qy, float qz, float &s, float &t,
+                                          float &cx, float &cy, float &cz) {
+  const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
+  const float p1 = wx * e1.x + wy * e1.y + wz * e1.z;
+  const float p2 = wx * e2.x + wy * e2.y + wz * e2.z;
+  s = a.w * p1 - e1.w * p2;
+  t = e2.w * p2 - e1.w * p1;
+  cx = a.x + s * e1.x + t * e2.x;
+  cy = a.y + s * e1.y + t * e2.y;
+  cz = a.z + s * e1.z + t * e2.z;
+}
+
+// the running best of a query whose nearest vertex is row v: that vertex
+__device__ __forceinline__ Best best_of_vertex(const DevView &m, float qx, float qy, float qz,
+                                               int v) {
+  const float4 pv = __ldg(&m.kd_points[v]);
+  const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
+  Best r;
+  r.d2 = dx * dx + dy * dy + dz * dz;
+  r.tid = (uint32_t)__float_as_int(pv.w);
+  return r;
+}
+
+// closest point and weights of the winner tid of a query whose nearest
+// vertex is row v (the only vertex the scan can end on: lists hold edges
+// and faces)
+__device__ __forceinline__ Closest closest_of(const DevView &m, float qx, float qy, float qz,
+                                              uint32_t tid, int v) {
+  Closest c;
+  const uint32_t type = tid >> 30;
+  const size_t id = tid & 0x3fffffffu;
+  if (type == 0u) {
+    const float4 pv = __ldg(&m.kd_points[v]);
+    c.cx = pv.x;
+    c.cy = pv.y;
+    c.cz = pv.z;
+    c.w1 = 0.f;
+    c.w2 = 0.f;
+  } else if (type == 1u) {
+    const float4 a = __ldg(&m.edge_rec[2 * id]);
+    const float4 d = __ldg(&m.edge_rec[2 * id + 1]);
+    c.w1 = edge_foot(a, d, qx, qy, qz, c.cx, c.cy, c.cz);
+    c.w2 = 0.f;
+  } else {
+    const float4 a = __ldg(&m.face_rec[3 * id]);
+    const float4 e1 = __ldg(&m.face_rec[3 * id + 1]);
+    const float4 e2 = __ldg(&m.face_rec[3 * id + 2]);
+    face_foot(a, e1, e2, qx, qy, qz, c.w1, c.w2, c.cx, c.cy, c.cz);
+  }
+  return c;
+}
 
 // a4 + a6/a7 for list entry j: Region-box test (the query's codes qw in its
 // chunk's entry frame against the entry's codes, quant.h), then the gated
@@ -466,55 +540,28 @@ __device__ __forceinline__ void test_entry(const DevView &m, float qx, float qy,
   const uint4 e = __ldg(&m.entries[j]);
   if (!q_pass(qw, e.y, e.z, e.w)) return;
   const uint32_t tid = e.x;
-  const uint32_t id = tid & 0x3fffffffu;
+  const size_t id = tid & 0x3fffffffu;
+  float cx, cy, cz;
   if ((tid >> 30) == 1u) {
     if (COUNT) ++wk->edges;
-    const float4 a = __ldg(&m.edge_rec[2 * (size_t)id]);
-    const float4 d = __ldg(&m.edge_rec[2 * (size_t)id + 1]);
-    const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
-    const float t = (wx * d.x + wy * d.y + wz * d.z) * a.w;
-    if (t > 0.f && t < 1.f) {
-      const float cx = a.x + t * d.x, cy = a.y + t * d.y, cz = a.z + t * d.z;
-      const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
-      const float d2 = ex * ex + ey * ey + ez * ez;
-      if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
-        r.d2 = d2;
-        r.cx = cx;
-        r.cy = cy;
-        r.cz = cz;
-        r.tid = tid;
-        r.w0 = 1.f - t;
-        r.w1 = t;
-        r.w2 = 0.f;
-      }
-    }
+    const float4 a = __ldg(&m.edge_rec[2 * id]);
+    const float4 d = __ldg(&m.edge_rec[2 * id + 1]);
+    const float t = edge_foot(a, d, qx, qy, qz, cx, cy, cz);
+    if (!(t > 0.f && t < 1.f)) return;
   } else {
     if (COUNT) ++wk->faces;
-    const float4 a = __ldg(&m.face_rec[3 * (size_t)id]);
-    const float4 e1 = __ldg(&m.face_rec[3 * (size_t)id + 1]);
-    const float4 e2 = __ldg(&m.face_rec[3 * (size_t)id + 2]);
-    const float wx = qx - a.x, wy = qy - a.y, wz = qz - a.z;
-    const float p1 = wx * e1.x + wy * e1.y + wz * e1.z;
-    const float p2 = wx * e2.x + wy * e2.y + wz * e2.z;
-    const float s = a.w * p1 - e1.w * p2;
-    const float t = e2.w * p2 - e1.w * p1;
-    if (s > 0.f && t > 0.f && s + t < 1.f) {
-      const float cx = a.x + s * e1.x + t * e2.x;
-      const float cy = a.y + s * e1.y + t * e2.y;
-      const float cz = a.z + s * e1.z + t * e2.z;
-      const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
-      const float d2 = ex * ex + ey * ey + ez * ez;
-      if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
-        r.d2 = d2;
-        r.cx = cx;
-        r.cy = cy;
-        r.cz = cz;
-        r.tid = tid;
-        r.w0 = 1.f - s - t;
-        r.w1 = s;
-        r.w2 = t;
-      }
-    }
+    const float4 a = __ldg(&m.face_rec[3 * id]);
+    const float4 e1 = __ldg(&m.face_rec[3 * id + 1]);
+    const float4 e2 = __ldg(&m.face_rec[3 * id + 2]);
+    float u, t;
+    face_foot(a, e1, e2, qx, qy, qz, u, t, cx, cy, cz);
+    if (!(u > 0.f && t > 0.f && u + t < 1.f)) return;
+  }
+  const float ex = qx - cx, ey = qy - cy, ez = qz - cz;
+  const float d2 = ex * ex + ey * ey + ez * ez;
+  if (d2 < r.d2 || (d2 == r.d2 && tid < r.tid)) {
+    r.d2 = d2;
+    r.tid = tid;
   }
 }
 
@@ -614,43 +661,39 @@ __device__ __forceinline__ bool group_best(const Best &r) {
   return (int)lane == __ffs(hold) - 1;
 }
 
+// a2..a8 for one query; returns its nearest vertex row (for closest_of)
 template <bool COUNT = false>
-__device__ __forceinline__ void query_one(const DevView &m, float qx, float qy, float qz,
-                                          Best &r, Work *wk = nullptr, int walk = 2,
-                                          int chunked = 2) {
+__device__ __forceinline__ int query_one(const DevView &m, float qx, float qy, float qz, Best &r,
+                                         Work *wk = nullptr, int walk = 2, int chunked = 2) {
   const int v = find_nearest<COUNT>(m, walk, qx, qy, qz, wk);
-  const float4 pv = __ldg(&m.kd_points[v]);
-  {
-    const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
-    r.d2 = dx * dx + dy * dy + dz * dz;
-    r.cx = pv.x;
-    r.cy = pv.y;
-    r.cz = pv.z;
-    r.tid = (uint32_t)__float_as_int(pv.w);
-    r.w0 = 1.f;
-    r.w1 = 0.f;
-    r.w2 = 0.f;
-  }
+  r = best_of_vertex(m, qx, qy, qz, v);
   scan_list<COUNT>(m, qx, qy, qz, v, chunked, r, wk);
+  return v;
 }
 
 __device__ __forceinline__ bool finite3(float x, float y, float z) {
   return isfinite(x) && isfinite(y) && isfinite(z);
 }
 
-__device__ __forceinline__ void store_result(int64_t o, const Best &r, bool ok, uint8_t st,
+// the outputs of query o (the winner r of a query at (qx, qy, qz) whose
+// nearest vertex is row v); w0 is saved as (1 - w1) - w2, as k_unpack does
+__device__ __forceinline__ void store_result(int64_t o, const DevView &m, float qx, float qy,
+                                             float qz, int v, const Best &r, bool ok, uint8_t st,
                                              float *dist, float *closest, int32_t *prim_id,
                                              uint8_t *prim_type, float4 *save, uint8_t *status) {
   if (ok) {
     dist[o] = sqrtf(r.d2);
-    if (closest) {
-      closest[3 * o] = r.cx;
-      closest[3 * o + 1] = r.cy;
-      closest[3 * o + 2] = r.cz;
+    if (closest || save) {
+      const Closest c = closest_of(m, qx, qy, qz, r.tid, v);
+      if (closest) {
+        closest[3 * o] = c.cx;
+        closest[3 * o + 1] = c.cy;
+        closest[3 * o + 2] = c.cz;
+      }
+      if (save) save[o] = make_float4(__uint_as_float(r.tid), (1.f - c.w1) - c.w2, c.w1, c.w2);
     }
     prim_id[o] = (int32_t)(r.tid & 0x3fffffffu);
     if (prim_type) prim_type[o] = (uint8_t)(r.tid >> 30);
-    if (save) save[o] = make_float4(__uint_as_float(r.tid), r.w0, r.w1, r.w2);
   } else {
     const float nan = __int_as_float(0x7fc00000);
     dist[o] = nan;
@@ -671,15 +714,17 @@ k_query(DevView m, const float4 *__restrict__ sq, int64_t n, float *dist,
   const float4 s = sq[i];
   const int64_t o = __float_as_int(s.w);
   Best r;
+  int v = 0;
   const bool ok = finite3(s.x, s.y, s.z);
   uint8_t st = ok ? 0 : 2;
   if (ok) {
     if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
         s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
       st |= 1;
-    query_one(m, s.x, s.y, s.z, r, nullptr, walk, chunked);
+    v = query_one(m, s.x, s.y, s.z, r, nullptr, walk, chunked);
   }
-  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+  store_result(o, m, s.x, s.y, s.z, v, r, ok, st, dist, closest, prim_id, prim_type, save,
+               status);
 }
 
 
@@ -780,10 +825,11 @@ __device__ __forceinline__ int warp_nearest(const DevView &m, float qx, float qy
   return best;
 }
 
+// returns the lane's nearest vertex row (0 for an inactive lane)
 template <bool COUNT>
-__device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy, float qz,
-                                           bool active, WarpSmem &ws, Best &r, Work *wk,
-                                           int walk) {
+__device__ __forceinline__ int warp_query(const DevView &m, float qx, float qy, float qz,
+                                          bool active, WarpSmem &ws, Best &r, Work *wk,
+                                          int walk) {
   int v;
   if (walk) {
     v = active ? nearest_walk<COUNT>(m, qx, qy, qz, wk, walk == 2) : 0;
@@ -792,18 +838,10 @@ __device__ __forceinline__ void warp_query(const DevView &m, float qx, float qy,
     v = warp_nearest<COUNT>(m, qx, qy, qz, active, ws, wk);
   }
   if (active) {
-    const float4 pv = __ldg(&m.kd_points[v]);
-    const float dx = qx - pv.x, dy = qy - pv.y, dz = qz - pv.z;
-    r.d2 = dx * dx + dy * dy + dz * dz;
-    r.cx = pv.x;
-    r.cy = pv.y;
-    r.cz = pv.z;
-    r.tid = (uint32_t)__float_as_int(pv.w);
-    r.w0 = 1.f;
-    r.w1 = 0.f;
-    r.w2 = 0.f;
+    r = best_of_vertex(m, qx, qy, qz, v);
+    scan_list<COUNT>(m, qx, qy, qz, v, 2, r, wk);
   }
-  if (active) scan_list<COUNT>(m, qx, qy, qz, v, 2, r, wk);
+  return v;
 }
 
 template <bool COUNT>
@@ -820,7 +858,7 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
   const bool ok = i < n && finite3(s.x, s.y, s.z);
   Best r;
   Work w = {0, 0, 0, 0, 0, 0};
-  warp_query<COUNT>(m, s.x, s.y, s.z, ok, ws, r, &w, walk);
+  const int v = warp_query<COUNT>(m, s.x, s.y, s.z, ok, ws, r, &w, walk);
   if (COUNT) {
     int v[6] = {w.nodes, w.points, w.entries, w.edges, w.faces, w.chunks};
 #pragma unroll
@@ -837,7 +875,8 @@ __global__ void k_query_warp(DevView m, const float4 *__restrict__ sq, int64_t n
   if (ok && (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
              s.y > m.dom_hi[1] || s.z > m.dom_hi[2]))
     st |= 1;
-  store_result(o, r, ok, st, dist, closest, prim_id, prim_type, save, status);
+  store_result(o, m, s.x, s.y, s.z, v, r, ok, st, dist, closest, prim_id, prim_type, save,
+               status);
 }
 
 
@@ -882,11 +921,14 @@ __global__ void k_vertex_scatter(const float4 *__restrict__ sq, int64_t n,
   vout[pos] = kr.x;
 }
 
-// three resident 512-thread CTAs per SM: caps k_list_pass at 40 registers
-// (75 % occupancy instead of 50 %), measured 3 % faster on the 1.3M-triangle
-// workload than the uncapped 56 registers
+// four resident 512-thread CTAs per SM: caps k_list_pass at 32 registers
+// (full occupancy; the running best is (d^2, typed id) only, and the few
+// values that spill stay in L1).  On the 1.3M-triangle workload the list
+// pass took 1.105 ms against 1.162 ms at 40 registers (three CTAs) after the
+// Morton sort, 1.104 against 1.117 ms after the seed-vertex sort; the
+// uncapped 56 registers took 1.40 ms
 #ifndef P2M_LIST_MIN_BLOCKS
-#define P2M_LIST_MIN_BLOCKS 3
+#define P2M_LIST_MIN_BLOCKS 4
 #endif
 
 // Pass 2: the list of each query's nearest vertex (regrouped stream).  The
@@ -920,21 +962,12 @@ k_list_pass(DevView m, const float4 *__restrict__ gq, const uint32_t *__restrict
   if (s.x < m.dom_lo[0] || s.y < m.dom_lo[1] || s.z < m.dom_lo[2] || s.x > m.dom_hi[0] ||
       s.y > m.dom_hi[1] || s.z > m.dom_hi[2])
     st |= 1u;
-  Best r;
-  const float4 pv = __ldg(&m.kd_points[v]);
-  const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
-  r.d2 = dx * dx + dy * dy + dz * dz;
-  r.cx = pv.x;
-  r.cy = pv.y;
-  r.cz = pv.z;
-  r.tid = (uint32_t)__float_as_int(pv.w);
-  r.w0 = 1.f;
-  r.w1 = 0.f;
-  r.w2 = 0.f;
+  Best r = best_of_vertex(m, s.x, s.y, s.z, v);
   scan_list<false>(m, s.x, s.y, s.z, v, chunked, r, nullptr, sub, G);
   if (!group_best<G>(r)) return;
-  rec[2 * o] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
-  rec[2 * o + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(st));
+  const Closest c = closest_of(m, s.x, s.y, s.z, r.tid, v);
+  rec[2 * o] = make_float4(c.cx, c.cy, c.cz, sqrtf(r.d2));
+  rec[2 * o + 1] = make_float4(__uint_as_float(r.tid), c.w1, c.w2, __uint_as_float(st));
 }
 
 // Records (caller order) -> the requested outputs, coalesced.  w0 is rebuilt
@@ -1260,9 +1293,11 @@ __global__ void k_batch_query(BatchDesc d, const float4 *__restrict__ sorted, in
       const int64_t l = gi - s_off[k];
       const BatchIO &io = d.ios[k];
       Best r;
+      int v = 0;
       const bool ok = finite3(s.x, s.y, s.z);
-      if (ok) query_one(d.views[k], s.x, s.y, s.z, r);
-      store_result(l, r, ok, 0, io.dist, io.closest, io.prim_id, io.prim_type, nullptr, nullptr);
+      if (ok) v = query_one(d.views[k], s.x, s.y, s.z, r);
+      store_result(l, d.views[k], s.x, s.y, s.z, v, r, ok, 0, io.dist, io.closest, io.prim_id,
+                   io.prim_type, nullptr, nullptr);
     }
   }
 }
@@ -1292,9 +1327,12 @@ __global__ void k_batch_nn(BatchDesc d, const float4 *__restrict__ sorted, int64
 }
 
 // resident 512-thread CTAs per SM the persistent batch list kernel is
-// compiled for (its register cap), as P2M_LIST_MIN_BLOCKS for k_list_pass
+// compiled for (its register cap, 40 registers): its mesh descriptor is
+// indexed by a run-time mesh number, so its fields take registers that
+// k_list_pass reads from its parameters, and a 32-register cap would spill
+// more than it does now
 #ifndef P2M_BATCH_LIST_MIN_BLOCKS
-#define P2M_BATCH_LIST_MIN_BLOCKS P2M_LIST_MIN_BLOCKS
+#define P2M_BATCH_LIST_MIN_BLOCKS 3
 #endif
 
 template <int G>
@@ -1337,21 +1375,12 @@ k_batch_list(BatchDesc d, const float4 *__restrict__ grouped, const uint32_t *__
         rec[2 * gi + 1] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, __uint_as_float(2u));
         continue;
       }
-      Best r;
-      const float4 pv = __ldg(&m.kd_points[v]);
-      const float dx = s.x - pv.x, dy = s.y - pv.y, dz = s.z - pv.z;
-      r.d2 = dx * dx + dy * dy + dz * dz;
-      r.cx = pv.x;
-      r.cy = pv.y;
-      r.cz = pv.z;
-      r.tid = (uint32_t)__float_as_int(pv.w);
-      r.w0 = 1.f;
-      r.w1 = 0.f;
-      r.w2 = 0.f;
+      Best r = best_of_vertex(m, s.x, s.y, s.z, (int)v);
       scan_list<false>(m, s.x, s.y, s.z, (int)v, 2, r, nullptr, sub, G);
       if (!group_best<G>(r)) continue;
-      rec[2 * gi] = make_float4(r.cx, r.cy, r.cz, sqrtf(r.d2));
-      rec[2 * gi + 1] = make_float4(__uint_as_float(r.tid), r.w1, r.w2, __uint_as_float(0u));
+      const Closest c = closest_of(m, s.x, s.y, s.z, r.tid, (int)v);
+      rec[2 * gi] = make_float4(c.cx, c.cy, c.cz, sqrtf(r.d2));
+      rec[2 * gi + 1] = make_float4(__uint_as_float(r.tid), c.w1, c.w2, __uint_as_float(0u));
     }
   }
 }
