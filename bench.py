@@ -724,7 +724,7 @@ def measure_forward(pg, m, args, local, *, steps, warmup, flush=None, dist=None,
                    "table_entries": st["n_entries"], "max_list": st["max_list"],
                    "build_split_ms": {"cells": st["cells_ms"],
                                       "flooding_and_packing": st["inspect_ms"]},
-                   "flooding": mesh.flood_stats()}}
+                   "flooding": mesh.flood_stats(), "cells": mesh.cell_stats()}}
     mesh.close()
     del q, out
     torch.cuda.empty_cache()

@@ -74,14 +74,17 @@ typedef struct {
   float delta_rel;     /* conservative widening of cells, Space-perp half-spaces, filter
                           and Region boxes, as a fraction of diag(D) (default 4e-6)        */
   int host_threads;    /* preprocessing threads, 0 = all cores (default 0)                 */
-  int device_assist;   /* 1 = certify Voronoi cells on the GPU (float32 nearest-vertex
-                          proposals, exact searches decided in double precision),
-                          2 = that and the flooding (Alg. 1) on the GPU too (one warp per
-                          primitive, the same double-precision steps, no fused
-                          multiply-adds), 0 = CPU only.
-                          Every setting gives the same tables bit for bit (default 2,
-                          the fastest build on a GB300; without a GPU every setting
-                          builds on the host)                                          */
+  int device_assist;   /* 1 = the exact searches that certify the corners of the Voronoi
+                          cells on the GPU (double-precision decisions),
+                          2 = that and the flooding (Alg. 1, one warp per primitive) on
+                          the GPU, 3 = that and the whole cell stage on the GPU too (one
+                          thread per cell), 0 = CPU only.  The GPU steps are the host's
+                          double-precision steps without fused multiply-adds; what
+                          their buffers cannot hold is handed back to the host.
+                          Every setting gives the same layout bit for bit (default 2,
+                          the fastest build on a GB300: its FP64 rate makes the cell
+                          stage slower there than on the host's cores; without a GPU
+                          every setting builds on the host)                            */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
 } p2m_build_opts;
 
@@ -436,6 +439,13 @@ p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]);
  * buffers, or whose cap loop needs the angular ordering).  All zero for a
  * handle made by p2m_load. */
 p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]);
+
+/* How the Voronoi cells of a handle's build were split: out[0] = cells
+ * made on the device (device_assist = 3), out[1] = made on the host (every
+ * cell with device_assist 0 to 2; with 3 the ones whose work overflowed the
+ * device's fixed buffers, whose cap loop needs the angular ordering or
+ * whose exact search gave up).  Both zero for a handle made by p2m_load. */
+p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[2]);
 
 /* The domain D (lo xyz, hi xyz) and delta of a handle. */
 p2m_status p2m_domain(const p2m_handle *h, float out[7]);

@@ -77,8 +77,8 @@ class P2M:
     preprocessing (Alg. A.1) through ``p2m_build``.  ``verts`` (V,3) float32
     and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors.
     ``device_assist``: False/0 host only, True/1 Voronoi-cell certification
-    on the GPU, 2 (default) the flooding (Alg. 1) on the GPU as well; every
-    setting gives the same tables."""
+    on the GPU, 2 (default) the flooding (Alg. 1) on the GPU as well, 3 the
+    whole Voronoi-cell stage too; every setting gives the same layout."""
 
     def __init__(self, verts=None, tris=None, *, segs=None, domain_scale=10.0,
                  domain_margin=0.0, delta_rel=4e-6, host_threads=0, device_assist=2,
@@ -92,8 +92,8 @@ class P2M:
                 np.zeros((0, 3)) if tris is None else tris, dtype=np.int32).reshape(-1, 3))
             desc = MeshDesc(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
             assist = int(device_assist)
-            if assist not in (0, 1, 2):
-                raise ValueError("device_assist must be 0, 1 or 2")
+            if assist not in (0, 1, 2, 3):
+                raise ValueError("device_assist must be 0, 1, 2 or 3")
             opts = BuildOpts(domain_scale, domain_margin, delta_rel, host_threads, assist,
                              leaf_size)
             h = ctypes.c_void_p()
@@ -153,6 +153,13 @@ class P2M:
         out = (ctypes.c_int64 * 3)()
         check(lib.p2m_flood_stats(self._h, out), "p2m_flood_stats")
         return {"device": out[0], "host_bounded": out[1], "host_unbounded": out[2]}
+
+    def cell_stats(self):
+        """How the build's Voronoi cells were split: made on the device, on
+        the host."""
+        out = (ctypes.c_int64 * 2)()
+        check(lib.p2m_cell_stats(self._h, out), "p2m_cell_stats")
+        return {"device": out[0], "host": out[1]}
 
     def domain(self):
         """(lo, hi, delta): the query domain D and the widening margin."""

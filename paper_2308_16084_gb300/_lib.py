@@ -70,6 +70,7 @@ _SIGS = {
     "p2m_get_edges": (_INT, [_P, _P, _P]),
     "p2m_stats": (_INT, [_P, _P]),
     "p2m_flood_stats": (_INT, [_P, _P]),
+    "p2m_cell_stats": (_INT, [_P, _P]),
     "p2m_domain": (_INT, [_P, _P]),
     "p2m_get_list": (_INT, [_P, ctypes.c_int32, _P, _P, _P, _I64, _P]),
     "p2m_save": (_INT, [_P, ctypes.c_char_p]),

@@ -26,7 +26,7 @@ def _nvcc():
 def _sources():
     return {
         "kernels.cu": "cu", "certify.cu": "cu", "p2m_api.cu": "cu", "noalloc.cu": "cu",
-        "flood.cu": "cu-nofma", "builder.cpp": "cpp",
+        "flood.cu": "cu-nofma", "cells.cu": "cu-nofma", "builder.cpp": "cpp",
     }
 
 
@@ -51,8 +51,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(OUT, src + ".o")
         path = os.path.join(CSRC, src)
         if kind.startswith("cu"):
-            # the device flooding must round every double operation on its
-            # own, as the host builder (-ffp-contract=off) does
+            # the device flooding and cells must round every double
+            # operation on its own, as the host builder (-ffp-contract=off)
+            # does
             nofma = ["-fmad=false"] if kind == "cu-nofma" else []
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-Xptxas", "-v" if verbose else "-O3", *nofma, *extra, *inc, "-c", path,

@@ -654,22 +654,72 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   for (int d = 0; d < 6; ++d) out.kd_root[d] = (float)T.box[d];
   if (on_tree && nearest && !on_tree(ctx, out)) nearest = nullptr;
 
-  // ---- Voronoi cells: k-nearest seeding
+  // ---- Voronoi cells: on the device service when asked (cell_core.h: the
+  // same steps, the same values); the rows it hands back, or all of them,
+  // here
   const double t_cells = now_ms();
-  std::vector<CellWork> cells(nv);
+  const double epsc = 1e-12 * diag * diag;
+  const bool trace = std::getenv("P2M_BUILD_TRACE") != nullptr;
+  std::vector<std::vector<int32_t>> nbr(nv);
+  std::vector<Poly> cell(nv);  // widened cells (loops only: no planes)
+  std::vector<int64_t> todo;   // rows whose cells are made here
+  bool cells_done_on_device = false;
+  int64_t rounds = 0, cert_queries = 0;  // the certification's counts over all rows
+  if (prm.device_cells && nearest) {
+    CellProblem cp;
+    cp.nv = nv;
+    for (int d = 0; d < 3; ++d) {
+      cp.lo[d] = Dlo[d];
+      cp.hi[d] = Dhi[d];
+    }
+    cp.eps = eps;
+    cp.epsc = epsc;
+    cp.delta = delta;
+    CellResult cr;
+    if (nearest->cells(cp, cr) && (int64_t)cr.gave_up.size() == nv &&
+        (int64_t)cr.nb_off.size() == nv + 1 && (int64_t)cr.pt_off.size() == nv + 1 &&
+        (int64_t)cr.beg_off.size() == nv + 1) {
+      cells_done_on_device = true;
+      rounds = cr.rounds;
+      cert_queries = cr.queries;
+      parallel_for(nv, threads, 1024, [&](int64_t p, int) {
+        if (cr.gave_up[p]) return;
+        nbr[p].assign(cr.nb.begin() + cr.nb_off[p], cr.nb.begin() + cr.nb_off[p + 1]);
+        Poly &c = cell[p];
+        c.pt.resize((size_t)(cr.pt_off[p + 1] - cr.pt_off[p]));
+        for (size_t i = 0; i < c.pt.size(); ++i) {
+          const double *x = &cr.pt[3 * ((size_t)cr.pt_off[p] + i)];
+          c.pt[i] = {x[0], x[1], x[2]};
+        }
+        c.beg.assign(cr.beg.begin() + cr.beg_off[p], cr.beg.begin() + cr.beg_off[p + 1]);
+      });
+      for (int64_t p = 0; p < nv; ++p)
+        if (cr.gave_up[p]) todo.push_back(p);
+    }
+  }
+  if (!cells_done_on_device) {
+    todo.resize(nv);
+    for (int64_t p = 0; p < nv; ++p) todo[p] = p;
+  }
+  out.cells_device = nv - (int64_t)todo.size();
+  out.cells_host = (int64_t)todo.size();
+  const int64_t nt = (int64_t)todo.size();
+  // k-nearest seeding of the rows in todo (cells[i] is row todo[i])
+  std::vector<CellWork> cells(nt);
   std::vector<CutScratch> scratch(threads);
   std::vector<Poly> tmp(threads);
   const bool fail_cells = inject_at("cells");
-  parallel_for(nv, threads, 64, [&](int64_t p, int t) {
-    if (fail_cells && p == nv / 2) throw std::bad_alloc();
-    CellWork &C = cells[p];
+  parallel_for(nt, threads, 64, [&](int64_t i, int t) {
+    if (fail_cells && i == nt / 2) throw std::bad_alloc();
+    const int64_t p = todo[i];
+    CellWork &C = cells[i];
     make_box(C.poly, Dlo, Dhi);
     int64_t ids[KSEED];
     double d2s[KSEED];
     int k = k_nearest(T, T.P[p], p, KSEED, ids, d2s);
-    for (int i = 0; i < k; ++i) {
-      if (cut(C.poly, bisector(T, p, ids[i], 0.0), eps, tmp[t], scratch[t])) std::swap(C.poly, tmp[t]);
-      C.applied.push_back((int32_t)ids[i]);
+    for (int j = 0; j < k; ++j) {
+      if (cut(C.poly, bisector(T, p, ids[j], 0.0), eps, tmp[t], scratch[t])) std::swap(C.poly, tmp[t]);
+      C.applied.push_back((int32_t)ids[j]);
     }
     // no vertex outside the k nearest can be nearer than p to a corner that
     // lies within half the k-th distance of p
@@ -677,127 +727,66 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   });
 
   // optional trace of the cell stage on stderr (P2M_BUILD_TRACE=1)
-  const bool trace = std::getenv("P2M_BUILD_TRACE") != nullptr;
-  if (trace) std::fprintf(stderr, "p2m build: seeding %.0f ms\n", now_ms() - t_cells);
-  std::atomic<int64_t> host_searches{0};
+  if (trace)
+    std::fprintf(stderr, "p2m build: %lld cells on the device, seeding of %lld here %.0f ms\n",
+                 (long long)out.cells_device, (long long)nt, now_ms() - t_cells);
   // ---- certification rounds: a corner x is settled when no vertex is
-  // strictly nearer to x than the cell's own vertex; a cell whose corners
-  // are all settled equals Cell(v) ∩ D (it is convex and contains the cell).
-  const double epsc = 1e-12 * diag * diag;
-  std::vector<std::vector<V3>> corner(nv);
-  std::vector<int64_t> coff(nv + 1);
-  std::vector<float> qbuf;
-  std::vector<int32_t> qans;
-  int64_t rounds = 0, cert_queries = 0;
+  // strictly nearer to x than the cell's own vertex (the exact search, on
+  // the device when it offers one); a cell whose corners are all settled
+  // equals Cell(v) ∩ D (it is convex and contains the cell)
+  std::vector<std::vector<V3>> corner(nt);
+  std::vector<int64_t> coff(nt + 1);
+  int64_t host_rounds = 0;
   for (;;) {
     // far corners of the cells still open
-    parallel_for(nv, threads, 256, [&](int64_t p, int) {
-      auto &cv = corner[p];
+    parallel_for(nt, threads, 256, [&](int64_t i, int) {
+      auto &cv = corner[i];
       cv.clear();
-      if (cells[p].done) return;
+      if (cells[i].done) return;
       std::vector<V3> all;
-      distinct_corners(cells[p].poly, all);
+      distinct_corners(cells[i].poly, all);
       for (V3 x : all)
-        if (len2(x - T.P[p]) > cells[p].safe2) cv.push_back(x);
-      if (cv.empty()) cells[p].done = true;
+        if (len2(x - T.P[todo[i]]) > cells[i].safe2) cv.push_back(x);
+      if (cv.empty()) cells[i].done = true;
     });
     coff[0] = 0;
-    for (int64_t p = 0; p < nv; ++p) coff[p + 1] = coff[p] + (int64_t)corner[p].size();
-    const int64_t nq = coff[nv];
+    for (int64_t i = 0; i < nt; ++i) coff[i + 1] = coff[i] + (int64_t)corner[i].size();
+    const int64_t nq = coff[nt];
     if (nq == 0) break;
-    ++rounds;
+    ++host_rounds;
+    rounds = std::max(rounds, host_rounds);
     cert_queries += nq;
     const double t_round = now_ms();
-    host_searches = 0;
-    bool used_device = false;
+    // the exact search of every corner: the nearest vertex strictly nearer
+    // than the cell's own (-2: not answered, searched here)
+    std::vector<int64_t> w_of(nq, -2);
     if (nearest) {
-      qbuf.resize(3 * nq);
-      qans.resize(nq);
-      parallel_for(nv, threads, 256, [&](int64_t p, int) {
-        for (size_t i = 0; i < corner[p].size(); ++i) {
-          V3 x = corner[p][i];
-          float *o = &qbuf[3 * (coff[p] + i)];
-          o[0] = (float)x.x;
-          o[1] = (float)x.y;
-          o[2] = (float)x.z;
+      std::vector<double> xs(3 * (size_t)nq), rs(nq);
+      parallel_for(nt, threads, 256, [&](int64_t i, int) {
+        for (size_t j = 0; j < corner[i].size(); ++j) {
+          const int64_t g = coff[i] + (int64_t)j;
+          const V3 x = corner[i][j];
+          xs[3 * g] = x.x;
+          xs[3 * g + 1] = x.y;
+          xs[3 * g + 2] = x.z;
+          rs[g] = len2(x - T.P[todo[i]]) - epsc;
         }
       });
-      used_device = nearest->query(qbuf.data(), nq, qans.data());
+      if (!nearest->within(xs.data(), rs.data(), nq, w_of.data()))
+        std::fill(w_of.begin(), w_of.end(), -2);
     }
-    // corners whose float32 proposal does not settle them: decided by the
-    // exact double-precision search, on the device when it offers one
-    std::vector<int64_t> exact(nq, -3);  // -3: not needed
-    if (used_device) {
-      // the corners each row needs searched, then their points and bounds
-      // packed row by row at offsets from a prefix sum
-      std::vector<uint8_t> need(nq, 0);
-      std::vector<int64_t> need_off(nv + 1, 0);
-      parallel_for(nv, threads, 256, [&](int64_t p, int) {
-        int64_t c = 0;
-        for (size_t i = 0; i < corner[p].size(); ++i) {
-          const int64_t g = coff[p] + (int64_t)i;
-          const V3 x = corner[p][i];
-          const double r2 = len2(x - T.P[p]) - epsc;
-          const int64_t prop = qans[g];
-          const bool settled = prop == p || (prop >= 0 && len2(T.P[prop] - x) < r2);
-          need[g] = settled ? 0 : 1;
-          c += need[g];
-        }
-        need_off[p + 1] = c;
-      });
-      for (int64_t p = 0; p < nv; ++p) need_off[p + 1] += need_off[p];
-      const int64_t nneed = need_off[nv];
-      if (nneed > 0) {
-        std::vector<double> xs(3 * (size_t)nneed), rs(nneed);
-        std::vector<int64_t> ans(nneed);
-        parallel_for(nv, threads, 256, [&](int64_t p, int) {
-          int64_t k = need_off[p];
-          for (size_t i = 0; i < corner[p].size(); ++i)
-            if (need[coff[p] + (int64_t)i]) {
-              const V3 x = corner[p][i];
-              xs[3 * k] = x.x;
-              xs[3 * k + 1] = x.y;
-              xs[3 * k + 2] = x.z;
-              rs[k] = len2(x - T.P[p]) - epsc;
-              ++k;
-            }
-        });
-        const double t_dev = now_ms();
-        if (nearest->within(xs.data(), rs.data(), nneed, ans.data()))
-          parallel_for(nv, threads, 256, [&](int64_t p, int) {
-            int64_t k = need_off[p];
-            for (size_t i = 0; i < corner[p].size(); ++i)
-              if (need[coff[p] + (int64_t)i]) exact[coff[p] + (int64_t)i] = ans[k++];
-          });
-        if (trace) std::fprintf(stderr, "p2m build:   exact device search %.0f ms\n", now_ms() - t_dev);
-      }
-    }
-    parallel_for(nv, threads, 64, [&](int64_t p, int t) {
-      CellWork &C = cells[p];
-      if (corner[p].empty()) return;
+    std::atomic<int64_t> host_searches{0};
+    parallel_for(nt, threads, 64, [&](int64_t i, int t) {
+      CellWork &C = cells[i];
+      if (corner[i].empty()) return;
+      const int64_t p = todo[i];
       std::vector<int64_t> cand;
-      for (size_t i = 0; i < corner[p].size(); ++i) {
-        V3 x = corner[p][i];
-        double r2 = len2(x - T.P[p]) - epsc;
-        int64_t w;
-        if (used_device) {
-          // the float32 search proposes, double precision decides; when the
-          // proposal is another vertex that is not strictly nearer in double
-          // (a float32 near-tie), the exact search settles the corner
-          const int64_t prop = qans[coff[p] + i];
-          w = (prop >= 0 && prop != p && len2(T.P[prop] - x) < r2) ? prop : -1;
-          if (w < 0 && prop != p) {
-            const int64_t e = exact[coff[p] + i];
-            if (e >= -1) {
-              w = e;
-            } else {
-              w = nearest_within(T, x, r2);
-              if (trace) ++host_searches;
-            }
-          }
-        } else {
-          w = nearest_within(T, x, r2);
-          if (trace) ++host_searches;
+      for (size_t j = 0; j < corner[i].size(); ++j) {
+        const V3 x = corner[i][j];
+        int64_t w = w_of[coff[i] + (int64_t)j];
+        if (w < -1) {
+          w = nearest_within(T, x, len2(x - T.P[p]) - epsc);
+          ++host_searches;
         }
         if (w >= 0 && w != p &&
             std::find(C.applied.begin(), C.applied.end(), (int32_t)w) == C.applied.end() &&
@@ -808,7 +797,8 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
         C.done = true;
         return;
       }
-      std::sort(cand.begin(), cand.end(), [&](int64_t a, int64_t b) {
+      // nearest first; equal distances in the order found
+      std::stable_sort(cand.begin(), cand.end(), [&](int64_t a, int64_t b) {
         return len2(T.P[a] - T.P[p]) < len2(T.P[b] - T.P[p]);
       });
       for (int64_t w : cand) {
@@ -817,23 +807,19 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       }
     });
     if (trace)
-      std::fprintf(stderr, "p2m build: round %lld: %lld corners, %lld exact searches on the "
-                   "device, %lld on the host, %.0f ms\n",
-                   (long long)rounds, (long long)nq,
-                   (long long)std::count_if(exact.begin(), exact.end(),
-                                            [](int64_t e) { return e >= -1; }),
+      std::fprintf(stderr, "p2m build: round %lld: %lld corners, %lld searched on the host, "
+                   "%.0f ms\n", (long long)host_rounds, (long long)nq,
                    (long long)host_searches.load(), now_ms() - t_round);
-    if (rounds > 64) break;
+    if (host_rounds > 64) break;
   }
   corner.clear();
   corner.shrink_to_fit();
 
   // neighbours (generators of surviving bisector faces) and widened cells
-  std::vector<std::vector<int32_t>> nbr(nv);
-  std::vector<Poly> cell(nv);
-  parallel_for(nv, threads, 64, [&](int64_t p, int t) {
+  parallel_for(nt, threads, 64, [&](int64_t i, int t) {
+    const int64_t p = todo[i];
     auto &nb = nbr[p];
-    for (const Plane &h : cells[p].poly.pl)
+    for (const Plane &h : cells[i].poly.pl)
       if (h.src >= 0 && std::find(nb.begin(), nb.end(), h.src) == nb.end()) nb.push_back(h.src);
     double wlo[3], whi[3];
     for (int d = 0; d < 3; ++d) {
@@ -844,11 +830,13 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     make_box(c, wlo, whi);
     for (int32_t w : nb)
       if (cut(c, bisector(T, p, w, delta), eps, tmp[t], scratch[t])) std::swap(c, tmp[t]);
-    cells[p].poly.clear();
-    cells[p].poly.pl.shrink_to_fit();
-    cells[p].poly.pt.shrink_to_fit();
-    cells[p].applied.clear();
-    cells[p].applied.shrink_to_fit();
+    c.pl.clear();
+    c.pl.shrink_to_fit();
+    cells[i].poly.clear();
+    cells[i].poly.pl.shrink_to_fit();
+    cells[i].poly.pt.shrink_to_fit();
+    cells[i].applied.clear();
+    cells[i].applied.shrink_to_fit();
   });
   cells.clear();
   cells.shrink_to_fit();

@@ -22,6 +22,32 @@ struct BuildParams {
   int threads = 0;
   int leaf_size = 8;
   bool device_flood = false;  // flood on the nearest service when it offers that
+  bool device_cells = false;  // Voronoi cells on the nearest service when it offers that
+};
+
+// The Voronoi cells of every row (KD-tree position), clipped to D, for a
+// device service: what the builder's cell stage takes (cell_core.h).
+struct CellProblem {
+  int64_t nv = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};  // the domain D
+  double eps = 0, epsc = 0, delta = 0;
+};
+
+// What a device service returns: per row, gave_up[p] = 1 where the host
+// must compute the cell itself, else its Voronoi neighbours
+// nb[nb_off[p] .. nb_off[p+1]) (rows, in the order of its faces) and its
+// widened cell (points pt[3 pt_off[p] ..), loops as in FloodProblem).
+struct CellResult {
+  std::vector<uint8_t> gave_up;
+  std::vector<int64_t> nb_off;
+  std::vector<int32_t> nb;
+  std::vector<int64_t> pt_off;
+  std::vector<double> pt;
+  std::vector<int64_t> beg_off;
+  std::vector<int32_t> beg;
+  // over the rows it kept: the most certification rounds one of them took
+  // and the corners they searched (the host's own counts over those rows)
+  int64_t rounds = 0, queries = 0;
 };
 
 // The flooding inspection (Alg. 1) of a set of primitives, for a device
@@ -62,12 +88,11 @@ struct FloodRec {
   float box[6];
 };
 
-// Batched nearest-vertex service used to certify Voronoi cells.  query()
-// receives float32 points and writes the KD-tree position of the nearest
-// vertex of each (or -1).
+// Device services of the builder: the exact search that certifies the
+// Voronoi cells' corners, the whole cell stage and the flooding.  Each
+// returns false where it is unavailable (the host then does the work).
 struct NearestService {
   virtual ~NearestService() = default;
-  virtual bool query(const float *xyz, int64_t n, int32_t *out_pos) = 0;
   // exact (double precision) certification search: for each x (3 doubles)
   // the nearest KD-tree position strictly closer than sqrt(r2), -1 if none,
   // -2 where the service gave up (the host searches); false = unavailable
@@ -82,6 +107,12 @@ struct NearestService {
   virtual bool flood(const FloodProblem &pb, std::vector<FloodRec> &out,
                      std::vector<uint8_t> &gave_up, int64_t &inspections) {
     (void)pb, (void)out, (void)gave_up, (void)inspections;
+    return false;
+  }
+  // the Voronoi cell of every row as the host builder computes it (the same
+  // values bit for bit), with the rows it hands back marked
+  virtual bool cells(const CellProblem &pb, CellResult &out) {
+    (void)pb, (void)out;
     return false;
   }
 };
@@ -142,6 +173,8 @@ struct Layout {
   // primitives flooded on the device, by the host's bounded core and by its
   // unbounded code (the ones the core gave up)
   int64_t flood_device = 0, flood_bounded = 0, flood_unbounded = 0;
+  // Voronoi cells made on the device and on the host
+  int64_t cells_device = 0, cells_host = 0;
   double ms_total = 0, ms_cells = 0, ms_inspect = 0;
 };
 

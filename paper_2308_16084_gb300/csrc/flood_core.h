@@ -109,20 +109,25 @@ constexpr int kMaxF = 96;    // faces of a work polytope
 constexpr int kMaxP = 512;   // loop points of a work polytope (or of a cell)
 constexpr int kMaxPerp = 16; // Space-perp half-spaces of one primitive
 
-// work polytope: face f's loop is pt[beg[f] .. beg[f+1])
+// work polytope: face f's loop is pt[beg[f] .. beg[f+1]); src[f] is the id
+// of whatever generated face f's plane (kept by cut for the Voronoi cells,
+// whose neighbours are the generators of their faces)
 struct WPoly {
   int nf, np;
   int32_t beg[kMaxF + 1];
+  int32_t src[kMaxF];
   D3 pt[kMaxP];
 };
 
 // read-only polytope: a cell in the caller's storage or a work polytope
+// (src: the faces' generators, or null where nobody needs them)
 struct PView {
   const D3 *pt;
   const int32_t *beg;  // nf + 1 loop starts
   int nf, np;
+  const int32_t *src;
 };
-P2M_HD PView view(const WPoly &w) { return {w.pt, w.beg, w.nf, w.np}; }
+P2M_HD PView view(const WPoly &w) { return {w.pt, w.beg, w.nf, w.np, w.src}; }
 
 struct Work {
   WPoly A, B;
@@ -166,7 +171,8 @@ struct Flat {
 
   P2M_HD PView cell(int32_t p) const {
     const int64_t b0 = beg_off[p], p0 = pt_off[p];
-    return {pt + p0, beg + b0, (int)(beg_off[p + 1] - b0 - 1), (int)(pt_off[p + 1] - p0)};
+    return {pt + p0, beg + b0, (int)(beg_off[p + 1] - b0 - 1), (int)(pt_off[p + 1] - p0),
+            nullptr};
   }
   P2M_HD D3 pv(int32_t p) const { return pos[p]; }
   P2M_HD int32_t vid(int32_t p) const { return vids[p]; }
@@ -216,8 +222,10 @@ P2M_HD D3 crossing(D3 a, D3 b, double sa, double sb) {
 // the hole is closed by a cap face chained from the loops' exit and entry
 // points.  kCutNone: nothing lies beyond (out untouched); kCutDone: out
 // holds the result (no faces when emptied); kCutGiveUp: a capacity would be
-// exceeded or the cap could not be chained.
-P2M_HD int cut(PView in, D3 hn, double hc, double eps, WPoly &out, Work &W) {
+// exceeded or the cap could not be chained.  A kept face keeps its
+// generator (in.src, -1 without one), the cap gets hsrc.
+P2M_HD int cut(PView in, D3 hn, double hc, double eps, WPoly &out, Work &W,
+               int32_t hsrc = -1) {
   if (in.np > kMaxP) return kCutGiveUp;
   bool beyond = false, within = false;
   for (int i = 0; i < in.np; ++i) {
@@ -267,6 +275,7 @@ P2M_HD int cut(PView in, D3 hn, double hc, double eps, WPoly &out, Work &W) {
     }
     if (out.np - start >= 3) {
       if (out.nf >= kMaxF) return kCutGiveUp;
+      out.src[out.nf] = in.src ? in.src[f] : -1;
       out.beg[++out.nf] = out.np;
     } else {
       out.np = start;
@@ -302,6 +311,7 @@ P2M_HD int cut(PView in, D3 hn, double hc, double eps, WPoly &out, Work &W) {
       cur = W.seg_out[best];
     }
     if (!(len2(cur - W.seg_in[0]) <= 1e6 * eps * eps)) return kCutGiveUp;
+    out.src[out.nf] = hsrc;
     out.beg[++out.nf] = out.np;
   }
   if (out.nf < 4) {

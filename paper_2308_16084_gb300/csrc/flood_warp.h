@@ -61,14 +61,17 @@ constexpr int kWQ = 1024;   // vertices one primitive may visit
 struct WPoly {
   int nf, np;
   int32_t beg[kWF + 1];
+  int32_t src[kWF];  // generator of each face's plane (fc::WPoly)
   D3 pt[kWP];
 };
 
 // polytope being read: a cell in global memory or a WPoly of this warp
+// (src: the faces' generators, or null)
 struct View {
   const D3 *pt;
   const int32_t *beg;
   int nf, np;
+  const int32_t *src;
 };
 
 struct WarpWork {
@@ -89,12 +92,14 @@ struct WarpWork {
   int cnt_np, cnt_nf;
 };
 
-P2M_HD View view_of(const WPoly &w) { return {w.pt, w.beg, w.nf, w.np}; }
+P2M_HD View view_of(const WPoly &w) { return {w.pt, w.beg, w.nf, w.np, w.src}; }
 
 enum { kNone = 0, kDone = 1, kGiveUp = 2 };
 
-// cut `in` by n.x <= c into `out` (fc::cut, lane-parallel)
-P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &out) {
+// cut `in` by n.x <= c into `out` (fc::cut, lane-parallel; a kept face
+// keeps its generator, the cap gets hsrc)
+P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &out,
+                    int32_t hsrc = -1) {
   if (in.np > kWIn || in.nf > kWF) return kGiveUp;
   P2M_LANES(l)
     bool b = false, w = false;
@@ -195,6 +200,7 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
         }
       }
       out.beg[S.frank[f]] = S.foff[f];
+      out.src[S.frank[f]] = in.src ? in.src[f] : -1;
     }
   P2M_END_LANES
   // the cap loop, chained by lane 0 (segments in face order, as the serial
@@ -229,7 +235,10 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
         }
       }
       if (ok && !(len2(cur - S.seg_in[first]) <= 1e6 * eps * eps)) ok = 0;
-      if (ok) out.beg[++nf] = np;
+      if (ok) {
+        out.src[nf] = hsrc;
+        out.beg[++nf] = np;
+      }
     }
     if (nf < 4) {
       nf = 0;
@@ -281,7 +290,7 @@ P2M_HD int flood_warp(WarpWork &S, Env &env, int64_t k, double eps, double delta
     P2M_SYNC;
     ++insp;
     const fc::PView cv = env.cell(p);
-    const View cell{cv.pt, cv.beg, cv.nf, cv.np};
+    const View cell{cv.pt, cv.beg, cv.nf, cv.np, nullptr};
     // a half-space with every point of the cell beyond it empties the result
     bool emptied = false;
     for (int j = 0; j < P.np && !emptied; ++j) {

@@ -17,6 +17,7 @@
 
 #include "../../include/p2m.h"
 #include "builder.h"
+#include "cells.h"
 #include "certify.h"
 #include "flood.h"
 #include "quant.h"
@@ -268,32 +269,11 @@ struct p2m_handle {
 
 namespace {
 
-// Nearest-vertex service for the builder: runs the device KD-tree search.
+// Device services of the builder: the exact certification search, the
+// Voronoi cells and the flooding, on the handle's device.
 struct DeviceNearest : p2m::NearestService {
   p2m_handle *h;
   explicit DeviceNearest(p2m_handle *hh) : h(hh) {}
-  bool query(const float *xyz, int64_t n, int32_t *out) override {
-    const int64_t chunk = 1 << 24;
-    float *dq = nullptr;
-    int32_t *dout = nullptr;
-    int64_t m = std::min(n, chunk);
-    if (cudaMalloc((void **)&dq, 12 * m) != cudaSuccess) return false;
-    if (cudaMalloc((void **)&dout, 4 * m) != cudaSuccess) {
-      cudaFree(dq);
-      return false;
-    }
-    bool ok = true;
-    for (int64_t s = 0; s < n && ok; s += chunk) {
-      int64_t k = std::min(chunk, n - s);
-      ok = cudaMemcpy(dq, xyz + 3 * s, 12 * k, cudaMemcpyHostToDevice) == cudaSuccess &&
-           p2m::launch_nearest(h->view, dq, k, dout, 0) == cudaSuccess &&
-           cudaMemcpy(out + s, dout, 4 * k, cudaMemcpyDeviceToHost) == cudaSuccess;
-    }
-    cudaFree(dq);
-    cudaFree(dout);
-    if (!ok) cudaGetLastError();
-    return ok;
-  }
   bool within(const double *xyz, const double *r2, int64_t n, int64_t *out) override {
     const int64_t chunk = 1 << 22;
     const int64_t m = std::min(n, chunk);
@@ -318,6 +298,9 @@ struct DeviceNearest : p2m::NearestService {
   bool flood(const p2m::FloodProblem &pb, std::vector<p2m::FloodRec> &out,
              std::vector<uint8_t> &gave_up, int64_t &inspections) override {
     return p2m::flood_on_device(pb, out, gave_up, inspections);
+  }
+  bool cells(const p2m::CellProblem &pb, p2m::CellResult &out) override {
+    return p2m::cells_on_device(h->view, pb, out);
   }
 };
 
@@ -382,7 +365,7 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
   p2m_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.domain_scale > 0.f) || !(o.domain_margin >= 0.f) || !(o.delta_rel >= 0.f) ||
-      o.leaf_size < 2 || o.leaf_size > 32 || o.device_assist < 0 || o.device_assist > 2)
+      o.leaf_size < 2 || o.leaf_size > 32 || o.device_assist < 0 || o.device_assist > 3)
     return P2M_ERR_INVALID_ARG;
   std::unique_ptr<p2m_handle> h(new (std::nothrow) p2m_handle());
   if (!h) return P2M_ERR_OOM;
@@ -395,7 +378,8 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
   prm.delta_rel = o.delta_rel;
   prm.threads = o.host_threads;
   prm.leaf_size = o.leaf_size;
-  prm.device_flood = o.device_assist == 2;
+  prm.device_flood = o.device_assist >= 2;
+  prm.device_cells = o.device_assist == 3;
   DeviceNearest dn(h.get());
   const bool assist = o.device_assist && h->device >= 0;
   std::string err;
@@ -868,6 +852,13 @@ p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]) {
   out[0] = h->L.flood_device;
   out[1] = h->L.flood_bounded;
   out[2] = h->L.flood_unbounded;
+  return P2M_OK;
+}
+
+p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[2]) {
+  if (!h || !out) return P2M_ERR_INVALID_ARG;
+  out[0] = h->L.cells_device;
+  out[1] = h->L.cells_host;
   return P2M_OK;
 }
 

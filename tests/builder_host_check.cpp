@@ -3,15 +3,18 @@
 // vertices, int32 triangles and segments, domain scale and margin) and
 //   1. builds the layout on the host;
 //   2. builds it again through a stand-in for the device services: the
-//      certification searches answered by brute force under the same rules
-//      (float32 proposal of the nearest vertex; exact search = the nearest
-//      tree position strictly inside the bound, lowest position on ties),
-//      and the flooding run with the device kernel's warp algorithm
-//      (flood_warp.h, lanes one after another), and requires every table,
-//      box code, neighbour list and count to equal the host build's;
+//      certification searches answered by brute force under the same rule
+//      (the nearest tree position strictly inside the bound, lowest
+//      position on ties), the Voronoi cells made by the device kernel's
+//      warp algorithm (cell_warp.h, lanes one after another) with every
+//      seventh cell handed back to the host, and the flooding run with the device kernel's warp
+//      algorithm (flood_warp.h, lanes one after another), and requires
+//      every table, box code, neighbour list and count to equal the host
+//      build's;
 //   3. injects an allocation failure into each build stage and requires
 //      std::bad_alloc to reach the caller.
 // Prints "OK" when every check holds.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -21,6 +24,8 @@
 #include <vector>
 
 #include "builder.h"
+#include "cell_core.h"
+#include "cell_warp.h"
 #include "flood_core.h"
 #include "flood_warp.h"
 
@@ -39,22 +44,74 @@ struct LaneEnv : fc::Flat {
   }
 };
 
+// the KD tree as the device's cell kernel reads it (the layout's float
+// points and child boxes), with the exact search done by brute force
+struct CellEnv {
+  const Layout *L;
+  int64_t nleaf0() const { return ((int64_t)1 << L->kd_depth) - 1; }
+  int64_t leaf_first(int64_t j) const { return (j * L->nv) >> L->kd_depth; }
+  fc::D3 pos(int64_t p) const {
+    return {(double)L->kd_points[4 * p], (double)L->kd_points[4 * p + 1],
+            (double)L->kd_points[4 * p + 2]};
+  }
+  void child_boxes(int64_t node, double b0[6], double b1[6]) const {
+    const float *o = &L->kd_nodes[12 * node];
+    for (int d = 0; d < 6; ++d) {
+      b0[d] = o[d];
+      b1[d] = o[6 + d];
+    }
+  }
+  int64_t within(fc::D3 x, double r2) const {
+    double best = r2;
+    int64_t bi = -1;
+    for (int64_t p = 0; p < L->nv; ++p) {
+      const double d = fc::len2(pos(p) - x);
+      if (d < best) {
+        best = d;
+        bi = p;
+      }
+    }
+    return bi;
+  }
+};
+
 struct StandIn : NearestService {
   const Layout *L = nullptr;
-  bool query(const float *xyz, int64_t n, int32_t *out) override {
-    for (int64_t i = 0; i < n; ++i) {
-      float best = INFINITY;
-      int32_t bi = -1;
-      for (int64_t p = 0; p < L->nv; ++p) {
-        const float dx = xyz[3 * i] - L->kd_points[4 * p], dy = xyz[3 * i + 1] - L->kd_points[4 * p + 1],
-                    dz = xyz[3 * i + 2] - L->kd_points[4 * p + 2];
-        const float d = dx * dx + dy * dy + dz * dz;
-        if (d < best) {
-          best = d;
-          bi = (int32_t)p;
+  bool cells(const CellProblem &pb, CellResult &out) override {
+    CellEnv env{L};
+    cc::CellParams cp;
+    for (int d = 0; d < 3; ++d) {
+      cp.lo[d] = pb.lo[d];
+      cp.hi[d] = pb.hi[d];
+    }
+    cp.eps = pb.eps;
+    cp.epsc = pb.epsc;
+    cp.delta = pb.delta;
+    std::unique_ptr<fw::WarpWork> S(new fw::WarpWork);
+    std::unique_ptr<cw::CellExtra> X(new cw::CellExtra);
+    out = CellResult();
+    out.gave_up.assign(pb.nv, 0);
+    out.nb_off.assign(1, 0);
+    out.pt_off.assign(1, 0);
+    out.beg_off.assign(1, 0);
+    for (int64_t p = 0; p < pb.nv; ++p) {
+      const fw::WPoly *w = nullptr;
+      if (p % 7 == 3 || cw::cell_warp(*S, *X, env, p, cp, w) != cc::kCellOk) {
+        out.gave_up[p] = 1;
+      } else {
+        for (int i = 0; i < w->np; ++i) {
+          out.pt.push_back(w->pt[i].x);
+          out.pt.push_back(w->pt[i].y);
+          out.pt.push_back(w->pt[i].z);
         }
+        for (int f = 0; f <= w->nf; ++f) out.beg.push_back(w->beg[f]);
+        for (int i = 0; i < X->nb_n; ++i) out.nb.push_back(X->nb[i]);
+        out.rounds = std::max<int64_t>(out.rounds, X->rounds);
+        out.queries += X->queries;
       }
-      out[i] = bi;
+      out.pt_off.push_back((int64_t)out.pt.size() / 3);
+      out.beg_off.push_back((int64_t)out.beg.size());
+      out.nb_off.push_back((int64_t)out.nb.size());
     }
     return true;
   }
@@ -114,7 +171,8 @@ bool same(const Layout &A, const Layout &B) {
          A.nb == B.nb && A.nb_off == B.nb_off && A.nbp == B.nbp && A.kd_points == B.kd_points &&
          A.kd_nodes == B.kd_nodes && A.edge_rec == B.edge_rec && A.face_rec == B.face_rec &&
          A.inspections == B.inspections && A.n_entries == B.n_entries &&
-         A.max_list == B.max_list && A.neighbour_pairs == B.neighbour_pairs;
+         A.max_list == B.max_list && A.neighbour_pairs == B.neighbour_pairs &&
+         A.cert_rounds == B.cert_rounds && A.cert_queries == B.cert_queries;
 }
 
 }  // namespace
@@ -155,6 +213,7 @@ int main(int argc, char **argv) {
   StandIn svc;
   BuildParams prm2 = prm;
   prm2.device_flood = true;
+  prm2.device_cells = true;
   Layout dev;
   auto on_tree = [](void *ctx, const Layout &L) {
     ((StandIn *)ctx)->L = &L;
@@ -162,6 +221,8 @@ int main(int argc, char **argv) {
   };
   CHECK(build_layout(V.data(), nv, Fp, nf, Sp, ns, prm2, &svc, on_tree, &svc, dev, err) == 0);
   CHECK(dev.flood_device > 0);
+  CHECK(dev.cells_device > 0 && dev.cells_host > 0);
+  CHECK(host.cells_device == 0 && host.cells_host == nv);
   CHECK(same(host, dev));
 
   for (const char *stage : {"cells", "flooding", "packing"}) {

@@ -127,7 +127,7 @@ def test_flood_stats_on_a_regular_mesh(pg):
 
 def test_device_assist_values(pg):
     V, F = dg.octahedron()
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         with pytest.raises(ValueError):
             pg.P2M(V.astype(np.float32), F, device_assist=bad)
 
@@ -378,23 +378,26 @@ def test_builder_spherical_surface_every_vertex_intercepts_every_face(pg):
 
 
 def test_build_options_and_stats_at_the_c_abi(pg):
-    """Through the C ABI itself: device_assist outside 0..2 is INVALID_ARG,
+    """Through the C ABI itself: device_assist outside 0..3 is INVALID_ARG,
     and the statistics calls reject NULL handles and outputs."""
     V, F = dg.octahedron()
     V = np.ascontiguousarray(V, np.float32)
     F = np.ascontiguousarray(F, np.int32)
     desc = pg.MeshDesc(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
     h = ctypes.c_void_p()
-    for bad in (-1, 3, 7):
+    for bad in (-1, 4, 7):
         opts = pg.BuildOpts(10.0, 0.0, 4e-6, 0, bad, 8)
         assert pg.lib.p2m_build(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)) == 1
     out = (ctypes.c_int64 * 16)()
     assert pg.lib.p2m_flood_stats(None, out) == 1
+    assert pg.lib.p2m_cell_stats(None, out) == 1
     assert pg.lib.p2m_stats(None, out) == 1
     m = _host(pg, dg.workload(0, n_queries=10, level=1))
     assert pg.lib.p2m_flood_stats(m._h, None) == 1
     assert pg.lib.p2m_flood_stats(m._h, out) == 0
     assert list(out[:3]) == [0, m.flood_stats()["host_bounded"], 0]
+    assert pg.lib.p2m_cell_stats(m._h, None) == 1
+    assert m.cell_stats() == {"device": 0, "host": 42}  # every cell of the 42 vertices
 
 
 @pytest.mark.parametrize("stage", ["cells", "flooding", "packing"])

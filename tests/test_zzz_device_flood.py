@@ -2,9 +2,11 @@
 (device_assist=2): each warp floods one primitive at a time with the steps
 of the core the host builder uses, in double precision without fused
 multiply-adds, and hands back the primitives its shared-memory buffers
-cannot hold.  The layout it builds is the host flooding's byte for byte:
-both builds are saved and the files compared (they hold every table, box
-code, neighbour list and the inspection count)."""
+cannot hold.  With device_assist=3 the Voronoi cells are made on the device
+too (one thread per cell, cell_core.h).  The layouts they build are the
+host's byte for byte: the builds are saved and the files compared (they
+hold every table, box code, neighbour list, the inspection count and the
+certification's counts)."""
 import os
 import tempfile
 
@@ -52,13 +54,19 @@ def test_device_flood_builds_the_host_layout(pg, name):
         # the apex's cell does not fit the core's buffers: handed back
         assert fa["host_unbounded"] > 0
     assert a.stats()["inspections"] == b.stats()["inspections"]
+    c = pg.P2M(m.verts, m.tris, device_assist=3, **kw)
+    cs = c.cell_stats()
+    assert cs["device"] > 0 and cs["device"] + cs["host"] == m.verts.shape[0]
+    assert a.cell_stats() == b.cell_stats() == {"device": 0, "host": m.verts.shape[0]}
     with tempfile.TemporaryDirectory() as d:
-        pa, pb = os.path.join(d, "a.p2m"), os.path.join(d, "b.p2m")
+        pa, pb, pc = (os.path.join(d, f"{x}.p2m") for x in "abc")
         a.save(pa)
         b.save(pb)
-        ba, bb = open(pa, "rb").read(), open(pb, "rb").read()
-    assert len(ba) == len(bb)
+        c.save(pc)
+        ba, bb, bc = (open(x, "rb").read() for x in (pa, pb, pc))
+    assert len(ba) == len(bb) == len(bc)
     assert ba == bb
+    assert bc == bb
 
 
 @pytest.mark.parametrize("name", ["sphere-L3", "displaced-L4", "heightfield-40",
