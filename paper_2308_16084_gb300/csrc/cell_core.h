@@ -68,7 +68,7 @@ P2M_HD double box_d2(const double b[6], D3 q) {
 }
 
 // Order-preserving 64-bit key of a double (+0 and -0 share one key, as they
-// compare equal): the corners are sorted and deduplicated on these keys, an
+// compare equal): the corners are ranked and deduplicated on these keys, an
 // integer comparison that gives the order and equality of the doubles.
 P2M_HD uint64_t order_key(double v) {
   uint64_t u;
@@ -87,24 +87,6 @@ P2M_HD bool corner_less(const D3 &a, const D3 &b) {
 
 P2M_HD bool corner_same(const D3 &a, const D3 &b) {
   return a.x == b.x && a.y == b.y && a.z == b.z;
-}
-
-// sorts c[0 .. n) by corner_less (shell sort with Ciura's gaps: equal
-// corners are removed afterwards, so the order among them does not matter)
-P2M_HD void sort_corners(D3 *c, int n) {
-  const int gaps[8] = {701, 301, 132, 57, 23, 10, 4, 1};
-  for (int g = 0; g < 8; ++g) {
-    const int h = gaps[g];
-    for (int i = h; i < n; ++i) {
-      const D3 x = c[i];
-      int j = i;
-      while (j >= h && corner_less(x, c[j - h])) {
-        c[j] = c[j - h];
-        j -= h;
-      }
-      c[j] = x;
-    }
-  }
 }
 
 // The 32 nearest tree positions to q other than self, ascending, with the
