@@ -5,8 +5,8 @@
 //   2. builds it again through a stand-in for the device services: the
 //      certification searches answered by brute force under the same rule
 //      (the nearest tree position strictly inside the bound, lowest
-//      position on ties), the Voronoi cells made by the device kernel's
-//      warp algorithm (cell_warp.h, lanes one after another) with every
+//      position on ties), the Voronoi cells made in the device's rounds by
+//      its warp phases (cell_warp.h, lanes one after another) with every
 //      seventh cell handed back to the host, and the flooding run with the device kernel's warp
 //      algorithm (flood_warp.h, lanes one after another), and requires
 //      every table, box code, neighbour list and count to equal the host
@@ -89,14 +89,52 @@ struct StandIn : NearestService {
     cp.delta = pb.delta;
     std::unique_ptr<fw::WarpWork> S(new fw::WarpWork);
     std::unique_ptr<cw::CellExtra> X(new cw::CellExtra);
+    const int64_t nv = pb.nv;
+    std::vector<cw::CellSlot> slots(nv);
+    // the device's rounds: seeding, then per round every open cell's far
+    // corners, all of them searched, every cell cut by what its corners found
+    for (int64_t p = 0; p < nv; ++p) {
+      if (p % 7 == 3) slots[p].status = cw::kGaveUp;
+      else cw::cell_seed(*S, *X, env, p, cp, slots[p]);
+    }
+    for (int round = 0; round < cc::kRounds; ++round) {
+      std::vector<fc::D3> xs;
+      std::vector<double> rs;
+      for (int64_t p = 0; p < nv; ++p) {
+        cw::CellSlot &c = slots[p];
+        if (c.status != cw::kOpen) continue;
+        const fc::D3 pv = env.pos(p);
+        const int m = cw::round_corners(*X, c, pv);
+        c.m = m;
+        if (m == 0) {
+          c.status = cw::kDone;
+          continue;
+        }
+        c.corner_at = (int64_t)xs.size();
+        c.rounds += 1;
+        c.queries += m;
+        for (int j = 0; j < m; ++j) {
+          xs.push_back(X->corner[j]);
+          rs.push_back(fc::len2(X->corner[j] - pv) - pb.epsc);
+        }
+      }
+      if (xs.empty()) break;
+      std::vector<int64_t> wres(xs.size());
+      for (size_t j = 0; j < xs.size(); ++j) wres[j] = env.within(xs[j], rs[j]);
+      for (int64_t p = 0; p < nv; ++p) {
+        cw::CellSlot &c = slots[p];
+        if (c.status == cw::kOpen && c.m > 0)
+          cw::round_apply(*S, *X, env, p, cp, c, &wres[c.corner_at]);
+      }
+    }
     out = CellResult();
-    out.gave_up.assign(pb.nv, 0);
+    out.gave_up.assign(nv, 0);
     out.nb_off.assign(1, 0);
     out.pt_off.assign(1, 0);
     out.beg_off.assign(1, 0);
-    for (int64_t p = 0; p < pb.nv; ++p) {
+    for (int64_t p = 0; p < nv; ++p) {
       const fw::WPoly *w = nullptr;
-      if (p % 7 == 3 || cw::cell_warp(*S, *X, env, p, cp, w) != cc::kCellOk) {
+      if (slots[p].status == cw::kGaveUp || !cw::cell_widen(*S, *X, env, p, cp, slots[p], w)) {
         out.gave_up[p] = 1;
       } else {
         for (int i = 0; i < w->np; ++i) {
@@ -106,8 +144,8 @@ struct StandIn : NearestService {
         }
         for (int f = 0; f <= w->nf; ++f) out.beg.push_back(w->beg[f]);
         for (int i = 0; i < X->nb_n; ++i) out.nb.push_back(X->nb[i]);
-        out.rounds = std::max<int64_t>(out.rounds, X->rounds);
-        out.queries += X->queries;
+        out.rounds = std::max<int64_t>(out.rounds, slots[p].rounds);
+        out.queries += slots[p].queries;
       }
       out.pt_off.push_back((int64_t)out.pt.size() / 3);
       out.beg_off.push_back((int64_t)out.beg.size());
