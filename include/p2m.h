@@ -81,10 +81,9 @@ typedef struct {
                           thread per cell), 0 = CPU only.  The GPU steps are the host's
                           double-precision steps without fused multiply-adds; what
                           their buffers cannot hold is handed back to the host.
-                          Every setting gives the same layout bit for bit (default 2,
-                          the fastest build on a GB300: its FP64 rate makes the cell
-                          stage slower there than on the host's cores; without a GPU
-                          every setting builds on the host)                            */
+                          Every setting gives the same layout bit for bit (default 3,
+                          the fastest build on a GB300; without a GPU every setting
+                          builds on the host)                                          */
   int leaf_size;       /* KD-tree bucket size, 2..32 (default 8)                            */
 } p2m_build_opts;
 
@@ -433,7 +432,7 @@ p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges);
 p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]);
 
 /* How the flooding of a handle's build was split: out[0] = primitives
- * flooded on the device (device_assist = 2), out[1] = flooded on the host by
+ * flooded on the device (device_assist 2 or 3), out[1] = flooded on the host by
  * the bounded core shared with the device, out[2] = flooded on the host by
  * the unbounded code (primitives whose polytopes exceed the core's fixed
  * buffers, or whose cap loop needs the angular ordering).  All zero for a

@@ -73,15 +73,15 @@ class P2M:
     """A preprocessed mesh on the current CUDA device.
 
     ``P2M(verts, tris, domain_scale=10, domain_margin=0, delta_rel=4e-6,
-    host_threads=0, device_assist=2, leaf_size=8)`` runs the paper's
+    host_threads=0, device_assist=3, leaf_size=8)`` runs the paper's
     preprocessing (Alg. A.1) through ``p2m_build``.  ``verts`` (V,3) float32
     and ``tris`` (F,3) int32 may be numpy arrays or CPU tensors.
     ``device_assist``: False/0 host only, True/1 Voronoi-cell certification
-    on the GPU, 2 (default) the flooding (Alg. 1) on the GPU as well, 3 the
+    on the GPU, 2 the flooding (Alg. 1) on the GPU as well, 3 (default) the
     whole Voronoi-cell stage too; every setting gives the same layout."""
 
     def __init__(self, verts=None, tris=None, *, segs=None, domain_scale=10.0,
-                 domain_margin=0.0, delta_rel=4e-6, host_threads=0, device_assist=2,
+                 domain_margin=0.0, delta_rel=4e-6, host_threads=0, device_assist=3,
                  leaf_size=8, _handle=None):
         self._h = None
         if _handle is not None:

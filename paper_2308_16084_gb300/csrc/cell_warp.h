@@ -40,6 +40,8 @@ using fc::len2;
 
 enum { kOpen = 0, kDone = 1, kGaveUp = 2 };
 
+constexpr int kSettled = 192;  // settled corners a cell remembers
+
 // one cell's state between the phases
 struct CellSlot {
   fw::WPoly poly;                  // the cell so far
@@ -51,6 +53,11 @@ struct CellSlot {
   int64_t corner_at;               // where they are in the round's search list
   int64_t queries;                 // far corners searched over all rounds
   double safe2;                    // corners nearer than this need no search
+  // far corners whose search found no vertex, or only one already applied:
+  // the same corner (bit for bit) gets the same answer in a later round, so
+  // it is not searched again
+  D3 settled[kSettled];
+  int n_settled;
 };
 
 // per-warp work space besides the cut's (fw::WarpWork)
@@ -117,6 +124,7 @@ P2M_HD void cell_seed(fw::WarpWork &S, CellExtra &X, const Env &env, int64_t p,
     c.rounds = 0;
     c.queries = 0;
     c.m = 0;
+    c.n_settled = 0;
   }
   P2M_SYNC;
   const int k = X.k;
@@ -186,13 +194,51 @@ P2M_HD int round_corners(CellExtra &X, const CellSlot &c, D3 pv) {
   return X.m;
 }
 
-// After the round's searches (wres[i]: the answer for the cell's i-th far
-// corner, -2 where the search gave up): the vertices found that were not
-// applied yet, first found first, then nearest first, cut into the cell.
-// No vertex found: the cell is done.
+// bit-for-bit equality (a miss only costs a search)
+P2M_HD bool same_bits(const D3 &a, const D3 &b) {
+  uint64_t u[3], v[3];
+  memcpy(u, &a, 24);
+  memcpy(v, &b, 24);
+  return u[0] == v[0] && u[1] == v[1] && u[2] == v[2];
+}
+
+// Of the round's far corners X.corner[0 .. m), the ones the cell has not
+// settled in an earlier round, in order, into X.sorted[0 .. ms); returns ms.
+P2M_HD int round_unsettled(CellExtra &X, const CellSlot &c, int m) {
+  const int ns = c.n_settled;
+  P2M_LANES(l)
+    for (int j = l; j < m; j += 32) {
+      const D3 x = X.corner[j];
+      int known = 0;
+      for (int t = 0; t < ns && !known; ++t) known = same_bits(x, c.settled[t]) ? 1 : 0;
+      X.keep[j] = 1 - known;
+    }
+  P2M_END_LANES
+  P2M_LANE0 {
+    int ms = 0;
+    for (int j = 0; j < m; ++j) {
+      X.rank[j] = ms;
+      ms += X.keep[j];
+    }
+    X.m = ms;
+  }
+  P2M_SYNC;
+  P2M_LANES(l)
+    for (int j = l; j < m; j += 32)
+      if (X.keep[j]) X.sorted[X.rank[j]] = X.corner[j];
+  P2M_END_LANES
+  return X.m;
+}
+
+// After the round's searches (the cell's c.m searched corners xs[3i ..],
+// wres[i] the answer for each, -2 where the search gave up): the vertices
+// found that were not applied yet, first found first, then nearest first,
+// cut into the cell; the corners that found none remembered as settled.  No
+// vertex found: the cell is done.
 template <class Env>
 P2M_HD void round_apply(fw::WarpWork &S, CellExtra &X, const Env &env, int64_t p,
-                        const cc::CellParams &cp, CellSlot &c, const int64_t *wres) {
+                        const cc::CellParams &cp, CellSlot &c, const double *xs,
+                        const int64_t *wres) {
   const D3 pv = env.pos(p);
   P2M_LANE0 {
     int flag = 0, nc = 0;
@@ -202,12 +248,14 @@ P2M_HD void round_apply(fw::WarpWork &S, CellExtra &X, const Env &env, int64_t p
         flag = 1;
         break;
       }
-      if (w >= 0 && w != p && !cc::has_row(c.applied, c.n_applied, (int32_t)w) &&
-          !cc::has_row(X.cand, nc, (int32_t)w)) {
+      const bool applied = w >= 0 && cc::has_row(c.applied, c.n_applied, (int32_t)w);
+      if (w >= 0 && w != p && !applied && !cc::has_row(X.cand, nc, (int32_t)w)) {
         X.cand[nc] = (int32_t)w;
         X.cand_d[nc] = len2(env.pos(w) - pv);
         ++nc;
       }
+      if ((w == -1 || applied) && c.n_settled < kSettled)
+        c.settled[c.n_settled++] = {xs[3 * i], xs[3 * i + 1], xs[3 * i + 2]};
     }
     for (int i = 1; i < nc; ++i) {
       const int32_t w = X.cand[i];

@@ -4,7 +4,8 @@
 // The cells are made a chunk at a time; each cell keeps its state in device
 // memory (cw::CellSlot).  A seeding kernel makes every cell of the chunk from
 // the box and its 32 nearest vertices; then each round a corner kernel lists
-// every open cell's far corners in one search list (atomic offsets), the
+// every open cell's far corners not settled in an earlier round in one
+// search list (atomic offsets), the
 // batched exact search (certify.cu, full occupancy) answers all of them,
 // and an apply kernel cuts every cell by the vertices its corners found; a
 // widening kernel finally writes the neighbours and the widened cells,
@@ -21,6 +22,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstdint>
+#include <thread>
 #include <vector>
 
 #include "cell_core.h"
@@ -116,22 +118,26 @@ __global__ void __launch_bounds__(kCellWarps * 32, 1)
     if (c.status != cw::kOpen) continue;
     const fc::D3 pv = env.pos(ch.c0 + i);
     const int m = cw::round_corners(X, c, pv);
+    // the far corners not settled in an earlier round go to the search
+    const int ms = m > 0 ? cw::round_unsettled(X, c, m) : 0;
     P2M_LANE0 {
       X.flag = 0;
       c.m = 0;
-      if (m == 0) {
-        c.status = cw::kDone;
+      if (m > 0) {
+        c.rounds += 1;
+        c.queries += m;
+      }
+      if (ms == 0) {
+        c.status = cw::kDone;  // no far corner, or every one settled
       } else {
-        const unsigned long long at = atomicAdd(sl.used, (unsigned long long)m);
+        const unsigned long long at = atomicAdd(sl.used, (unsigned long long)ms);
         X.out_at[0] = at;
-        if (at + m > sl.cap) {
+        if (at + ms > sl.cap) {
           c.status = cw::kGaveUp;  // no room left: the host makes this cell
           X.flag = at < sl.cap ? 2 : 0;
         } else {
           c.corner_at = (int64_t)at;
-          c.m = m;
-          c.rounds += 1;
-          c.queries += m;
+          c.m = ms;
           X.flag = 1;
         }
       }
@@ -140,8 +146,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 1)
     const unsigned long long at = X.out_at[0];
     if (X.flag == 1) {
       P2M_LANES(l)
-        for (int j = l; j < m; j += 32) {
-          const fc::D3 x = X.corner[j];
+        for (int j = l; j < ms; j += 32) {
+          const fc::D3 x = X.sorted[j];
           sl.xs[3 * (at + j)] = x.x;
           sl.xs[3 * (at + j) + 1] = x.y;
           sl.xs[3 * (at + j) + 2] = x.z;
@@ -164,12 +170,13 @@ __global__ void __launch_bounds__(kCellWarps * 32, 1)
 
 // every cell with far corners cut by the vertices they found
 __global__ void __launch_bounds__(kCellWarps * 32, 1)
-    k_cell_apply(CellEnv env, cc::CellParams cp, Chunk ch, const int64_t *__restrict__ wres) {
+    k_cell_apply(CellEnv env, cc::CellParams cp, Chunk ch, const double *__restrict__ xs,
+                 const int64_t *__restrict__ wres) {
   CELL_WARP_SETUP
   for (int64_t i; (i = next_cell(S, ch)) >= 0;) {
     cw::CellSlot &c = ch.slots[i];
     if (c.status != cw::kOpen || c.m == 0) continue;
-    cw::round_apply(S, X, env, ch.c0 + i, cp, c, wres + c.corner_at);
+    cw::round_apply(S, X, env, ch.c0 + i, cp, c, xs + 3 * c.corner_at, wres + c.corner_at);
   }
 }
 
@@ -319,7 +326,7 @@ bool cells_on_device(const DevView &m, const CellProblem &pb, CellResult &out) {
       if (e == cudaSuccess && trace) e = cudaDeviceSynchronize();
       t_search += ms() - ts;
       reset();
-      if (e == cudaSuccess) k_cell_apply<<<grid, threads, smem>>>(env, cp, ch, sl.wres);
+      if (e == cudaSuccess) k_cell_apply<<<grid, threads, smem>>>(env, cp, ch, sl.xs, sl.wres);
       if (e == cudaSuccess) e = cudaGetLastError();
     }
     reset();
@@ -373,19 +380,28 @@ bool cells_on_device(const DevView &m, const CellProblem &pb, CellResult &out) {
   out.pt.resize(3 * (size_t)out.pt_off[nv]);
   out.beg.resize((size_t)out.beg_off[nv]);
   out.nb.resize((size_t)out.nb_off[nv]);
-  for (int64_t p = 0; p < nv; ++p) {
-    if (out.gave_up[p]) continue;
-    const int64_t *r = &info[6 * (size_t)p];
-    for (int64_t i = 0; i < r[1]; ++i) {
-      const fc::D3 x = pt[(size_t)(r[0] + i)];
-      double *d = &out.pt[3 * (size_t)(out.pt_off[p] + i)];
-      d[0] = x.x;
-      d[1] = x.y;
-      d[2] = x.z;
+  // the rows' copies are independent: spread them over the host's cores
+  auto gather = [&](int64_t p0, int64_t p1) {
+    for (int64_t p = p0; p < p1; ++p) {
+      if (out.gave_up[p]) continue;
+      const int64_t *r = &info[6 * (size_t)p];
+      for (int64_t i = 0; i < r[1]; ++i) {
+        const fc::D3 x = pt[(size_t)(r[0] + i)];
+        double *d = &out.pt[3 * (size_t)(out.pt_off[p] + i)];
+        d[0] = x.x;
+        d[1] = x.y;
+        d[2] = x.z;
+      }
+      std::copy(beg.begin() + r[2], beg.begin() + r[2] + r[3], out.beg.begin() + out.beg_off[p]);
+      std::copy(nb.begin() + r[4], nb.begin() + r[4] + r[5], out.nb.begin() + out.nb_off[p]);
     }
-    std::copy(beg.begin() + r[2], beg.begin() + r[2] + r[3], out.beg.begin() + out.beg_off[p]);
-    std::copy(nb.begin() + r[4], nb.begin() + r[4] + r[5], out.nb.begin() + out.nb_off[p]);
-  }
+  };
+  const int64_t nthreads =
+      std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), nv / 4096));
+  std::vector<std::thread> pool;
+  for (int64_t t = 0; t < nthreads; ++t)
+    pool.emplace_back(gather, nv * t / nthreads, nv * (t + 1) / nthreads);
+  for (auto &th : pool) th.join();
   if (trace)
     std::fprintf(stderr,
                  "p2m build:   device cells: %.0f ms on the device (searches %.0f ms), gather "

@@ -327,7 +327,7 @@ void p2m_default_opts(p2m_build_opts *o) {
   o->domain_margin = 0.f;
   o->delta_rel = 4e-6f;
   o->host_threads = 0;
-  o->device_assist = 2;
+  o->device_assist = 3;
   o->leaf_size = 8;
 }
 

@@ -98,33 +98,45 @@ struct StandIn : NearestService {
       else cw::cell_seed(*S, *X, env, p, cp, slots[p]);
     }
     for (int round = 0; round < cc::kRounds; ++round) {
-      std::vector<fc::D3> xs;
-      std::vector<double> rs;
+      std::vector<double> xs, rs;
       for (int64_t p = 0; p < nv; ++p) {
         cw::CellSlot &c = slots[p];
         if (c.status != cw::kOpen) continue;
         const fc::D3 pv = env.pos(p);
         const int m = cw::round_corners(*X, c, pv);
-        c.m = m;
-        if (m == 0) {
+        const int ms = m > 0 ? cw::round_unsettled(*X, c, m) : 0;
+        c.m = 0;
+        if (m > 0) {
+          c.rounds += 1;
+          c.queries += m;
+        }
+        if (ms == 0) {
           c.status = cw::kDone;
           continue;
         }
-        c.corner_at = (int64_t)xs.size();
-        c.rounds += 1;
-        c.queries += m;
-        for (int j = 0; j < m; ++j) {
-          xs.push_back(X->corner[j]);
-          rs.push_back(fc::len2(X->corner[j] - pv) - pb.epsc);
+        c.m = ms;
+        c.corner_at = (int64_t)rs.size();
+        for (int j = 0; j < ms; ++j) {
+          const fc::D3 x = X->sorted[j];
+          xs.push_back(x.x);
+          xs.push_back(x.y);
+          xs.push_back(x.z);
+          rs.push_back(fc::len2(x - pv) - pb.epsc);
         }
       }
-      if (xs.empty()) break;
-      std::vector<int64_t> wres(xs.size());
-      for (size_t j = 0; j < xs.size(); ++j) wres[j] = env.within(xs[j], rs[j]);
+      if (rs.empty()) {
+        bool open = false;
+        for (const auto &c : slots) open |= c.status == cw::kOpen;
+        if (!open) break;
+        continue;
+      }
+      std::vector<int64_t> wres(rs.size());
+      for (size_t j = 0; j < rs.size(); ++j)
+        wres[j] = env.within({xs[3 * j], xs[3 * j + 1], xs[3 * j + 2]}, rs[j]);
       for (int64_t p = 0; p < nv; ++p) {
         cw::CellSlot &c = slots[p];
         if (c.status == cw::kOpen && c.m > 0)
-          cw::round_apply(*S, *X, env, p, cp, c, &wres[c.corner_at]);
+          cw::round_apply(*S, *X, env, p, cp, c, &xs[3 * c.corner_at], &wres[c.corner_at]);
       }
     }
     out = CellResult();

@@ -32,7 +32,7 @@ int main(int argc, char **argv) {
   mesh.tris = F;
   mesh.n_tris = 8;
   p2m_default_opts(&opts);
-  CHECK(opts.device_assist == 2 && opts.domain_scale == 10.f);
+  CHECK(opts.device_assist == 3 && opts.domain_scale == 10.f);
   opts.device_assist = 0;
   CHECK(p2m_build(&mesh, &opts, &h) == P2M_OK && h != NULL);
   CHECK(p2m_stats(h, st) == P2M_OK);

@@ -338,8 +338,8 @@ def test_device_flooding_algorithm_on_the_host_builds_the_same_layout(pg, name, 
 
 
 def test_device_flooding_requested_without_a_gpu(pg):
-    """device_assist=2 on a machine without a GPU builds on the host (the
-    same layout), and a loaded handle reports no flooding split."""
+    """device_assist=2 and 3 on a machine without a GPU build on the host
+    (the same layout), and a loaded handle reports no flooding split."""
     import torch
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
@@ -349,6 +349,10 @@ def test_device_flooding_requested_without_a_gpu(pg):
     b = _host(pg, m)
     assert a.flood_stats() == b.flood_stats()
     assert a.flood_stats()["device"] == 0
+    c = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
+               device_assist=3)
+    assert c.cell_stats() == {"device": 0, "host": m.verts.shape[0]}
+    assert c.flood_stats() == b.flood_stats()
     with tempfile.TemporaryDirectory() as d:
         pa, pb = os.path.join(d, "a.p2m"), os.path.join(d, "b.p2m")
         a.save(pa)
