@@ -24,6 +24,8 @@
 // which runs the same arithmetic serially.
 #pragma once
 
+#include <cstring>
+
 #include "flood_core.h"
 
 #if defined(__CUDA_ARCH__)
@@ -203,53 +205,83 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
       out.src[S.frank[f]] = in.src ? in.src[f] : -1;
     }
   P2M_END_LANES
-  // the cap loop, chained by lane 0 (segments in face order, as the serial
-  // core keeps them)
-  P2M_LANE0 {
-    int nf = S.cnt_nf, np = S.cnt_np;
-    out.beg[nf] = np;
-    int ok = 1;
-    if (m >= 3) {
-      int first = 0;
-      while (!S.fseg[first]) ++first;
-      out.pt[np++] = S.seg_in[first];
-      D3 cur = S.seg_out[first];
+  // the cap loop, chained from segment to segment (segments in face order,
+  // as the serial core keeps them): each step takes the first unused
+  // segment whose entry point is nearest to the current point.  The lanes
+  // compute the distances, one segment each; the first minimum is found on
+  // integer keys (a non-negative double's bits order like its value), so
+  // the choice is the serial loop's.
+  int nf = S.cnt_nf, np = S.cnt_np;
+  P2M_LANE0 { out.beg[nf] = np; }
+  int ok = 1;
+  if (m >= 3) {
+    int first = 0;
+    while (!S.fseg[first]) ++first;
+    P2M_LANE0 {
+      out.pt[np] = S.seg_in[first];
       S.fseg[first] = 2;
-      for (int step = 1; step < m && ok; ++step) {
-        out.pt[np++] = cur;
-        int best = -1;
-        double bd = INFINITY;
-        for (int f = 0; f < in.nf; ++f)
+    }
+    ++np;
+    D3 cur = S.seg_out[first];
+    for (int step = 1; step < m && ok; ++step) {
+      P2M_LANE0 { out.pt[np] = cur; }
+      ++np;
+      P2M_LANES(l)
+        uint64_t bk = ~0ull;
+        int bf = -1;
+        for (int f = l; f < in.nf; f += 32)
           if (S.fseg[f] == 1) {
             const double d = len2(S.seg_in[f] - cur);
-            if (d < bd) {
-              bd = d;
-              best = f;
+            uint64_t key;
+            memcpy(&key, &d, 8);
+            if (key < bk) {
+              bk = key;
+              bf = f;
             }
           }
-        if (best < 0 || bd > 1e6 * eps * eps) {
-          ok = 0;
-        } else {
-          S.fseg[best] = 2;
-          cur = S.seg_out[best];
+        memcpy(&S.red_d[l][0], &bk, 8);
+        S.red_i[l] = bf;
+      P2M_END_LANES
+      uint64_t bk = ~0ull;
+      int best = -1;
+      for (int t = 0; t < 32; ++t) {
+        uint64_t key;
+        memcpy(&key, &S.red_d[t][0], 8);
+        const int f = S.red_i[t];
+        if (f >= 0 && (key < bk || (key == bk && f < best))) {
+          bk = key;
+          best = f;
         }
       }
-      if (ok && !(len2(cur - S.seg_in[first]) <= 1e6 * eps * eps)) ok = 0;
-      if (ok) {
-        out.src[nf] = hsrc;
-        out.beg[++nf] = np;
+      double bd;
+      memcpy(&bd, &bk, 8);
+      if (best < 0 || bd > 1e6 * eps * eps) {
+        ok = 0;
+      } else {
+        P2M_LANE0 { S.fseg[best] = 2; }
+        cur = S.seg_out[best];
       }
+      P2M_SYNC;
     }
-    if (nf < 4) {
-      nf = 0;
-      np = 0;
+    if (ok && !(len2(cur - S.seg_in[first]) <= 1e6 * eps * eps)) ok = 0;
+    if (ok) {
+      P2M_LANE0 {
+        out.src[nf] = hsrc;
+        out.beg[nf + 1] = np;
+      }
+      ++nf;
     }
+  }
+  if (nf < 4) {
+    nf = 0;
+    np = 0;
+  }
+  P2M_LANE0 {
     out.nf = nf;
     out.np = np;
-    S.flag = ok ? 0 : 1;
   }
   P2M_SYNC;
-  return S.flag ? kGiveUp : kDone;
+  return ok ? kDone : kGiveUp;
 }
 
 // minimum / maximum of the lanes' box candidates, one column per lane
