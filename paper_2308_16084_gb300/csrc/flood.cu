@@ -48,9 +48,13 @@ struct DevEnv : fc::Flat {
 
 __global__ void __launch_bounds__(kFloodWarps * 32, 1)
     k_flood_warp(DevEnv env, int64_t n, double eps, double delta, double eta, uint8_t *gave_up,
-                 unsigned long long *insp_total, unsigned long long *next) {
+                 unsigned long long *insp_total, unsigned long long *next, int32_t *seen,
+                 int64_t nv) {
   extern __shared__ __align__(16) unsigned char flood_smem[];
   fw::WarpWork &S = reinterpret_cast<fw::WarpWork *>(flood_smem)[threadIdx.x >> 5];
+  // this warp's row stamps (null: the queue is scanned instead)
+  int32_t *my_seen =
+      seen ? seen + ((int64_t)blockIdx.x * kFloodWarps + (threadIdx.x >> 5)) * nv : nullptr;
   DevEnv e = env;
   for (;;) {
     P2M_LANE0 { S.item = (int64_t)atomicAdd(next, 1ull); }
@@ -59,7 +63,7 @@ __global__ void __launch_bounds__(kFloodWarps * 32, 1)
     P2M_SYNC;
     if (k >= n) return;
     int64_t insp = 0;
-    const int r = fw::flood_warp(S, e, k, eps, delta, eta, insp);
+    const int r = fw::flood_warp(S, e, k, eps, delta, eta, insp, my_seen);
     P2M_LANE0 {
       gave_up[k] = (uint8_t)(r != 0);
       if (r == 0) atomicAdd(insp_total, (unsigned long long)insp);
@@ -140,17 +144,31 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     // set of a run is deterministic)
     unsigned long long cap = (unsigned long long)std::max<int64_t>(1 << 20, 64 * n);
     unsigned long long h_cnt[2] = {0, 0};
+    // one row stamp per warp and row (4 bytes each: 3.2 GB for the 655k rows of
+    // the 1.3M-triangle mesh), when that fits in 8 GB; else the warps scan
+    // their queues
+    int32_t *seen = nullptr;
+    const size_t seen_bytes = sizeof(int32_t) * (size_t)sms * kFloodWarps * (size_t)nv;
+    if (e == cudaSuccess && seen_bytes <= ((size_t)8 << 30)) {
+      if (cudaMalloc((void **)&seen, seen_bytes) == cudaSuccess) {
+        B.p.push_back(seen);
+      } else {
+        cudaGetLastError();
+        seen = nullptr;
+      }
+    }
     for (int attempt = 0; attempt < 2 && e == cudaSuccess; ++attempt) {
       FloodRec *drec = B.get<FloodRec>((size_t)cap, e);
       if (e != cudaSuccess) break;
       e = cudaMemset(cnt, 0, 3 * sizeof(unsigned long long));
+      if (e == cudaSuccess && seen) e = cudaMemset(seen, 0, seen_bytes);
       if (e != cudaSuccess) break;
       env.rec = drec;
       env.count = cnt;
       env.cap = cap;
       t1 = ms();
       k_flood_warp<<<sms, kFloodWarps * 32, smem>>>(env, n, pb.eps, pb.delta, pb.eta, dgave,
-                                                     cnt + 1, cnt + 2);
+                                                     cnt + 1, cnt + 2, seen, nv);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaDeviceSynchronize();
       t2 = ms();

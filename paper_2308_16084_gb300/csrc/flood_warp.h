@@ -84,6 +84,7 @@ struct WarpWork {
   D3 seg_in[kWF], seg_out[kWF];  // per face: its cap segment (Y -> X)
   int32_t fcnt[kWF], foff[kWF], frank[kWF];
   uint8_t fseg[kWF];      // 1: face has a cap segment (2 once chained)
+  uint8_t fone[kWF];      // 1: face's loop leaves and enters the kept side at most once
   int32_t red_i[32];
   double red_d[32][6];    // per-lane box candidates (lo xyz, hi xyz)
   double box[6];          // their minimum / maximum
@@ -129,7 +130,7 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
   P2M_LANES(l)
     for (int f = l; f < in.nf; f += 32) {
       const int b = in.beg[f], k = in.beg[f + 1] - b;
-      int cnt = 0;
+      int cnt = 0, turns = 0;
       bool has_x = false, has_y = false;
       D3 X{0, 0, 0}, Y{0, 0, 0};
       for (int i = 0; i < k; ++i) {
@@ -137,6 +138,7 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
         const double sa = S.s[ia], sb = S.s[ib];
         const bool ka = sa <= eps, kb = sb <= eps;
         if (ka) ++cnt;
+        turns += ka != kb;
         if (ka && !kb) {
           if (sa >= -eps) {
             X = in.pt[ia];
@@ -158,10 +160,11 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
       S.fcnt[f] = cnt >= 3 ? cnt : 0;
       const bool hs = has_x && has_y && len2(X - Y) > eps * eps;
       S.fseg[f] = hs ? 1 : 0;
-      if (hs) {
-        S.seg_in[f] = Y;
-        S.seg_out[f] = X;
-      }
+      // the exit and entry points, kept for pass 2 when the loop crosses
+      // once each way (then pass 2's crossings are these)
+      S.fone[f] = turns <= 2 ? 1 : 0;
+      S.seg_in[f] = Y;
+      S.seg_out[f] = X;
     }
   P2M_END_LANES
   // placement of the kept faces, in face order
@@ -190,15 +193,18 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
       if (S.fcnt[f] == 0) continue;
       const int b = in.beg[f], k = in.beg[f + 1] - b;
       int o = S.foff[f];
+      const bool one = S.fone[f] != 0;
       for (int i = 0; i < k; ++i) {
         const int ia = b + i, ib = b + (i + 1) % k;
         const double sa = S.s[ia], sb = S.s[ib];
         const bool ka = sa <= eps, kb = sb <= eps;
         if (ka) out.pt[o++] = in.pt[ia];
         if (ka && !kb) {
-          if (!(sa >= -eps)) out.pt[o++] = fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
+          if (!(sa >= -eps))
+            out.pt[o++] = one ? S.seg_out[f] : fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
         } else if (!ka && kb) {
-          if (!(sb >= -eps)) out.pt[o++] = fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
+          if (!(sb >= -eps))
+            out.pt[o++] = one ? S.seg_in[f] : fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
         }
       }
       out.beg[S.frank[f]] = S.foff[f];
@@ -298,19 +304,25 @@ P2M_HD void reduce_box(WarpWork &S) {
 }
 
 // Flood primitive k of the flat problem with the warp.  Env: fc::Flat's
-// accessors and emit(row, tid, box).  Returns 0 when done (insp = vertices
-// inspected), 1 when given up (records already emitted for it must be
-// dropped).
+// accessors and emit(row, tid, box).  seen: null, or the warp's array of one
+// stamp per row (zero at first), which then marks the rows queued for k
+// (stamp k + 1) instead of a scan of the queue.  Returns 0 when done (insp =
+// vertices inspected), 1 when given up (records already emitted for it must
+// be dropped).
 template <class Env>
 P2M_HD int flood_warp(WarpWork &S, Env &env, int64_t k, double eps, double delta, double eta,
-                      int64_t &insp) {
+                      int64_t &insp, int32_t *seen = nullptr) {
+  const int32_t stamp = (int32_t)(k + 1);
   insp = 0;
   P2M_LANE0 { S.flag = env.load(k, S.P) ? 0 : 1; }
   P2M_SYNC;
   if (S.flag) return 1;
   const fc::Prim &P = S.P;
   P2M_LANE0 {
-    for (int s = 0; s < P.ns; ++s) S.queue[s] = P.seed_row[s];
+    for (int s = 0; s < P.ns; ++s) {
+      S.queue[s] = P.seed_row[s];
+      if (seen) seen[P.seed_row[s]] = stamp;
+    }
     S.head = 0;
     S.tail = P.ns;
   }
@@ -463,11 +475,15 @@ P2M_HD int flood_warp(WarpWork &S, Env &env, int64_t k, double eps, double delta
         if (base + l < nb1) {
           const int32_t w = env.nb(base + l);
           isnew = 1;
-          for (int64_t q = 0; q < tail0; ++q)
-            if (S.queue[q] == w) {
-              isnew = 0;
-              break;
-            }
+          if (seen) {
+            isnew = seen[w] != stamp;
+          } else {
+            for (int64_t q = 0; q < tail0; ++q)
+              if (S.queue[q] == w) {
+                isnew = 0;
+                break;
+              }
+          }
         }
         S.red_i[l] = isnew;
       P2M_END_LANES
@@ -478,7 +494,9 @@ P2M_HD int flood_warp(WarpWork &S, Env &env, int64_t k, double eps, double delta
             if (S.tail >= kWQ) {
               S.flag = 1;
             } else {
-              S.queue[S.tail++] = env.nb(base + l);
+              const int32_t w = env.nb(base + l);
+              S.queue[S.tail++] = w;
+              if (seen) seen[w] = stamp;
             }
           }
       }

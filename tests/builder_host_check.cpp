@@ -8,7 +8,8 @@
 //      position on ties), the Voronoi cells made in the device's rounds by
 //      its warp phases (cell_warp.h, lanes one after another) with every
 //      seventh cell handed back to the host, and the flooding run with the device kernel's warp
-//      algorithm (flood_warp.h, lanes one after another), and requires
+//      algorithm (flood_warp.h, lanes one after another, row stamps as on
+//      the device), and requires
 //      every table, box code, neighbour list and count to equal the host
 //      build's;
 //   3. injects an allocation failure into each build stage and requires
@@ -205,9 +206,10 @@ struct StandIn : NearestService {
     gave_up.assign(pb.n, 0);
     inspections = 0;
     std::unique_ptr<fw::WarpWork> S(new fw::WarpWork);
+    std::vector<int32_t> seen(pb.nv, 0);  // the device's row stamps
     for (int64_t i = pb.n - 1; i >= 0; --i) {  // any order: the host sorts
       int64_t k = 0;
-      const int r = fw::flood_warp(*S, env, i, pb.eps, pb.delta, pb.eta, k);
+      const int r = fw::flood_warp(*S, env, i, pb.eps, pb.delta, pb.eta, k, seen.data());
       gave_up[i] = r != 0;  // records of a given-up primitive stay in: the host drops them
       if (r == 0) inspections += k;
     }
