@@ -57,11 +57,13 @@ P2M_HD double dmax(double a, double b) { return a < b ? b : a; }
 // 0 <= t <= 1, whose end values g(x0), g(x1) lie on opposite sides of zero
 // (pos0: g(x0) > 0).  Along the edge the filter is the quadratic
 // p(t) = (A t + B) t + C with A >= 0 (its Hessian is positive semidefinite),
-// so the sign change brackets exactly one root.  The root is enclosed by a
-// regula falsi iteration that keeps the bracket, with the Illinois rule (the
-// retained end's value is halved when the same end is kept twice), until
-// the bracket is 2^-40 of the edge or 64 steps have passed; [*ta, *tb]
-// receives it.  The caller adds the points at both ends of the bracket to
+// so the sign change brackets exactly one root.  The root's closed form
+// (the quadratic formula in its stable form) is tried first: a bracket 2^-40
+// of the edge wide around it is taken when p has the end values' signs at
+// its ends.  Otherwise the root is enclosed by a regula falsi iteration that
+// keeps the bracket, with the Illinois rule (the retained end's value is
+// halved when the same end is kept twice), until the bracket is 2^-40 of
+// the edge or 64 steps have passed.  [*ta, *tb] receives the bracket.  The caller adds the points at both ends of the bracket to
 // the Region box: their box contains the segment between them, hence the
 // crossing, whatever the rounding of p.  If p disagrees with the end values
 // at an end (rounding at a crossing that close to it) that end is returned
@@ -77,6 +79,37 @@ P2M_HD void edge_crossing(double A, double B, double C, bool pos0, double *ta, d
   if (fhi > 0.0) {
     *ta = *tb = 1.0;
     return;
+  }
+  // The root from the quadratic formula in its stable form (the larger-
+  // magnitude root as q / A, the other as C / q), bracketed 2^-40 wide and
+  // accepted when the signs of p at the bracket's ends confirm it; where they
+  // do not (rounding near a double root, say) the iteration below runs.
+  {
+    double t = -1.0;
+    if (A == 0.0) {
+      if (B != 0.0) t = -C / B;
+    } else {
+      const double disc = B * B - 4.0 * A * C;
+      if (disc >= 0.0) {
+        const double sq = sqrt(disc);
+        const double q = -0.5 * (B >= 0.0 ? B + sq : B - sq);
+        if (q != 0.0) {
+          const double r1 = q / A, r2 = C / q;
+          t = (r1 > 0.0 && r1 < 1.0) ? r1 : r2;
+        }
+      }
+    }
+    if (t > 0.0 && t < 1.0) {
+      double a = t - 0x1p-41, b = t + 0x1p-41;
+      if (!(a > 0.0)) a = 0.0;
+      if (!(b < 1.0)) b = 1.0;
+      const double fa = sg * ((A * a + B) * a + C), fb = sg * ((A * b + B) * b + C);
+      if (fa > 0.0 && !(fb > 0.0)) {
+        *ta = a;
+        *tb = b;
+        return;
+      }
+    }
   }
   int kept = 0;  // +1: lo moved last, -1: hi moved last
   for (int it = 0; it < 64 && hi - lo > 0x1p-40; ++it) {
