@@ -67,16 +67,10 @@ P2M_HD double box_d2(const double b[6], D3 q) {
   return dx * dx + dy * dy + dz * dz;
 }
 
-// Order-preserving 64-bit key of a double (+0 and -0 share one key, as they
-// compare equal): the corners are ranked and deduplicated on these keys, an
-// integer comparison that gives the order and equality of the doubles.
-P2M_HD uint64_t order_key(double v) {
-  uint64_t u;
-  memcpy(&u, &v, 8);
-  if (u == 0x8000000000000000ull) u = 0;
-  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-}
+using fc::order_key;
 
+// corners are ranked and deduplicated on order_key: the integer comparison
+// gives the order and equality of the doubles
 P2M_HD bool corner_less(const D3 &a, const D3 &b) {
   const uint64_t ax = order_key(a.x), bx = order_key(b.x);
   if (ax != bx) return ax < bx;

@@ -23,6 +23,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #if defined(__CUDACC__)
 #define P2M_HD __host__ __device__ __forceinline__
@@ -49,9 +50,21 @@ P2M_HD bool lex_less(D3 a, D3 b) {
   if (a.y != b.y) return a.y < b.y;
   return a.z < b.z;
 }
-// the selection rules of std::min / std::max (first argument on ties)
-P2M_HD double dmin(double a, double b) { return b < a ? b : a; }
-P2M_HD double dmax(double a, double b) { return a < b ? b : a; }
+// Order-preserving 64-bit key of a double that is not NaN: its bits with the
+// sign flipped so that the keys order like the values (+0 and -0 share one
+// key, as they compare equal).  Comparisons of keys run on the integer units
+// instead of the double-precision pipe.
+P2M_HD uint64_t order_key(double v) {
+  uint64_t u;
+  memcpy(&u, &v, 8);
+  if (u == 0x8000000000000000ull) u = 0;
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+P2M_HD bool dless(double a, double b) { return order_key(a) < order_key(b); }
+// the selection rules of std::min / std::max (first argument on ties),
+// compared on the keys
+P2M_HD double dmin(double a, double b) { return dless(b, a) ? b : a; }
+P2M_HD double dmax(double a, double b) { return dless(a, b) ? b : a; }
 
 // Where the filter crosses zero on one polytope edge x(t) = x0 + t (x1 - x0),
 // 0 <= t <= 1, whose end values g(x0), g(x1) lie on opposite sides of zero
