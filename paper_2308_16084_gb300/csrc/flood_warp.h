@@ -104,13 +104,18 @@ enum { kNone = 0, kDone = 1, kGiveUp = 2 };
 P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &out,
                     int32_t hsrc = -1) {
   if (in.np > kWIn || in.nf > kWF) return kGiveUp;
+  // every point's signed distance and its class, kept in S.nxt while the
+  // cut runs (bit 0: s <= eps, on the kept side; bit 1: s >= -eps, not
+  // strictly inside), so that the passes below compare no double again
   P2M_LANES(l)
     bool b = false, w = false;
     for (int i = l; i < in.np; i += 32) {
       const double s = dot(hn, in.pt[i]) - hc;
       S.s[i] = s;
-      b |= s > eps;
-      w |= s < -eps;
+      const bool beyond = s > eps, inside = s < -eps;
+      b |= beyond;
+      w |= inside;
+      S.nxt[i] = (int16_t)((beyond ? 0 : 1) | (inside ? 0 : 2));
     }
     S.red_i[l] = (b ? 1 : 0) | (w ? 2 : 0);
   P2M_END_LANES
@@ -136,11 +141,12 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
       for (int i = 0; i < k; ++i) {
         const int ia = b + i, ib = b + (i + 1) % k;
         const double sa = S.s[ia], sb = S.s[ib];
-        const bool ka = sa <= eps, kb = sb <= eps;
+        const int ca = S.nxt[ia], cb = S.nxt[ib];
+        const bool ka = (ca & 1) != 0, kb = (cb & 1) != 0;
         if (ka) ++cnt;
         turns += ka != kb;
         if (ka && !kb) {
-          if (sa >= -eps) {
+          if (ca & 2) {
             X = in.pt[ia];
           } else {
             X = fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
@@ -148,7 +154,7 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
           }
           has_x = true;
         } else if (!ka && kb) {
-          if (sb >= -eps) {
+          if (cb & 2) {
             Y = in.pt[ib];
           } else {
             Y = fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
@@ -197,13 +203,14 @@ P2M_HD int warp_cut(WarpWork &S, View in, D3 hn, double hc, double eps, WPoly &o
       for (int i = 0; i < k; ++i) {
         const int ia = b + i, ib = b + (i + 1) % k;
         const double sa = S.s[ia], sb = S.s[ib];
-        const bool ka = sa <= eps, kb = sb <= eps;
+        const int ca = S.nxt[ia], cb = S.nxt[ib];
+        const bool ka = (ca & 1) != 0, kb = (cb & 1) != 0;
         if (ka) out.pt[o++] = in.pt[ia];
         if (ka && !kb) {
-          if (!(sa >= -eps))
+          if (!(ca & 2))
             out.pt[o++] = one ? S.seg_out[f] : fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
         } else if (!ka && kb) {
-          if (!(sb >= -eps))
+          if (!(cb & 2))
             out.pt[o++] = one ? S.seg_in[f] : fc::crossing(in.pt[ia], in.pt[ib], sa, sb);
         }
       }
