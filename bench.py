@@ -65,7 +65,7 @@ def parse(argv=None):
     ap.add_argument("--cpu-timeout", type=float, default=1500.0,
                     help="seconds to wait for the CPU oracle's tables after the GPU work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pipe-depth", type=int, default=4,
+    ap.add_argument("--pipe-depth", type=int, default=8,
                     help="slots of the pipelined host API in the end-to-end figure")
     ap.add_argument("--only", default=None,
                     choices=["headline", "cfg0", "cfg2", "fwd_bwd", "batched"],
