@@ -1123,6 +1123,11 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
   cudaEventCreate(&e1);
   p2m::QueryTuning best = h->tune;
   float bms = 1e30f;
+  struct Timed {
+    float ms;
+    p2m::QueryTuning t;
+  };
+  std::vector<Timed> timed;
   const int bits_c[] = {12, 15, 18, 21, 24};
   const int block_c[] = {128, 256};
   // threads per query: in the one-pass kernel, one thread per query (wm = 0)
@@ -1159,11 +1164,35 @@ p2m_status p2m_autotune(p2m_handle *h, const float *q, int64_t n, int reps, void
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      if (ms < bms) {
-        bms = ms;
-        best = h->tune;
-      }
+      timed.push_back({ms, h->tune});
     }
+  // the fastest few timed again, in turns, three times: the one with the
+  // lowest time wins (configurations within a few per cent of each other
+  // would otherwise be ranked by the noise of one timing)
+  {
+    std::sort(timed.begin(), timed.end(),
+              [](const Timed &a, const Timed &b) { return a.ms < b.ms; });
+    const size_t k = std::min<size_t>(timed.size(), 4);
+    std::vector<float> low(k, 1e30f);
+    for (int round = 0; round < 3; ++round)
+      for (size_t c = 0; c < k; ++c) {
+        h->tune = timed[c].t;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+          if ((s = p2m_query(h, q, n, dd, nullptr, dp, nullptr, nullptr, nullptr, st)))
+            goto done;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        low[c] = std::min(low[c], ms / reps);
+      }
+    for (size_t c = 0; c < k; ++c)
+      if (low[c] < bms) {
+        bms = low[c];
+        best = timed[c].t;
+      }
+  }
 done:
   h->tune = best;
   cudaStreamSynchronize(st);
