@@ -77,8 +77,8 @@ typedef struct {
   int device_assist;   /* 1 = the exact searches that certify the corners of the Voronoi
                           cells on the GPU (double-precision decisions),
                           2 = that and the flooding (Alg. 1, one warp per primitive) on
-                          the GPU, 3 = that and the whole cell stage on the GPU too (one
-                          thread per cell), 0 = CPU only.  The GPU steps are the host's
+                          the GPU, 3 = that, the whole cell stage (one warp per cell)
+                          and the packing of the table on the GPU too, 0 = CPU only.  The GPU steps are the host's
                           double-precision steps without fused multiply-adds; what
                           their buffers cannot hold is handed back to the host.
                           Every setting gives the same layout bit for bit (default 3,
@@ -443,8 +443,10 @@ p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]);
  * made on the device (device_assist = 3), out[1] = made on the host (every
  * cell with device_assist 0 to 2; with 3 the ones whose work overflowed the
  * device's fixed buffers, whose cap loop needs the angular ordering or
- * whose exact search gave up).  Both zero for a handle made by p2m_load. */
-p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[2]);
+ * whose exact search gave up); out[2] = 1 if the table was packed on the
+ * device (device_assist = 3; the host packs when a row is longer than the
+ * device's sort holds), else 0.  All zero for a handle made by p2m_load. */
+p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[3]);
 
 /* The domain D (lo xyz, hi xyz) and delta of a handle. */
 p2m_status p2m_domain(const p2m_handle *h, float out[7]);

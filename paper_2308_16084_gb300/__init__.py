@@ -155,11 +155,11 @@ class P2M:
         return {"device": out[0], "host_bounded": out[1], "host_unbounded": out[2]}
 
     def cell_stats(self):
-        """How the build's Voronoi cells were split: made on the device, on
-        the host."""
-        out = (ctypes.c_int64 * 2)()
+        """How the build's Voronoi cells were split (made on the device, on
+        the host) and whether the table was packed on the device."""
+        out = (ctypes.c_int64 * 3)()
         check(lib.p2m_cell_stats(self._h, out), "p2m_cell_stats")
-        return {"device": out[0], "host": out[1]}
+        return {"device": out[0], "host": out[1], "packed_on_device": out[2]}
 
     def domain(self):
         """(lo, hi, delta): the query domain D and the widening margin."""

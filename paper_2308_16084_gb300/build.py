@@ -26,7 +26,7 @@ def _nvcc():
 def _sources():
     return {
         "kernels.cu": "cu", "certify.cu": "cu", "p2m_api.cu": "cu", "noalloc.cu": "cu",
-        "flood.cu": "cu-nofma", "cells.cu": "cu-nofma", "builder.cpp": "cpp",
+        "flood.cu": "cu-nofma", "cells.cu": "cu-nofma", "pack.cu": "cu-nofma", "builder.cpp": "cpp",
     }
 
 

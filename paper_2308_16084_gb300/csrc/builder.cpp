@@ -14,6 +14,7 @@
 #include "builder.h"
 #include "flood_core.h"
 #include "flood_warp.h"
+#include "pack.h"
 #include "quant.h"
 
 #include <algorithm>
@@ -1267,6 +1268,34 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     out.flood_bounded += x.bounded;
     out.flood_unbounded += x.unbounded;
   }
+  // ---- packing: the code frame, then the table on the device service when
+  // asked (pack_core.h: the same steps and words), else here
+  float qstep[3], qbase[3];
+  for (int d = 0; d < 3; ++d) {
+    float flo = (float)(Dlo[d] - 4 * delta), fhi = (float)(Dhi[d] + 4 * delta);
+    out.qframe_lo[d] = flo;
+    out.qframe_inv[d] = (float)((double)(kQMax - 16) / ((double)fhi - (double)flo));
+  }
+  q_frame_derive(out.qframe_lo, out.qframe_inv, qstep, qbase);
+  int64_t maxl = 0;
+  std::atomic<int64_t> bad_boxes{0};
+  bool packed = false;
+  if (prm.device_pack && nearest) {
+    std::vector<PackPart> parts;
+    for (auto &x : tls) parts.push_back({x.recs.data(), (int64_t)x.recs.size()});
+    parts.push_back({drec.data(), (int64_t)drec.size()});
+    int64_t ml = 0, bad = 0;
+    if (nearest->pack(nv, parts, out.qframe_lo, out.qframe_inv, out, ml, bad)) {
+      packed = true;
+      maxl = ml;
+      bad_boxes = bad;
+      total = out.row_off[nv];
+      out.pack_device = 1;
+      tls.clear();
+      std::vector<Rec>().swap(drec);
+    }
+  }
+  if (!packed) {
   // bucket the records by row: counts and then positions taken with atomic
   // increments, in parallel over blocks of every record list (the order
   // inside a row is fixed by the sort below, a total order)
@@ -1350,17 +1379,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   });
   sort_keys.clear();
   sort_tmp.clear();
-  int64_t maxl = 0;
   for (int64_t p = 0; p < nv; ++p) maxl = std::max<int64_t>(maxl, out.row_off[p + 1] - out.row_off[p]);
 
   // ---- chunks of every row, and the 15-bit box codes (quant.h)
-  float qstep[3], qbase[3];
-  for (int d = 0; d < 3; ++d) {
-    float flo = (float)(Dlo[d] - 4 * delta), fhi = (float)(Dhi[d] + 4 * delta);
-    out.qframe_lo[d] = flo;
-    out.qframe_inv[d] = (float)((double)(kQMax - 16) / ((double)fhi - (double)flo));
-  }
-  q_frame_derive(out.qframe_lo, out.qframe_inv, qstep, qbase);
   out.chunk_off.assign(nv + 1, 0);
   for (int64_t p = 0; p < nv; ++p) {
     uint32_t len = out.row_off[p + 1] - out.row_off[p];
@@ -1368,7 +1389,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   }
   out.chunks.assign(4 * (size_t)out.chunk_off[nv], 0u);
   out.entries.assign(4 * (size_t)total, 0u);
-  std::atomic<int64_t> bad_boxes{0};
   parallel_for(nv, threads, 1024, [&](int64_t p, int) {
     uint32_t c = out.chunk_off[p];
     for (uint32_t j = out.row_off[p]; j < out.row_off[p + 1]; j += Layout::kChunk, ++c) {
@@ -1444,6 +1464,7 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       q_words(sl, sh, &out.supers[4 * (size_t)sidx]);
     }
   });
+  }  // host packing
   if (bad_boxes.load()) {
     err = "internal error: a Region box does not fit the code frame of its chunk";
     return 5;

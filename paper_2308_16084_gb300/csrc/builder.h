@@ -23,6 +23,7 @@ struct BuildParams {
   int leaf_size = 8;
   bool device_flood = false;  // flood on the nearest service when it offers that
   bool device_cells = false;  // Voronoi cells on the nearest service when it offers that
+  bool device_pack = false;   // the table's packing on the nearest service when it offers that
 };
 
 // The Voronoi cells of every row (KD-tree position), clipped to D, for a
@@ -88,6 +89,14 @@ struct FloodRec {
   float box[6];
 };
 
+struct Layout;
+
+// a run of records for the packing service
+struct PackPart {
+  const FloodRec *rec;
+  int64_t n;
+};
+
 // Device services of the builder: the exact search that certifies the
 // Voronoi cells' corners, the whole cell stage and the flooding.  Each
 // returns false where it is unavailable (the host then does the work).
@@ -113,6 +122,16 @@ struct NearestService {
   // values bit for bit), with the rows it hands back marked
   virtual bool cells(const CellProblem &pb, CellResult &out) {
     (void)pb, (void)out;
+    return false;
+  }
+  // the packing of the table from the records of parts[] (row >= 0, any
+  // order) in the code frame qlo / qinv, as the host builder packs it (the
+  // same words bit for bit): out's row_off, entries, chunk_off, chunks,
+  // super_off, supers, the longest row and the count of entry codes outside
+  // their chunk's frame
+  virtual bool pack(int64_t nv, const std::vector<PackPart> &parts, const float qlo[3],
+                    const float qinv[3], Layout &out, int64_t &max_list, int64_t &bad_boxes) {
+    (void)nv, (void)parts, (void)qlo, (void)qinv, (void)out, (void)max_list, (void)bad_boxes;
     return false;
   }
 };
@@ -173,8 +192,9 @@ struct Layout {
   // primitives flooded on the device, by the host's bounded core and by its
   // unbounded code (the ones the core gave up)
   int64_t flood_device = 0, flood_bounded = 0, flood_unbounded = 0;
-  // Voronoi cells made on the device and on the host
-  int64_t cells_device = 0, cells_host = 0;
+  // Voronoi cells made on the device and on the host; 1 if the table was
+  // packed on the device
+  int64_t cells_device = 0, cells_host = 0, pack_device = 0;
   double ms_total = 0, ms_cells = 0, ms_inspect = 0;
 };
 

@@ -20,6 +20,7 @@
 #include "cells.h"
 #include "certify.h"
 #include "flood.h"
+#include "pack.h"
 #include "quant.h"
 #include "kernels.h"
 #include "quant.h"
@@ -302,6 +303,11 @@ struct DeviceNearest : p2m::NearestService {
   bool cells(const p2m::CellProblem &pb, p2m::CellResult &out) override {
     return p2m::cells_on_device(h->view, pb, out);
   }
+  bool pack(int64_t nv, const std::vector<p2m::PackPart> &parts, const float qlo[3],
+            const float qinv[3], p2m::Layout &out, int64_t &max_list,
+            int64_t &bad_boxes) override {
+    return p2m::pack_on_device(nv, parts, qlo, qinv, out, max_list, bad_boxes);
+  }
 };
 
 // the builder fills the handle's own layout; once its KD tree exists the
@@ -380,6 +386,7 @@ p2m_status p2m_build_mixed(const p2m_mesh *mesh, const int32_t *segs, int64_t n_
   prm.leaf_size = o.leaf_size;
   prm.device_flood = o.device_assist >= 2;
   prm.device_cells = o.device_assist == 3;
+  prm.device_pack = o.device_assist == 3;
   DeviceNearest dn(h.get());
   const bool assist = o.device_assist && h->device >= 0;
   std::string err;
@@ -855,10 +862,11 @@ p2m_status p2m_flood_stats(const p2m_handle *h, int64_t out[3]) {
   return P2M_OK;
 }
 
-p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[2]) {
+p2m_status p2m_cell_stats(const p2m_handle *h, int64_t out[3]) {
   if (!h || !out) return P2M_ERR_INVALID_ARG;
   out[0] = h->L.cells_device;
   out[1] = h->L.cells_host;
+  out[2] = h->L.pack_device;
   return P2M_OK;
 }
 

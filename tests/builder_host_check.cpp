@@ -7,7 +7,8 @@
 //      (the nearest tree position strictly inside the bound, lowest
 //      position on ties), the Voronoi cells made in the device's rounds by
 //      its warp phases (cell_warp.h, lanes one after another) with every
-//      seventh cell handed back to the host, and the flooding run with the device kernel's warp
+//      seventh cell handed back to the host, the packing by pack_core.h's
+//      steps (rows in reverse order), and the flooding run with the device kernel's warp
 //      algorithm (flood_warp.h, lanes one after another, row stamps as on
 //      the device), and requires
 //      every table, box code, neighbour list and count to equal the host
@@ -29,6 +30,7 @@
 #include "cell_warp.h"
 #include "flood_core.h"
 #include "flood_warp.h"
+#include "pack_core.h"
 
 using namespace p2m;
 
@@ -166,6 +168,60 @@ struct StandIn : NearestService {
     }
     return true;
   }
+  // the device's packing: records bucketed by row in reverse order, every
+  // row sorted on pack_core.h's keys, chunks and super-chunks encoded by it
+  bool pack(int64_t nv, const std::vector<PackPart> &parts, const float qlo[3],
+            const float qinv[3], Layout &out, int64_t &max_list, int64_t &bad_boxes) override {
+    std::vector<std::vector<FloodRec>> rows(nv);
+    for (auto it = parts.rbegin(); it != parts.rend(); ++it)
+      for (int64_t j = it->n - 1; j >= 0; --j)
+        if (it->rec[j].row >= 0) rows[it->rec[j].row].push_back(it->rec[j]);
+    pk::Frame fr;
+    for (int d = 0; d < 3; ++d) {
+      fr.lo[d] = qlo[d];
+      fr.inv[d] = qinv[d];
+    }
+    q_frame_derive(fr.lo, fr.inv, fr.step, fr.base);
+    out.row_off.assign(nv + 1, 0);
+    out.chunk_off.assign(nv + 1, 0);
+    out.super_off.assign(nv + 1, 0);
+    max_list = 0;
+    for (int64_t p = 0; p < nv; ++p) {
+      const uint32_t len = (uint32_t)rows[p].size();
+      max_list = std::max<int64_t>(max_list, len);
+      out.row_off[p + 1] = out.row_off[p] + len;
+      const uint32_t nc = (len + pk::kChunk - 1) / pk::kChunk;
+      out.chunk_off[p + 1] = out.chunk_off[p] + nc;
+      out.super_off[p + 1] = out.super_off[p] + (nc + pk::kChunk - 1) / pk::kChunk;
+    }
+    out.entries.assign(4 * (size_t)out.row_off[nv], 0u);
+    out.chunks.assign(4 * (size_t)out.chunk_off[nv], 0u);
+    out.supers.assign(4 * (size_t)out.super_off[nv], 0u);
+    bad_boxes = 0;
+    for (int64_t p = 0; p < nv; ++p) {
+      auto &r = rows[p];
+      if (r.size() >= 2) {
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (const FloodRec &x : r) pk::centre_bounds_add(x, lo, hi);
+        std::sort(r.begin(), r.end(), [&](const FloodRec &a, const FloodRec &b) {
+          return pk::row_key(a, lo, hi) < pk::row_key(b, lo, hi);
+        });
+      }
+      uint32_t c = out.chunk_off[p];
+      for (uint32_t j = 0; j < r.size(); j += pk::kChunk, ++c) {
+        const uint32_t cnt = std::min<uint32_t>(pk::kChunk, (uint32_t)r.size() - j);
+        bad_boxes += pk::encode_chunk(r.data() + j, cnt, fr.lo, fr.inv, fr.step, fr.base,
+                                      &out.chunks[4 * (size_t)c],
+                                      &out.entries[4 * (size_t)(out.row_off[p] + j)]);
+      }
+      uint32_t sidx = out.super_off[p];
+      for (uint32_t k = out.chunk_off[p]; k < out.chunk_off[p + 1]; k += pk::kChunk, ++sidx)
+        pk::encode_super(&out.chunks[4 * (size_t)k],
+                         std::min<uint32_t>(pk::kChunk, out.chunk_off[p + 1] - k),
+                         &out.supers[4 * (size_t)sidx]);
+    }
+    return true;
+  }
   bool within(const double *xyz, const double *r2, int64_t n, int64_t *out) override {
     for (int64_t i = 0; i < n; ++i) {
       double best = r2[i];
@@ -266,6 +322,7 @@ int main(int argc, char **argv) {
   BuildParams prm2 = prm;
   prm2.device_flood = true;
   prm2.device_cells = true;
+  prm2.device_pack = true;
   Layout dev;
   auto on_tree = [](void *ctx, const Layout &L) {
     ((StandIn *)ctx)->L = &L;
@@ -274,6 +331,7 @@ int main(int argc, char **argv) {
   CHECK(build_layout(V.data(), nv, Fp, nf, Sp, ns, prm2, &svc, on_tree, &svc, dev, err) == 0);
   CHECK(dev.flood_device > 0);
   CHECK(dev.cells_device > 0 && dev.cells_host > 0);
+  CHECK(dev.pack_device == 1 && host.pack_device == 0);
   CHECK(host.cells_device == 0 && host.cells_host == nv);
   CHECK(same(host, dev));
 

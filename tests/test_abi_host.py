@@ -351,7 +351,7 @@ def test_device_flooding_requested_without_a_gpu(pg):
     assert a.flood_stats()["device"] == 0
     c = pg.P2M(m.verts, m.tris, domain_scale=m.domain_scale, domain_margin=m.domain_margin,
                device_assist=3)
-    assert c.cell_stats() == {"device": 0, "host": m.verts.shape[0]}
+    assert c.cell_stats() == {"device": 0, "host": m.verts.shape[0], "packed_on_device": 0}
     assert c.flood_stats() == b.flood_stats()
     with tempfile.TemporaryDirectory() as d:
         pa, pb = os.path.join(d, "a.p2m"), os.path.join(d, "b.p2m")
@@ -401,7 +401,8 @@ def test_build_options_and_stats_at_the_c_abi(pg):
     assert pg.lib.p2m_flood_stats(m._h, out) == 0
     assert list(out[:3]) == [0, m.flood_stats()["host_bounded"], 0]
     assert pg.lib.p2m_cell_stats(m._h, None) == 1
-    assert m.cell_stats() == {"device": 0, "host": 42}  # every cell of the 42 vertices
+    # every cell of the 42 vertices, packed on the host
+    assert m.cell_stats() == {"device": 0, "host": 42, "packed_on_device": 0}
 
 
 @pytest.mark.parametrize("stage", ["cells", "flooding", "packing"])

@@ -57,7 +57,9 @@ def test_device_flood_builds_the_host_layout(pg, name):
     c = pg.P2M(m.verts, m.tris, device_assist=3, **kw)
     cs = c.cell_stats()
     assert cs["device"] > 0 and cs["device"] + cs["host"] == m.verts.shape[0]
-    assert a.cell_stats() == b.cell_stats() == {"device": 0, "host": m.verts.shape[0]}
+    assert cs["packed_on_device"] == 1
+    assert a.cell_stats() == b.cell_stats() == {"device": 0, "host": m.verts.shape[0],
+                                                "packed_on_device": 0}
     with tempfile.TemporaryDirectory() as d:
         pa, pb, pc = (os.path.join(d, f"{x}.p2m") for x in "abc")
         a.save(pa)
