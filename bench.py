@@ -166,8 +166,11 @@ def _oracle_worker(conn, level, n_queries, threads):
         import oracle
         m = dg.workload(WORKLOAD, n_queries=n_queries, level=level)
         t0 = time.perf_counter()
+        # two cores left to the GPU side while the tables build beside its
+        # measurements (its end-to-end loop and the builder's host threads);
+        # the timed queries below take all of them
         o = oracle.OracleMesh(m.verts, m.tris, m.domain_scale, m.domain_margin,
-                              threads=threads, voronoi="delaunay")
+                              threads=max(1, threads - 2), voronoi="delaunay")
         build_s = time.perf_counter() - t0
         conn.send(("built", {"build_s": round(build_s, 1), "qhull_s": round(o.delaunay_s, 1),
                              "table_entries": o.n_entries, "times_ms": o.times_ms}))
