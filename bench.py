@@ -8,8 +8,9 @@ queries.  The headline is workload 1: the 1,310,720-triangle displaced
 icosphere with 10M uniform queries.  The same JSON line (rank 0) also
 carries the other four workloads, each with its own CUDA-event timing,
 clocks, roofline and end-to-end figure:
-  configs["0"], configs["2"]  plain forward on the small noisy icosphere and
-                              on the 2.1M-triangle jittered height field;
+  configs                     workloads 0 and 2: plain forward on the small
+                              noisy icosphere and on the 2.1M-triangle
+                              jittered height field;
   fwd_bwd                     workload 3: forward+backward against forward;
   batched                     workload 4: 64 meshes in one CUDA-graph launch
                               against 64 per-mesh launches.
