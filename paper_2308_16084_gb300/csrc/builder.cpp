@@ -1137,56 +1137,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
 
   const double t_flat = now_ms();
   if (trace) std::fprintf(stderr, "p2m build: flooding problem %.0f ms\n", t_flat - t_flood);
-  // on the device service, when asked; the host floods what it gives up
-  std::vector<uint8_t> host_todo;  // empty: the host floods everything
-  int64_t n_device = 0;
-  std::vector<Rec> drec;  // the device's records (row -1: dropped)
-  if (prm.device_flood && nearest && nk > 0) {
-    FloodProblem pb;
-    pb.nv = nv;
-    pb.n = nk;
-    pb.cell_pt_off = pt_off.data();
-    pb.cell_pt = &cpt.data()->x;
-    pb.cell_beg_off = beg_off.data();
-    pb.cell_beg = cbeg.data();
-    pb.pv = &T.P.data()->x;
-    pb.vid = T.order.data();
-    pb.nb_off = out.nb_off.data();
-    pb.nb = out.nb.data();
-    pb.perp_off = perp_off.data();
-    pb.perp = fperp.data();
-    pb.gtype = gtype.data();
-    pb.g = fg.data();
-    pb.seed_row = srow.data();
-    pb.seed_vid = svid.data();
-    pb.tid = tids.data();
-    pb.eps = eps;
-    pb.delta = delta;
-    pb.eta = eta;
-    std::vector<uint8_t> gave;
-    int64_t dinsp = 0;
-    if (nearest->flood(pb, drec, gave, dinsp) && (int64_t)gave.size() == nk) {
-      host_todo.swap(gave);
-      std::vector<uint8_t> prim_gave(nprim, 0);
-      for (int64_t k = 0; k < nk; ++k) {
-        if (host_todo[k]) prim_gave[idx[k]] = 1;
-        else ++n_device;
-      }
-      // the records of the primitives handed back are the host's to make
-      const int64_t nd = (int64_t)drec.size();
-      parallel_for((nd + 4095) / 4096, threads, 16, [&](int64_t c, int) {
-        for (int64_t j = 4096 * c; j < std::min(nd, 4096 * (c + 1)); ++j) {
-          Rec &r = drec[j];
-          const int64_t pi = prim_of_tid(r.tid);
-          if (!(r.row >= 0 && r.row < nv && pi >= 0 && pi < nprim && !prim_gave[pi])) r.row = -1;
-        }
-      });
-      tls[0].inspections += dinsp;
-    } else {
-      drec.clear();
-    }
-  }
-
   // the host side of the shared core
   struct HostEnv : fc::Flat {
     int64_t *seen;
@@ -1206,10 +1156,6 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
       recs->push_back(r);
     }
   };
-  const double t_host_flood = now_ms();
-  if (trace && !host_todo.empty())
-    std::fprintf(stderr, "p2m build: device flooding %.0f ms (%lld primitives, %lld handed back)\n",
-                 t_host_flood - t_flat, (long long)n_device, (long long)(nk - n_device));
   // P2M_FLOOD_UNBOUNDED=1 floods every primitive with the unbounded code;
   // P2M_FLOOD_LANES=1 floods with the device kernel's warp algorithm
   // (flood_warp.h, its 32 lanes run one after another) before the bounded
@@ -1223,9 +1169,9 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
   std::vector<std::unique_ptr<fw::WarpWork>> lane_work(lanes ? threads : 0);
   for (auto &w : lane_work) w.reset(new fw::WarpWork);
   const bool fail_flooding = inject_at("flooding");
-  parallel_for(nk, threads, 32, [&](int64_t k, int t) {
-    if (fail_flooding && k == nk / 2) throw std::bad_alloc();
-    if (!host_todo.empty() && !host_todo[k]) return;
+  // primitive k flooded here by worker t: the bounded core, else the
+  // unbounded code
+  auto flood_here = [&](int64_t k, int t) {
     TLS &X = tls[t];
     HostEnv env;
     static_cast<fc::Flat &>(env) = fl;
@@ -1255,6 +1201,168 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     PrimData P;
     setup(idx[k], P);
     flood_unbounded(2 * k + 1, P, X);
+  };
+
+  // On the device service, when asked, side by side with the host: the
+  // device floods primitives from the front of [0, nk) in a few calls, each
+  // taking a share of what nobody has taken yet, while host workers flood
+  // from the back, a small block at a time, and take up first what an
+  // earlier call handed back.  Which side floods a primitive changes none of
+  // its records, and every row is sorted into a total order when packed, so
+  // the layout is the same whatever the split.
+  std::vector<uint8_t> host_todo;  // empty: the host floods everything
+  int64_t n_device = 0, n_beside = 0, device_calls = 0, device_returned = 0;
+  std::vector<Rec> drec;  // the device's records (row -1: dropped)
+  if (prm.device_flood && nearest && nk > 0) {
+    FloodProblem pb;
+    pb.nv = nv;
+    pb.cell_pt_off = pt_off.data();
+    pb.cell_pt = &cpt.data()->x;
+    pb.cell_beg_off = beg_off.data();
+    pb.cell_beg = cbeg.data();
+    pb.pv = &T.P.data()->x;
+    pb.vid = T.order.data();
+    pb.nb_off = out.nb_off.data();
+    pb.nb = out.nb.data();
+    pb.perp = fperp.data();
+    pb.eps = eps;
+    pb.delta = delta;
+    pb.eta = eta;
+    // host workers beside the thread that drives the device; the device
+    // floods about as fast as 22 Grace cores (390 k against 13 k primitives
+    // a second on the 1.3M-triangle mesh), so its first share is, unless
+    // set, 22.5 / (22.5 + workers) of all, and each later call takes 0.6 of
+    // what is left while that is at least flood_min_share primitives
+    const int nw = prm.flood_host_workers >= 0 ? std::min(prm.flood_host_workers, threads)
+                   : (threads > 2 ? threads - 1 : 1);
+    constexpr int64_t kBlock = 64;
+    const int64_t min_share = std::max<int64_t>(1, prm.flood_min_share);
+    const double first = prm.flood_first_share >= 0 ? std::min(1.0, prm.flood_first_share)
+                                                    : 22.5 / (22.5 + nw);
+    std::mutex mu;
+    int64_t front = 0, back = nk;    // [front, back): not taken yet
+    std::vector<int64_t> returned;   // handed back by a finished device call
+    size_t returned_at = 0;          // returned[0 .. returned_at): taken up
+    bool stop = false;
+    std::exception_ptr failure;
+    std::atomic<int64_t> beside{0};
+    auto worker = [&](int t) {
+      int64_t mine = 0;
+      try {
+        if (fail_flooding) throw std::bad_alloc();
+        for (;;) {
+          int64_t k0 = 0, k1 = 0, hb = -1;
+          {
+            std::lock_guard<std::mutex> g(mu);
+            if (stop) break;
+            if (returned_at < returned.size()) {
+              hb = returned[returned_at++];
+            } else if (back > front) {
+              k1 = back;
+              k0 = std::max(front, back - kBlock);
+              back = k0;
+            } else {
+              break;
+            }
+          }
+          if (hb >= 0) {
+            flood_here(hb, t);
+            continue;
+          }
+          for (int64_t k = k1 - 1; k >= k0; --k) flood_here(k, t);
+          mine += k1 - k0;
+        }
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!failure) failure = std::current_exception();
+        stop = true;
+      }
+      beside += mine;
+    };
+    // one device call on [k0, k1): the problem's per-primitive arrays from
+    // k0 on (the offsets stay absolute, into the whole arrays)
+    int64_t dinsp = 0;
+    auto device_call = [&](int64_t k0, int64_t k1, std::vector<uint8_t> &gave) {
+      FloodProblem sub = pb;
+      sub.n = k1 - k0;
+      sub.perp_off = perp_off.data() + k0;
+      sub.gtype = gtype.data() + k0;
+      sub.g = fg.data() + 6 * k0;
+      sub.seed_row = srow.data() + 3 * k0;
+      sub.seed_vid = svid.data() + 3 * k0;
+      sub.tid = tids.data() + k0;
+      std::vector<Rec> r;
+      int64_t insp = 0;
+      if (!nearest->flood(sub, r, gave, insp) || (int64_t)gave.size() != sub.n) return false;
+      ++device_calls;
+      dinsp += insp;
+      if (drec.empty()) drec.swap(r);
+      else drec.insert(drec.end(), r.begin(), r.end());
+      return true;
+    };
+    front = std::max<int64_t>(1, std::min<int64_t>(nk, (int64_t)std::ceil(first * (double)nk)));
+    int64_t k0 = 0, k1 = front;
+    std::vector<std::thread> pool;
+    try {
+      for (int t = 0; t < nw; ++t) pool.emplace_back(worker, t);
+      for (;;) {
+        std::vector<uint8_t> gave;
+        const bool ok = device_call(k0, k1, gave);
+        std::lock_guard<std::mutex> g(mu);
+        if (!ok) {
+          front = k0;  // the workers take the range back (front == k1 until now)
+          break;
+        }
+        for (int64_t k = k0; k < k1; ++k)
+          if (gave[k - k0]) returned.push_back(k);
+          else ++n_device;
+        const int64_t left = back - front;
+        if (stop || left < min_share) break;
+        k0 = front;
+        k1 = front + (int64_t)std::ceil(0.6 * left);
+        front = k1;
+      }
+    } catch (...) {
+      std::lock_guard<std::mutex> g(mu);
+      if (!failure) failure = std::current_exception();
+      stop = true;
+    }
+    for (auto &th : pool) th.join();
+    if (failure) std::rethrow_exception(failure);
+    n_beside = beside.load();
+    device_returned = (int64_t)returned.size();
+    // what the workers did not take up is flooded below; the device's
+    // records of every primitive it handed back are dropped
+    host_todo.assign(nk, 0);
+    for (size_t j = returned_at; j < returned.size(); ++j) host_todo[returned[j]] = 1;
+    // and a range nobody took (a failed call's, given back after the
+    // workers had finished)
+    for (int64_t k = front; k < back; ++k) host_todo[k] = 1;
+    std::vector<uint8_t> prim_gave(nprim, 0);
+    for (int64_t k : returned) prim_gave[idx[k]] = 1;
+    std::vector<int64_t>().swap(returned);
+    const int64_t nd = (int64_t)drec.size();
+    parallel_for((nd + 4095) / 4096, threads, 16, [&](int64_t c, int) {
+      for (int64_t j = 4096 * c; j < std::min(nd, 4096 * (c + 1)); ++j) {
+        Rec &r = drec[j];
+        const int64_t pi = prim_of_tid(r.tid);
+        if (!(r.row >= 0 && r.row < nv && pi >= 0 && pi < nprim && !prim_gave[pi])) r.row = -1;
+      }
+    });
+    tls[0].inspections += dinsp;
+  }
+
+  const double t_host_flood = now_ms();
+  if (trace && !host_todo.empty())
+    std::fprintf(stderr,
+                 "p2m build: device flooding %.0f ms (%lld primitives in %lld calls, %lld handed "
+                 "back; %lld flooded here beside it)\n",
+                 t_host_flood - t_flat, (long long)n_device, (long long)device_calls,
+                 (long long)device_returned, (long long)n_beside);
+  parallel_for(nk, threads, 32, [&](int64_t k, int t) {
+    if (fail_flooding && k == nk / 2) throw std::bad_alloc();
+    if (!host_todo.empty() && !host_todo[k]) return;
+    flood_here(k, t);
   });
 
   const double t_pack = now_ms();

@@ -24,6 +24,13 @@ struct BuildParams {
   bool device_flood = false;  // flood on the nearest service when it offers that
   bool device_cells = false;  // Voronoi cells on the nearest service when it offers that
   bool device_pack = false;   // the table's packing on the nearest service when it offers that
+  // the device flooding beside the host's: host workers beside the device
+  // (< 0: the build's threads but one), the share of all primitives the
+  // first device call takes (< 0: sized from the workers) and the fewest
+  // primitives a later call takes
+  int flood_host_workers = -1;
+  double flood_first_share = -1.0;
+  int64_t flood_min_share = 1 << 14;
 };
 
 // The Voronoi cells of every row (KD-tree position), clipped to D, for a

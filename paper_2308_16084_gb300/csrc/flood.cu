@@ -139,10 +139,17 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     uint8_t *dgave = B.get<uint8_t>((size_t)n, e);
     // records, inspections, work counter
     unsigned long long *cnt = B.get<unsigned long long>(3, e);
-    // room for 64 records a primitive (workload meshes take 15 to 45); a
-    // second run with the exact count when that is not enough (the record
-    // set of a run is deterministic)
-    unsigned long long cap = (unsigned long long)std::max<int64_t>(1 << 20, 64 * n);
+    // room for 128 records a primitive (the workload meshes take 15 to 45
+    // on average over all primitives, but up to about 100 over their faces
+    // alone, and a call may be given faces only), within half the free
+    // device memory; a second run with the exact count when that is not
+    // enough (the record set of a run is deterministic)
+    size_t free_bytes = 0, total_bytes = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_bytes, &total_bytes);
+    unsigned long long cap = std::max<unsigned long long>(
+        1ull << 20, std::min<unsigned long long>(128ull * (unsigned long long)n,
+                                                 free_bytes / 2 / sizeof(FloodRec)));
+    int runs = 0;
     unsigned long long h_cnt[2] = {0, 0};
     // one row stamp per warp and row (4 bytes each: 3.2 GB for the 655k rows of
     // the 1.3M-triangle mesh), when that fits in 8 GB; else the warps scan
@@ -166,7 +173,7 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
       env.rec = drec;
       env.count = cnt;
       env.cap = cap;
-      t1 = ms();
+      if (runs++ == 0) t1 = ms();
       k_flood_warp<<<sms, kFloodWarps * 32, smem>>>(env, n, pb.eps, pb.delta, pb.eta, dgave,
                                                      cnt + 1, cnt + 2, seen, nv);
       e = cudaGetLastError();
@@ -190,9 +197,9 @@ bool flood_on_device(const FloodProblem &pb, std::vector<FloodRec> &out,
     inspections = (int64_t)h_cnt[1];
     if (trace)
       std::fprintf(stderr,
-                   "p2m build:   device flooding: upload %.0f ms, kernel %.0f ms, download %.0f ms "
-                   "(%llu records)\n",
-                   t1 - t0, t2 - t1, ms() - t2, h_cnt[0]);
+                   "p2m build:   device flooding: %lld primitives, upload %.0f ms, kernel %.0f ms, "
+                   "download %.0f ms (%llu records, %d run(s))\n",
+                   (long long)n, t1 - t0, t2 - t1, ms() - t2, h_cnt[0], runs);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -80,6 +80,8 @@ struct CellEnv {
 
 struct StandIn : NearestService {
   const Layout *L = nullptr;
+  int flood_calls = 0;     // flooding calls answered
+  int64_t hand_back = 0;   // > 0: every hand_back-th primitive of a call handed back too
   bool cells(const CellProblem &pb, CellResult &out) override {
     CellEnv env{L};
     cc::CellParams cp;
@@ -266,9 +268,11 @@ struct StandIn : NearestService {
     for (int64_t i = pb.n - 1; i >= 0; --i) {  // any order: the host sorts
       int64_t k = 0;
       const int r = fw::flood_warp(*S, env, i, pb.eps, pb.delta, pb.eta, k, seen.data());
-      gave_up[i] = r != 0;  // records of a given-up primitive stay in: the host drops them
-      if (r == 0) inspections += k;
+      // records of a given-up primitive stay in: the host drops them
+      gave_up[i] = r != 0 || (hand_back > 0 && i % hand_back == hand_back - 1);
+      if (!gave_up[i]) inspections += k;
     }
+    ++flood_calls;
     return true;
   }
 };
@@ -335,6 +339,25 @@ int main(int argc, char **argv) {
   CHECK(host.cells_device == 0 && host.cells_host == nv);
   CHECK(same(host, dev));
 
+  // the flooding in several device calls on sub-ranges of the primitives
+  // (no host workers beside it: the calls' ranges are fixed), every fifth
+  // primitive of a call handed back; then with the workers beside it
+  for (int workers : {0, -1}) {
+    StandIn s3;
+    s3.hand_back = 5;
+    BuildParams prm3 = prm2;
+    prm3.flood_host_workers = workers;
+    prm3.flood_first_share = 0.3;
+    prm3.flood_min_share = 16;
+    Layout d3;
+    CHECK(build_layout(V.data(), nv, Fp, nf, Sp, ns, prm3, &s3, on_tree, &s3, d3, err) == 0);
+    CHECK(s3.flood_calls >= 1 && d3.flood_device > 0);
+    if (workers == 0) CHECK(s3.flood_calls >= 3);
+    CHECK(d3.flood_device + d3.flood_bounded + d3.flood_unbounded ==
+          dev.flood_device + dev.flood_bounded + dev.flood_unbounded);
+    CHECK(same(host, d3));
+  }
+
   for (const char *stage : {"cells", "flooding", "packing"}) {
     setenv("P2M_INJECT_BAD_ALLOC", stage, 1);
     Layout L;
@@ -345,6 +368,20 @@ int main(int argc, char **argv) {
       thrown = true;
     }
     CHECK(thrown);
+  }
+  // a failure of a host worker beside the device flooding: the build
+  // throws once the device call has come back and every worker has ended
+  {
+    setenv("P2M_INJECT_BAD_ALLOC", "flooding", 1);
+    StandIn s4;
+    Layout L;
+    bool thrown = false;
+    try {
+      build_layout(V.data(), nv, Fp, nf, Sp, ns, prm2, &s4, on_tree, &s4, L, err);
+    } catch (const std::bad_alloc &) {
+      thrown = true;
+    }
+    CHECK(thrown && s4.flood_calls == 1);
   }
   unsetenv("P2M_INJECT_BAD_ALLOC");
   std::printf("OK\n");
