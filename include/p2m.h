@@ -77,7 +77,8 @@ typedef struct {
   int device_assist;   /* 1 = the exact searches that certify the corners of the Voronoi
                           cells on the GPU (double-precision decisions),
                           2 = that and the flooding (Alg. 1, one warp per primitive) on
-                          the GPU, 3 = that, the whole cell stage (one warp per cell)
+                          the GPU, the host threads flooding a share of the primitives
+                          beside it, 3 = that, the whole cell stage (one warp per cell)
                           and the packing of the table on the GPU too, 0 = CPU only.  The GPU steps are the host's
                           double-precision steps without fused multiply-adds; what
                           their buffers cannot hold is handed back to the host.
@@ -432,7 +433,8 @@ p2m_status p2m_get_edges(const p2m_handle *h, int32_t *edges, int64_t *n_edges);
 p2m_status p2m_stats(const p2m_handle *h, int64_t out[16]);
 
 /* How the flooding of a handle's build was split: out[0] = primitives
- * flooded on the device (device_assist 2 or 3), out[1] = flooded on the host by
+ * flooded on the device (device_assist 2 or 3; how many depends on how fast
+ * the host threads flooding beside it are), out[1] = flooded on the host by
  * the bounded core shared with the device, out[2] = flooded on the host by
  * the unbounded code (primitives whose polytopes exceed the core's fixed
  * buffers, or whose cap loop needs the angular ordering).  All zero for a
