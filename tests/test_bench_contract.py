@@ -71,3 +71,43 @@ def test_oracle_sample_is_seeded_and_sorted():
     a = bench.oracle_sample(10_000_000, 5000)
     b = bench.oracle_sample(10_000_000, 5000)
     assert (a == b).all() and (a[1:] > a[:-1]).all() and a.max() < 10_000_000
+
+
+def test_clock_samples_summary():
+    """The clocks object: median SM clock under load, the highest maximum
+    clock reported, and every throttle reason seen active in any sample;
+    header, unit or malformed lines are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    na, act = "Not Active", "Active"
+    lines = [
+        "index, clocks.sm [MHz], clocks.max.sm [MHz], power.draw [W], ...",
+        f"0, 2070, 2070, 900.5, 0x0, {na}, {na}, {na}, {na}",
+        f"0, 1980, 2070, 1400.0, 0x4, {na}, {na}, {na}, {act}",
+        f"0, 2070, 2070, 1100.2, 0x0, {na}, {na}, {na}, {na}",
+        "0, [N/A], 2070, 0, 0x0, N/A, N/A, N/A, N/A",
+        "garbage",
+    ]
+    s = bench.ClockSampler.summarise(lines)
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    hot = bench.ClockSampler.summarise([f"0, 1500, 2070, 1300, 0x8, {na}, {act}, {act}, {na}"])
+    assert hot["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise([])["sm_mhz"] is None
+
+
+def test_kernels_per_step_counts_the_launches_of_a_call():
+    """gpu_launches: the sort (count, three scans, scatter; one copy of the
+    queries in their own order when the sort is off), then either the
+    one-pass kernel, which writes the outputs itself, or per concurrent
+    range the nn pass, three scans, the vertex scatter and the list pass,
+    and then the output write.  A range holds at least 2^18 queries."""
+    sys.path.insert(0, ROOT)
+    import bench
+    two_pass = {"sort_bits": 12, "group_by_vertex": 1, "warp_cooperative": 0, "streams": 2}
+    assert bench.kernels_per_step(two_pass, 10_000_000) == 5 + 12 + 1
+    assert bench.kernels_per_step(two_pass, 100_000) == 5 + 6 + 1
+    assert bench.kernels_per_step(dict(two_pass, streams=1), 10_000_000) == 12
+    one_pass = {"sort_bits": 0, "group_by_vertex": 0}
+    assert bench.kernels_per_step(one_pass, 100_000) == 2
+    assert bench.kernels_per_step(dict(two_pass, warp_cooperative=1), 10_000_000) == 6
