@@ -45,6 +45,15 @@ MUTATIONS = [
     ("Region box without the edge crossings",
      "          GROW(xc);\n        }\n      }",
      "          (void)xc;\n        }\n      }"),
+    ("ties between types reversed",
+     "  if (a->type != b->type) return a->type < b->type;",
+     "  if (a->type != b->type) return a->type > b->type;"),
+    ("ties between ids reversed",
+     "  return a->id < b->id;\n}",
+     "  return a->id > b->id;\n}"),
+    ("second-best distance kept from earlier bests only",
+     "    else if (cand_better(&c, &sec)) sec = c;         \\",
+     "    else if (0) sec = c;                             \\"),
 ]
 
 

@@ -212,6 +212,67 @@ def test_kdt_ties_go_to_lowest_index():
     assert nn[0] == 0
 
 
+def test_primitive_ties_follow_the_type_then_id_order():
+    """Equidistant primitives: the paper fixes no order (Sec. 4.1 asks for
+    the minimum only); the reading taken is vertex < edge < face, then the
+    lower id.  Every coordinate is a dyadic rational, so each tie below is
+    exact in FP64; the tied distances are confirmed with the closed-triangle
+    projection, one triangle at a time."""
+    q = np.array([[0.25, 0.25, 1.0]])
+    base = [[0, 0, 0], [1, 0, 0], [0, 1, 0]]  # face 0, at distance 1 under q
+    # vertex 3 at distance 1 above q, its triangle rising away from q
+    # (its face and its edges are farther): vertex 3 before face 0
+    V = np.array(base + [[0.25, 0.25, 2], [0.25, 3, 5], [3, 0.25, 5]], np.float32)
+    # the open edge 3-4 passes 1 above q (closest point its midpoint), its
+    # triangle rising away: that edge before face 0
+    W = np.array(base + [[-1, 0.25, 2], [1.5, 0.25, 2], [0.25, 3, 5]], np.float32)
+    F = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    for X in (V, W):
+        for tri in F:
+            assert closest_on_closed_triangles(X, tri[None], q)[0] == 1.0
+    o = oracle.OracleMesh(V, F)
+    for r in (o.bruteforce(q), o.query(q), o.query(q, use_boxes=True)):
+        assert r["dist"][0] == 1.0 and (r["ptype"][0], r["pid"][0]) == (0, 3)
+    o = oracle.OracleMesh(W, F)
+    e = [list(x) for x in o.edges()].index([3, 4])
+    for r in (o.bruteforce(q), o.query(q), o.query(q, use_boxes=True)):
+        assert r["dist"][0] == 1.0 and (r["ptype"][0], r["pid"][0]) == (1, e)
+        assert np.array_equal(r["cp"][0], [0.25, 0.25, 2.0])
+    # two faces at z = +1 and z = -1 over the same corner, q midway: the
+    # lower face id wins, whichever of the two triangles is listed first
+    up = [[0, 0, 1], [2, 0, 1], [0, 2, 1]]
+    down = [[0, 0, -1], [2, 0, -1], [0, 2, -1]]
+    p = np.array([[0.5, 0.5, 0.0]])
+    for first, z in ((up, 1.0), (down, -1.0)):
+        X = np.array(first + (down if first is up else up), np.float32)
+        o = oracle.OracleMesh(X, F)
+        for r in (o.bruteforce(p), o.query(p), o.query(p, use_boxes=True)):
+            assert r["dist"][0] == 1.0 and (r["ptype"][0], r["pid"][0]) == (2, 0)
+            assert np.array_equal(r["cp"][0], [0.5, 0.5, z])
+
+
+def test_second_best_distance_closed_form():
+    """``second``, the best distance over every primitive but the reported
+    one (what near-tie detection reads), in closed form: two parallel
+    triangles at z = 0 and z = 1/2.  Under both, the best is face 0 at 1 and
+    the second face 1 at 3/2 (listed after the best), not face 0's nearest
+    edge at sqrt(5); midway between them both faces are at 1/4 (a tie: the
+    second is 1/4 too).  Over face 0 alone the second is its nearest edge:
+    sqrt(5) under it, sqrt(1 + 1/16) a quarter above (1, 1)."""
+    V = np.array([[0, 0, 0], [8, 0, 0], [0, 8, 0],
+                  [0, 0, 0.5], [8, 0, 0.5], [0, 8, 0.5]], np.float32)
+    F = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    q = np.array([[2.0, 2.0, -1.0], [1.0, 1.0, 0.25]])
+    r = oracle.OracleMesh(V, F, build_tables=False).bruteforce(q)
+    assert np.allclose(r["dist"], [1.0, 0.25], rtol=0, atol=1e-15)
+    assert (r["ptype"] == 2).all() and list(r["pid"]) == [0, 0]
+    assert np.allclose(r["second"], [1.5, 0.25], rtol=0, atol=1e-15)
+    V1 = V[:3]
+    r = oracle.OracleMesh(V1, F[:1], build_tables=False).bruteforce(q)
+    assert np.allclose(r["second"], [math.sqrt(5.0), math.sqrt(1.0 + 0.0625)], rtol=0,
+                       atol=1e-15)
+
+
 # --------------------------------------------------------------------------
 # convex polytope cutting (Sec. 4.4 "Implementation") and Voronoi cells
 # --------------------------------------------------------------------------
