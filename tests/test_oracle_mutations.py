@@ -54,6 +54,15 @@ MUTATIONS = [
     ("second-best distance kept from earlier bests only",
      "    else if (cand_better(&c, &sec)) sec = c;         \\",
      "    else if (0) sec = c;                             \\"),
+    ("KD tree prunes a subtree at equal distance",
+     "  if (kd_box_d2(m, node, q) > *bd2) return;",
+     "  if (kd_box_d2(m, node, q) >= *bd2) return;"),
+    ("widened cells' bisectors not pushed out",
+     "    bisector_plane(m, (int32_t)i, x->nbs[i][j], m->delta, pl);",
+     "    bisector_plane(m, (int32_t)i, x->nbs[i][j], 0.0, pl);"),
+    ("widened cells' domain not grown",
+     "  for (int d = 0; d < 3; ++d) { lo[d] = m->dlo[d] - m->delta; hi[d] = m->dhi[d] + m->delta; }",
+     "  for (int d = 0; d < 3; ++d) { lo[d] = m->dlo[d]; hi[d] = m->dhi[d]; }"),
 ]
 
 
@@ -82,7 +91,7 @@ def _pins_with_oracle_copy(base, name, old, new):
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     runs = [("unmodified", None, None)] + MUTATIONS
-    with cf.ThreadPoolExecutor(4) as ex:
+    with cf.ThreadPoolExecutor(max(4, min(8, os.cpu_count() or 4))) as ex:
         res = list(ex.map(lambda m: _pins_with_oracle_copy(str(tmp_path), *m), runs))
     code, out = res[0]
     assert code == 0, "the unmodified copy must pass the pins:\n" + out

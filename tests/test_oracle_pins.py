@@ -212,6 +212,23 @@ def test_kdt_ties_go_to_lowest_index():
     assert nn[0] == 0
 
 
+def test_kdt_ties_on_a_lattice_go_to_lowest_index():
+    """Equidistant vertices go to the lowest index (reading 7), where ties
+    are everywhere: a shuffled 6x6x6 integer lattice, queried at every
+    half-integer point of its box (cube centres tie 8 vertices, face centres
+    4, edge midpoints 2; all exact in FP64), against numpy's first minimum
+    over the squared distances."""
+    r_ = rng(21)
+    g = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    V = g[r_.permutation(len(g))].astype(np.float32)
+    F = np.arange(len(V), dtype=np.int32).reshape(-1, 3)
+    o = oracle.OracleMesh(V, F, build_tables=False)
+    h = np.arange(0, 5.01, 0.5)
+    q = np.stack(np.meshgrid(h, h, h, indexing="ij"), -1).reshape(-1, 3)
+    nn, _ = o.kdt_nn(q)
+    np.testing.assert_array_equal(nn, brute_nn(V, q))
+
+
 def test_primitive_ties_follow_the_type_then_id_order():
     """Equidistant primitives: the paper fixes no order (Sec. 4.1 asks for
     the minimum only); the reading taken is vertex < edge < face, then the
@@ -466,6 +483,30 @@ def small_meshes():
     m = dg.workload(2, n_queries=10, grid=24)
     out["heightfield-24"] = (m.verts, m.tris, m.domain_scale, m.domain_margin)
     return out
+
+
+@pytest.mark.parametrize("name", ["noisy-L3", "cube", "heightfield-24"])
+def test_widened_cells_are_the_cells_pushed_out_by_delta(small_meshes, name):
+    """The widened cell of v, which the flooding clips (the conservative
+    relaxation by delta): D grown by delta, cut by the bisector of every
+    Voronoi neighbour pushed delta away from v.  Each corner the oracle
+    reports keeps every one of those constraints and lies on at least three
+    of them (a corner of that polytope), checked from the positions."""
+    V, F, s, mg = small_meshes[name]
+    o = oracle.OracleMesh(V, F, s, mg)
+    P = o.V
+    lo, hi = o.domain_lo - o.delta, o.domain_hi + o.delta
+    tol = 1e-9 * float(np.linalg.norm(o.domain_hi - o.domain_lo))
+    for v in range(o.nv):
+        X = o.cell_corners(v)
+        nb = o.cell_neighbors(v)
+        assert len(X) >= 4 and len(nb) >= 1
+        n = P[nb] - P[v]
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        mid = 0.5 * (P[nb] + P[v])
+        slack = np.concatenate([X @ n.T - (n * mid).sum(1) - o.delta, lo - X, X - hi], 1)
+        assert slack.max() <= tol, (name, v)
+        assert ((np.abs(slack) <= tol).sum(1) >= 3).all(), (name, v)
 
 
 @pytest.mark.parametrize("name", ["noisy-L3", "sphere-L2", "cube", "octahedron", "heightfield-24"])
