@@ -519,3 +519,23 @@ def test_builder_tables_equal_oracle_tables_on_a_lat_long_sphere(pg):
     m = dg.Mesh("latlong-6x48", V.astype(np.float32), F.astype(np.int32),
                 np.zeros((1, 3), np.float32), 1.25, 0.02, meta={})
     _check_tables(pg, m)
+
+
+@pytest.mark.parametrize("name", ["displaced-L4", "heightfield-40", "soup", "mixed"])
+def test_packed_codes_nest(pg, tmp_path, name):
+    """The two-level R-tree over each interception list is conservative:
+    on every axis the float32 values an entry's 15-bit code test admits (in
+    its chunk's frame) lie inside those its chunk's code test admits (in the
+    global frame), and a chunk's inside its super-chunk's, so a query the
+    entry test admits is never skipped at a chunk or a super-chunk.  Read
+    from the saved layout and decided exactly (tests/packed_codes.py)."""
+    from tests import packed_codes
+    m = {"displaced-L4": lambda: dg.workload(1, n_queries=10, level=4),
+         "heightfield-40": lambda: dg.workload(2, n_queries=10, grid=40),
+         "soup": lambda: dg.soup_workload("penetrating", level=2, n_queries=10),
+         "mixed": lambda: dg.mixed_workload(mesh_level=2, wire_level=1, n_queries=10)}[name]()
+    h = _host(pg, m)
+    p = str(tmp_path / "m.p2m")
+    h.save(p)
+    arr, lo, inv = packed_codes.read_layout(p)
+    assert packed_codes.check_codes_nest(arr, lo, inv) == h.stats()["n_entries"]

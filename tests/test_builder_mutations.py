@@ -1,7 +1,7 @@
 """Mutation check of the host tests of the product builder: every mistake
 below, planted in a copy of the library sources, makes the builder-versus-
-oracle table tests of tests/test_abi_host.py fail, while the unmodified
-copy passes them.  Each copy of the package is built into a temporary
+oracle table tests or the nesting test of the packed box codes in
+tests/test_abi_host.py fail, while the unmodified copy passes them.  Each copy of the package is built into a temporary
 directory and tested in a subprocess on the CPU (no GPU is visible to it);
 the committed sources are never touched."""
 import concurrent.futures as cf
@@ -27,9 +27,20 @@ MUTATIONS = [
     ("flood never leaves the seeds", "flood_core.h",
      "      if (env.mark(w, queue, tail)) {",
      "      if (false && env.mark(w, queue, tail)) {"),
+    ("chunk codes without their two-code widening", "builder.cpp",
+     "        cl[d] = a >= 2 ? a - 2 : 0;\n        ch[d] = std::min(kQMax, b + 2);",
+     "        cl[d] = a;\n        ch[d] = b;"),
+    ("super-chunk codes from its first chunk only", "builder.cpp",
+     "      for (uint32_t k = c; k < ce; ++k) {\n        uint32_t cl[3], ch[3];",
+     "      for (uint32_t k = c; k < c + 1; ++k) {\n        uint32_t cl[3], ch[3];"),
+    ("chunk hull from its first entry only", "builder.cpp",
+     "      for (uint32_t k = j; k < j + cnt; ++k)\n        for (int d = 0; d < 3; ++d) {\n"
+     "          lo[d] = std::min(lo[d], all[k].box[d]);",
+     "      for (uint32_t k = j; k < j + 1; ++k)\n        for (int d = 0; d < 3; ++d) {\n"
+     "          lo[d] = std::min(lo[d], all[k].box[d]);"),
 ]
 
-TESTS = "tables_equal_oracle_tables and not random"
+TESTS = "(tables_equal_oracle_tables and not random) or packed_codes"
 
 
 def _host_tests_with_copy(base, name, fname, old, new):
@@ -60,7 +71,7 @@ def _host_tests_with_copy(base, name, fname, old, new):
 
 def test_every_planted_builder_mistake_fails_a_host_test(tmp_path):
     runs = [("unmodified", None, None, None)] + MUTATIONS
-    with cf.ThreadPoolExecutor(3) as ex:
+    with cf.ThreadPoolExecutor(4) as ex:
         res = list(ex.map(lambda m: _host_tests_with_copy(str(tmp_path), *m), runs))
     code, out = res[0]
     assert code == 0, "the unmodified copy must pass:\n" + out
