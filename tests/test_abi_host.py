@@ -539,3 +539,44 @@ def test_packed_codes_nest(pg, tmp_path, name):
     h.save(p)
     arr, lo, inv = packed_codes.read_layout(p)
     assert packed_codes.check_codes_nest(arr, lo, inv) == h.stats()["n_entries"]
+
+
+@pytest.mark.parametrize("name,leaf", [("displaced-L4", 8), ("heightfield-40", 3), ("soup", 32)])
+def test_kd_tree_boxes_are_the_hulls_of_their_points(pg, tmp_path, name, leaf):
+    """The layout's KD tree, which the nearest-vertex modes and the exact
+    searches descend: leaf j of the 2^depth leaves holds tree positions
+    [j nv / L, (j + 1) nv / L); internal node i (heap order) stores the boxes
+    of its children 2i + 1 and 2i + 2.  Every such box is the float32 hull
+    of the points below it, the root box that of all; the tree's points are
+    the vertices, each once, and pos_of_vertex is the inverse order."""
+    from tests import packed_codes
+    m = {"displaced-L4": lambda: dg.workload(1, n_queries=10, level=4),
+         "heightfield-40": lambda: dg.workload(2, n_queries=10, grid=40),
+         "soup": lambda: dg.soup_workload("penetrating", level=2, n_queries=10)}[name]()
+    h = _host(pg, m, leaf_size=leaf)
+    p = str(tmp_path / "m.p2m")
+    h.save(p)
+    arr, _, _ = packed_codes.read_layout(p)
+    raw = open(p, "rb").read()
+    depth = int(np.frombuffer(raw[12:108], np.int64)[3])
+    root = np.frombuffer(raw[108:184], np.float32)[7:13]
+    nv = h.n_verts
+    L = 1 << depth
+    kp = arr["kd_points"].reshape(nv, 4)
+    ids = kp[:, 3].view(np.int32)
+    pts = kp[:, :3].view(np.float32)
+    np.testing.assert_array_equal(np.sort(ids), np.arange(nv))
+    np.testing.assert_array_equal(pts, np.asarray(m.verts, np.float32)[ids])
+    np.testing.assert_array_equal(arr["pos_of_vertex"].view(np.int32)[ids], np.arange(nv))
+    assert L <= nv and -(-nv // L) <= max(2, leaf)
+    np.testing.assert_array_equal(root, np.concatenate([pts.min(0), pts.max(0)]))
+    nodes = arr["kd_nodes"].view(np.float32).reshape(L - 1, 12)
+    for i in range(L - 1):
+        k = int(np.floor(np.log2(i + 1)))
+        span = L >> (k + 1)                    # leaves under each child
+        a = (i - ((1 << k) - 1)) * 2 * span    # first leaf of child 2i + 1
+        for c, box in enumerate((nodes[i, :6], nodes[i, 6:])):
+            lo_leaf = a + c * span
+            s, e = (lo_leaf * nv) >> depth, ((lo_leaf + span) * nv) >> depth
+            assert e > s
+            np.testing.assert_array_equal(box, np.concatenate([pts[s:e].min(0), pts[s:e].max(0)]))

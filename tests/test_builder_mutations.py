@@ -1,7 +1,8 @@
 """Mutation check of the host tests of the product builder: every mistake
 below, planted in a copy of the library sources, makes the builder-versus-
-oracle table tests or the nesting test of the packed box codes in
-tests/test_abi_host.py fail, while the unmodified copy passes them.  Each copy of the package is built into a temporary
+oracle table tests, the nesting test of the packed box codes or the KD
+tree's box test in tests/test_abi_host.py fail, while the unmodified copy
+passes them.  Each copy of the package is built into a temporary
 directory and tested in a subprocess on the CPU (no GPU is visible to it);
 the committed sources are never touched."""
 import concurrent.futures as cf
@@ -38,9 +39,12 @@ MUTATIONS = [
      "          lo[d] = std::min(lo[d], all[k].box[d]);",
      "      for (uint32_t k = j; k < j + 1; ++k)\n        for (int d = 0; d < 3; ++d) {\n"
      "          lo[d] = std::min(lo[d], all[k].box[d]);"),
+    ("KD children's boxes exported swapped", "builder.cpp",
+     "    const double *c0 = &T.box[6 * (2 * i + 1)], *c1 = &T.box[6 * (2 * i + 2)];",
+     "    const double *c0 = &T.box[6 * (2 * i + 2)], *c1 = &T.box[6 * (2 * i + 1)];"),
 ]
 
-TESTS = "(tables_equal_oracle_tables and not random) or packed_codes"
+TESTS = "(tables_equal_oracle_tables and not random) or packed_codes or kd_tree_boxes"
 
 
 def _host_tests_with_copy(base, name, fname, old, new):
