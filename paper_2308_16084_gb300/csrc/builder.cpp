@@ -1229,10 +1229,11 @@ int build_layout(const float *Vin, int64_t nv, const int32_t *Fin, int64_t nf,
     pb.delta = delta;
     pb.eta = eta;
     // host workers beside the thread that drives the device; the device
-    // floods about as fast as 22 Grace cores (390 k against 13 k primitives
-    // a second on the 1.3M-triangle mesh), so its first share is, unless
-    // set, 22.5 / (22.5 + workers) of all, and each later call takes 0.6 of
-    // what is left while that is at least flood_min_share primitives
+    // floods about as fast as 30 Grace cores (390 k against 13 k primitives
+    // a second on the 1.3M-triangle mesh); its first share is, unless set,
+    // 22.5 / (22.5 + workers) of all, a little less than that rate gives it,
+    // and each later call takes 0.6 of what is left while that is at least
+    // flood_min_share primitives
     const int nw = prm.flood_host_workers >= 0 ? std::min(prm.flood_host_workers, threads)
                    : (threads > 2 ? threads - 1 : 1);
     constexpr int64_t kBlock = 64;
